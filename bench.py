@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the heat + CG hot path on GB300.
+
+One step = one pass of the whole path over one batch of synthetic input:
+  heat: upload u0 (512^3 interior, 8 sine modes + 1e-3 noise), 1000 FTCS steps
+        at r = 0.15 in FP64 (Boundary + Interior kernels, pointer swap), read back;
+  CG:   solve the 256^3 7-point Dirichlet Laplacian system, b ~ N(0,1),
+        rtol 1e-8, FP64, once matrix-free and once with the CSR int32 matrix.
+``value`` is heat GLUP/s over the heat segment of the timed steps (device time
+from CUDA events on the launching stream); CG iterations/s and p50/p99 solve
+latencies are reported beside it.  All inputs are larger than L2 (129 MB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(independent replicas: the path has no exchange step on one box), the timed
+region is bracketed by barriers, and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUP/s & % of HBM peak (heat 512³ FP64/FP32); CG it/s; p50/p99 solve latency"
+SEED = 20261202
+FP64_INSTR_PER_LUP = 7          # 5 DADD + 2 DFMA in the Interior kernel
+BYTES_PER_LUP_F64 = 16          # read u once, write u' once
+# FP64 issue peak derived from the nominal 1.25 TFLOP/s (FMA = 2 flops): 0.625e12 instr/s
+FP64_INSTR_PEAK_T = 0.625
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--heat-n", type=int, default=512)
+    ap.add_argument("--heat-steps", type=int, default=1000)
+    ap.add_argument("--r", type=float, default=0.15)
+    ap.add_argument("--cg-n", type=int, default=256)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows, self.proc, self.thread = [], None, None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() in ("active", "yes", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------------
+def cpu_baseline(args, threads):
+    """The oracle as it stands, on this host's cores, on a bounded sample of the
+    workload: a few 512^3 FP64 steps (timed step loop only) and a few CG
+    iterations on 256^3."""
+    import numpy as np
+
+    import oracle
+    from workloads import cg_rhs, heat_u0_modes
+
+    oracle.build()
+    n = args.heat_n
+    u0, _, _ = heat_u0_modes(n, n, n, seed=SEED)
+    _, t1 = oracle.heat_run(u0, args.r, 1, threads=threads, return_seconds=True)
+    steps = int(max(2, min(200, 12.0 / max(t1, 1e-3))))
+    _, secs = oracle.heat_run(u0, args.r, steps, threads=threads, return_seconds=True)
+    glups = n ** 3 * steps / secs / 1e9
+    m = args.cg_n
+    b = cg_rhs(m ** 3, seed=SEED)
+    cg_iters = 20
+    _, info = oracle.cg_solve(b, 1e-30, cg_iters, shape=(m, m, m), threads=threads)
+    return {"value": glups, "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+            "sample": f"heat {n}^3 FP64 r={args.r}, {steps} of {args.heat_steps} steps, timed step "
+                      f"loop only; CG matrix-free {m}^3, {cg_iters} iterations",
+            "cg_matrix_free_its_per_s": cg_iters / info["loop_seconds"]}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample (a few 512^3 heat steps) of the same workload and metric."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from workloads import heat_u0_modes
+
+    oracle.build()
+    threads = host_cores()
+    n = args.heat_n
+    u0, _, _ = heat_u0_modes(n, n, n, seed=SEED)
+    _, t1 = oracle.heat_run(u0, args.r, 1, threads=threads, return_seconds=True)
+    per = int(max(1, min(50, 8.0 / max(t1, 1e-3))))   # heat steps per sample
+    times = []
+    for s in range(args.warmup + args.steps):
+        _, secs = oracle.heat_run(u0, args.r, per, threads=threads, return_seconds=True)
+        if s >= args.warmup:
+            times.append(secs)
+    total = sum(times)
+    value = n ** 3 * per * len(times) / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"heat {n}^3 FP64 r={args.r} (sample: {per} steps per bench step)",
+                       "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per} heat steps of {n}^3 per bench step"},
+            "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    from paper_2608_11882_gb300.build import build
+    build()
+    import paper_2608_11882_gb300 as pkg
+    from paper_2608_11882_gb300 import _native as nat
+    from workloads import cg_rhs, heat_u0_modes, lap7_csr
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    n, m = args.heat_n, args.cg_n
+    stream = torch.cuda.current_stream()
+
+    # ---- inputs (seeded, synthetic), resident in HBM before timing -------------
+    u0_np, _, _ = heat_u0_modes(n, n, n, seed=SEED)
+    u0_host = torch.from_numpy(u0_np).pin_memory()
+    u0_dev = u0_host.to("cuda", non_blocking=False)
+    u_out_dev = torch.empty_like(u0_dev)
+    b_np = cg_rhs(m ** 3, seed=SEED)
+    b_host = torch.from_numpy(b_np).pin_memory()
+    b_dev = b_host.cuda()
+    rowptr, col, val = lap7_csr(m, m, m)
+    csr_dev = [torch.from_numpy(a).cuda() for a in (rowptr, col, val)]
+    nnz = int(col.size)
+    del rowptr, col, val
+    x_mf = torch.zeros(m ** 3, dtype=torch.float64, device="cuda")
+    x_csr = torch.zeros_like(x_mf)
+
+    heat = pkg.Heat(n, n, n, args.r, dtype="f64", stream=stream)
+    cg_mf = pkg.CG(pkg.Operator.stencil(m, m, m), stream=stream)
+    cg_csr = pkg.CG(pkg.Operator.csr(*csr_dev), stream=stream)
+    torch.cuda.synchronize()
+
+    hsteps = args.heat_steps
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(hsteps)]
+
+    def one_step(timed_interior: bool):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        heat.upload(u0_dev)
+        if timed_interior:
+            for s in range(hsteps):
+                heat.boundary()
+                pairs[s][0].record(stream)
+                heat.interior()
+                pairs[s][1].record(stream)
+                heat.swap()
+        else:
+            heat.step(hsteps)
+        heat.read(u_out_dev)
+        ev[1].record(stream)
+        x_mf.zero_()
+        _, info_mf = cg_mf.run(b_dev, x_mf, rtol=args.rtol, max_iter=20000)
+        ev[2].record(stream)
+        x_csr.zero_()
+        _, info_csr = cg_csr.run(b_dev, x_csr, rtol=args.rtol, max_iter=20000)
+        ev[3].record(stream)
+        return ev, info_mf, info_csr
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    launches0 = nat.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    seg = {"heat": [], "cg_mf": [], "cg_csr": []}
+    interior_ms = []
+    infos = []
+    for s in range(args.steps):
+        ev, i_mf, i_csr = one_step(True)
+        ev[3].synchronize()
+        seg["heat"].append(ev[0].elapsed_time(ev[1]))
+        seg["cg_mf"].append(ev[1].elapsed_time(ev[2]))
+        seg["cg_csr"].append(ev[2].elapsed_time(ev[3]))
+        interior_ms.append(sum(a.elapsed_time(b) for a, b in pairs) / hsteps)
+        infos.append((i_mf, i_csr))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = nat.launch_count() - launches0
+    clock_info = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    heat_ms = sum(seg["heat"])
+    if world > 1:
+        t = torch.tensor([elapsed_ms, heat_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms, heat_ms = float(t[0]), float(t[1])
+
+    lup_step = float(n) ** 3 * hsteps
+    value = world * lup_step * args.steps / (heat_ms * 1e-3) / 1e9
+    hbm_gbs, peak_kind = measured_peaks()
+
+    # dominant kernel: the FP64 Interior kernel (ALU bound on GB300's FP64 pipe)
+    int_ms = statistics.mean(interior_ms)
+    lup_interior = float(n) * n * max(n - 2, 0)
+    instr_rate = lup_interior * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
+    hbm_rate = lup_interior * BYTES_PER_LUP_F64 / (int_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_heat_interior<double> (FP64, 7 instr/LUP)",
+                "achieved": instr_rate, "peak": FP64_INSTR_PEAK_T, "unit": "T FP64-instr/s",
+                "frac": instr_rate / FP64_INSTR_PEAK_T, "traffic": None,
+                "hbm_achieved_gbs": hbm_rate, "hbm_peak_gbs": hbm_gbs,
+                "hbm_frac": hbm_rate / hbm_gbs, "hbm_peak_kind": peak_kind,
+                "interior_ms_per_launch": int_ms}
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    it_mf = [i[0]["iters"] for i in infos]
+    it_csr = [i[1]["iters"] for i in infos]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"heat {n}^3 FP64 r={args.r} {hsteps} steps (u0 = 8 sine modes k in "
+                               f"[1,16] + 1e-3 U[-1,1]) + CG {m}^3 FP64 7-pt Dirichlet Laplacian, "
+                               f"matrix-free and CSR int32 (nnz {nnz}), b ~ N(0,1), rtol {args.rtol}",
+                   "value_covers": "heat segment (upload + steps + device readback), device time",
+                   "l2": "no flush: every input exceeds L2 (field 1.07 GB, vectors 134 MB)",
+                   "parallelism": f"replicas x{world}", "seed": SEED},
+        "heat": {"glups": value / world, "ms_per_solve": heat_ms / args.steps,
+                 "hbm_frac_16B_per_lup": value / world * 16 / hbm_gbs},
+        "cg": {"matrix_free": {"iters": it_mf[-1], "its_per_s": it_mf[-1] / (statistics.median(seg["cg_mf"]) * 1e-3),
+                               "ms_per_solve": statistics.median(seg["cg_mf"]),
+                               "relres_true": infos[-1][0]["relres_true"]},
+               "csr": {"iters": it_csr[-1], "its_per_s": it_csr[-1] / (statistics.median(seg["cg_csr"]) * 1e-3),
+                       "ms_per_solve": statistics.median(seg["cg_csr"]),
+                       "relres_true": infos[-1][1]["relres_true"]}},
+        "latency_ms": {k: {"p50": pct(v, 0.5), "p99": pct(v, 0.99)} for k, v in seg.items()},
+        "roofline": roofline,
+        "clocks": clock_info,
+        "gpu_launches": launches,
+    }
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    if not args.no_e2e:
+        u_back = torch.empty_like(u0_host).pin_memory()
+        x_host = torch.zeros(m ** 3, dtype=torch.float64).pin_memory()
+        e2e_heat, e2e_cg = [], []
+        barrier()
+        for s in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            heat.upload(u0_host)                   # pinned host -> device
+            heat.step(hsteps)
+            heat.read(u_back)                      # device -> pinned host (synchronises)
+            t1 = time.perf_counter()
+            x_host.zero_()
+            cg_mf.run(b_host.numpy(), x_host.numpy(), rtol=args.rtol, max_iter=20000)
+            t2 = time.perf_counter()
+            e2e_heat.append(t1 - t0)
+            e2e_cg.append(t2 - t1)
+        e2e_t = max(sum(e2e_heat), 0.0)
+        if world > 1:
+            t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_t = float(t[0])
+        line["e2e"] = {"value": world * lup_step * args.steps / e2e_t / 1e9, "unit": "GLUP/s",
+                       "h2d_bytes_per_step": int(u0_host.numel() * 8),
+                       "d2h_bytes_per_step": int(u_back.numel() * 8),
+                       "covers": "heat: heat_upload from pinned host, heat_step, heat_read to pinned host",
+                       "cg_matrix_free_host_buffers_its_per_s": it_mf[-1] / statistics.median(e2e_cg)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, host_cores())
+
+    heat.close()
+    cg_mf.close()
+    cg_csr.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

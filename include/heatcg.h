@@ -1,0 +1,197 @@
+/*
+ * heatcg.h -- C ABI of the GB300 (sm_103a) heat-stencil and CG library.
+ *
+ * The library advances the three-dimensional heat equation of Section 4 with
+ * the explicit update of Eq. 4 in its constant-coefficient form
+ *
+ *     u'[k,j,i] = u + r * ((u[i-1] + u[i+1]) + (u[j-1] + u[j+1]) + (u[k-1] + u[k+1]) - 6 u)
+ *
+ * (r = alpha*dt/h^2) on a box whose boundary values are held at zero, and
+ * solves the companion system A x = b of Section 7.5 by conjugate gradients,
+ * A being the 7-point Dirichlet Laplacian (CSR or matrix-free).
+ *
+ * Conventions shared by every entry point:
+ *   - Grid sizes are INTERIOR counts nx, ny, nz (the boundary layer is not
+ *     counted; h = 1/(n+1) per axis).  Fields cross the ABI as dense arrays
+ *     of nx*ny*nz elements, x fastest, then y, then z (the paper's k, j, i
+ *     loop order, Algorithm COMPUTE_SINGLE_GPU).
+ *   - Every function returns HS_OK (0) or a negative HS_E* code.  On error,
+ *     hs_last_error() returns a message for the calling thread, and nothing
+ *     has been enqueued unless the code is HS_ECUDA.
+ *   - "stream" arguments are cudaStream_t handles passed as void*; NULL
+ *     means the legacy default stream.  Work is enqueued asynchronously on
+ *     that stream unless a function says it synchronises.
+ *   - Pointers marked "device" must be device (or managed) memory of the
+ *     current CUDA device; the caller keeps ownership of every buffer it
+ *     passes in and must keep it alive until the work that uses it is done.
+ *   - The library is not thread safe per handle: one handle, one thread at a
+ *     time.  Distinct handles may be used from distinct threads.
+ */
+#ifndef HEATCG_H
+#define HEATCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define HS_OK          0
+#define HS_EINVAL     (-1)  /* bad size, pointer, flag or dtype            */
+#define HS_ENOMEM     (-2)  /* device or pinned-host allocation failed     */
+#define HS_ECUDA      (-3)  /* a CUDA call or kernel launch failed         */
+#define HS_EUNSTABLE  (-4)  /* r > 1/6 without HS_ALLOW_UNSTABLE           */
+#define HS_ENOCONV    (-5)  /* CG stopped at max_iter before reaching rtol */
+#define HS_ETIMEOUT   (-6)  /* a bounded device-side wait expired          */
+#define HS_EBUSY      (-7)  /* the handle has work in a state that forbids the call */
+#define HS_ERANGE     (-8)  /* a value lies outside the range a format can hold */
+
+/* ---- element types ---------------------------------------------------- */
+#define HS_F64 0
+#define HS_F32 1
+
+/* ---- heat handle flags ------------------------------------------------ */
+/* Accept r > 1/6.  The explicit update of Eq. 4 is stable in three
+ * dimensions only for r <= 1/6 (Section 4, Eq. 6 prints the one-dimensional
+ * bound dt/h^2 < 0.5); larger r makes the highest grid mode grow. */
+#define HS_ALLOW_UNSTABLE   0x1u
+/* FP64 only: evaluate the update with one rounding per operation, in exactly
+ * the order written above and without fused multiply-add (the paper compiles
+ * with --fmad=false / -ffp-contract=off, Section 5, table of compiler
+ * flags).  Slower (9 instead of 7 FP64 instructions per point). */
+#define HS_EXACT_ROUNDING   0x2u
+/* Advance each step with one kernel over the whole interior (Algorithm
+ * COMPUTE_SINGLE_GPU) instead of the Interior + Boundary pair (Algorithms
+ * INTERIOR and BOUNDARY).  Results are bitwise identical either way. */
+#define HS_SCHED_FULL       0x4u
+
+typedef struct hs_heat* hs_heat_t;
+
+typedef struct {
+    int32_t  nx, ny, nz;   /* interior points per axis, each >= 1              */
+    double   r;            /* alpha*dt/h^2 >= 0; see HS_ALLOW_UNSTABLE         */
+    uint32_t flags;        /* HS_* heat flags                                 */
+    int32_t  dtype;        /* HS_F64 or HS_F32: storage and arithmetic type   */
+    int32_t  reserved0;    /* must be 0                                       */
+    void*    stream;       /* cudaStream_t for all work of this handle        */
+} hs_heat_desc;
+
+/* Create a heat handle (Algorithm "1-GPU Baseline", setup and allocation).
+ * Allocates two device buffers of (nz+2) planes x (ny+2) rows x pitch
+ * elements; their boundary layer is zero and is never written again, so the
+ * Dirichlet data survive every buffer swap.  Both buffers start all zero.
+ * Errors: HS_EINVAL (desc NULL, a size < 1, r < 0 or not finite, unknown flag
+ * or dtype), HS_EUNSTABLE (r > 1/6 without HS_ALLOW_UNSTABLE), HS_ENOMEM. */
+int heat_create(hs_heat_t* out, const hs_heat_desc* desc);
+
+/* Device bytes heat_create would allocate for desc (for admission control). */
+int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
+
+/* Load the interior field u (nx*ny*nz elements of the handle's dtype, x
+ * fastest) as the current time level and reset the step counter.  (The paper
+ * copies u_old and u_new alike, Algorithm "1-GPU Baseline"; here the spare
+ * buffer needs no copy: its boundary layer is zero from creation and the next
+ * step writes every interior value of it before any is read.)  u is host memory
+ * if src_is_device == 0 (pinned host memory makes the copy asynchronous),
+ * device memory otherwise.  Enqueued on the handle's stream. */
+int heat_upload(hs_heat_t h, const void* u, int src_is_device);
+
+/* Advance n_steps >= 0 steps.  Each step runs the Boundary kernel on the
+ * first and last interior k-planes and the Interior kernel on the planes
+ * between them (Algorithms BOUNDARY and INTERIOR; on one GPU the planes a
+ * k-split would exchange are the outermost interior planes), then swaps the
+ * buffers by pointer (Algorithm "1-GPU Baseline").  Asynchronous: launch
+ * errors are returned here, errors raised while kernels run are returned by
+ * the next synchronising call. */
+int heat_step(hs_heat_t h, int64_t n_steps);
+
+/* The three parts of one step, for callers that schedule them themselves:
+ * the Interior kernel, the Boundary kernel (each writes the next time level
+ * into the spare buffer), and the pointer swap that makes it current.
+ * heat_step(h, 1) == heat_boundary(h); heat_interior(h); heat_swap(h). */
+int heat_interior(hs_heat_t h);
+int heat_boundary(hs_heat_t h);
+int heat_swap(hs_heat_t h);
+
+/* Copy the current interior field to dst (nx*ny*nz elements, x fastest):
+ * host memory if dst_is_device == 0, device memory otherwise.  Synchronises
+ * the handle's stream and reports any asynchronous error. */
+int heat_read(hs_heat_t h, void* dst, int dst_is_device);
+
+/* Steps applied since the last heat_upload. */
+int heat_steps_done(hs_heat_t h, int64_t* steps);
+
+/* Release the handle and its device buffers (synchronises its stream). */
+int heat_destroy(hs_heat_t h);
+
+/* ---- conjugate gradients (Section 7.5) --------------------------------- */
+#define HS_OP_STENCIL7 0   /* matrix-free 7-point Dirichlet Laplacian on nx*ny*nz */
+#define HS_OP_CSR      1   /* CSR matrix (rowptr, col, val), int32 indices        */
+
+typedef struct {
+    int32_t        kind;      /* HS_OP_STENCIL7 or HS_OP_CSR                     */
+    int32_t        nx, ny, nz;/* STENCIL7: interior grid (n = nx*ny*nz)          */
+    int64_t        n;         /* rows = unknowns (CSR; for STENCIL7 n = nx*ny*nz) */
+    int64_t        nnz;       /* CSR entries                                     */
+    const int32_t* rowptr;    /* CSR row starts, n+1 entries, rowptr[0] = 0      */
+    const int32_t* col;       /* CSR column indices, nnz entries, each in [0, n) */
+    const void*    val;       /* CSR values, nnz entries of dtype               */
+    int32_t        dtype;     /* HS_F64                                          */
+    int32_t        host;      /* 0: rowptr/col/val are device memory; 1: host
+                                 memory that cg_create copies to the device     */
+} hs_op;
+
+typedef struct {
+    int32_t iters;          /* CG iterations taken                            */
+    int32_t status;         /* HS_OK or HS_ENOCONV                            */
+    double  relres_recur;   /* sqrt(r.r)/||b|| of the recurrence at exit      */
+    double  relres_true;    /* ||b - A x|| / ||b|| recomputed at exit         */
+} hs_cg_info;
+
+typedef struct hs_cg* hs_cg_t;
+
+/* y = A p on the device (the SpMV of a CG iteration, Algorithm "spmv" (b)
+ * for CSR).  p and y are device arrays of n FP64 values; A's arrays must be
+ * device memory (host == 0). */
+int op_apply(const hs_op* A, const void* p, void* y, void* stream);
+
+/* Create a CG context: checks A, takes a device copy of A's arrays when
+ * A->host == 1 (otherwise it keeps A's device pointers, which must outlive
+ * the context), and allocates the workspace (r, p, q, reduction partials and
+ * device scalars).  Errors: HS_EINVAL, HS_ENOMEM, HS_ECUDA. */
+int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
+
+/* Solve A x = b by unpreconditioned FP64 CG (textbook form, Section 7.5):
+ * r0 = b - A x0, p0 = r0; each iteration q = A p, alpha = rho/(p.q),
+ * x += alpha p, r -= alpha q, rho' = r.r, stop when sqrt(rho')/||b|| <= rtol,
+ * else p = r + (rho'/rho) p.  x holds x0 on entry (zeros allowed) and the
+ * last iterate on exit.  b and x are host arrays if host_buffers != 0 (copied
+ * in and out on the context's stream), device arrays otherwise.  Dot products
+ * accumulate in FP64 in a fixed order, so repeated runs agree bit for bit.
+ * Synchronises the stream.  Returns HS_OK when converged, HS_ENOCONV when
+ * max_iter iterations ran without reaching rtol (x and info are still
+ * filled), or an error code.  info may be NULL. */
+int cg_run(hs_cg_t c, const void* b, void* x, int host_buffers, double rtol, int32_t max_iter,
+           hs_cg_info* info);
+
+/* Release a CG context (synchronises its stream). */
+int cg_destroy(hs_cg_t c);
+
+/* One-shot form: cg_create + cg_run (device b and x) + cg_destroy. */
+int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
+             hs_cg_info* info, void* stream);
+
+/* ---- misc ---------------------------------------------------------------- */
+/* Message describing the last error on the calling thread ("" if none). */
+const char* hs_last_error(void);
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int hs_version(void);
+/* Number of kernel launches this library has issued in this process. */
+int64_t hs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEATCG_H */

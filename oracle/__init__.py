@@ -51,7 +51,8 @@ def build(force: bool = False) -> Path:
 
 class _CgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("relres_recur", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("status", ctypes.c_int32)]
+                ("relres_true", ctypes.c_double), ("status", ctypes.c_int32),
+                ("loop_seconds", ctypes.c_double)]
 
 
 class _Op(ctypes.Structure):
@@ -71,6 +72,8 @@ def _load():
         lib.oracle_heat_run.argtypes = [ctypes.c_int32] * 3 + [ctypes.c_double, ctypes.c_int64,
                                                                 dp, dp, ctypes.c_int32]
         lib.oracle_heat_run.restype = ctypes.c_int
+        lib.oracle_heat_run_timed.argtypes = lib.oracle_heat_run.argtypes + [dp]
+        lib.oracle_heat_run_timed.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_lap7_apply.argtypes = [ctypes.c_int32] * 3 + [dp, dp, ctypes.c_int32]
         lib.oracle_csr_spmv.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int32]
@@ -91,24 +94,27 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def heat_run(u0: np.ndarray, r: float, n_steps: int, threads: int = 1) -> np.ndarray:
+def heat_run(u0: np.ndarray, r: float, n_steps: int, threads: int = 1,
+             return_seconds: bool = False):
     """Advance the interior field ``u0`` (shape (nz, ny, nx), x fastest) by
     ``n_steps`` explicit FTCS steps with zero Dirichlet boundary.
 
     Section 4, Eq. 4 in its constant-coefficient form u' = u + r (sum of six
     neighbours - 6u); boundary fixed at zero; the double buffer and pointer
     swap of Algorithm "1-GPU Baseline"; loop order of COMPUTE_SINGLE_GPU.
+    With ``return_seconds`` also returns the wall time of the step loop alone.
     """
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
     if u0.ndim != 3:
         raise ValueError("u0 must have shape (nz, ny, nx)")
     nz, ny, nx = u0.shape
     out = np.empty_like(u0)
-    rc = _load().oracle_heat_run(nx, ny, nz, float(r), int(n_steps), _ptr(u0), _ptr(out),
-                                 int(threads))
+    secs = ctypes.c_double(0.0)
+    rc = _load().oracle_heat_run_timed(nx, ny, nz, float(r), int(n_steps), _ptr(u0), _ptr(out),
+                                       int(threads), ctypes.addressof(secs))
     if rc != 0:
         raise ValueError(f"oracle_heat_run failed with {rc}")
-    return out
+    return (out, secs.value) if return_seconds else out
 
 
 def lap7_apply(p: np.ndarray, threads: int = 1) -> np.ndarray:
@@ -174,7 +180,8 @@ def cg_solve(b: np.ndarray, rtol: float, max_iter: int, *, shape=None, csr=None,
     if rc != 0:
         raise ValueError(f"oracle_cg failed with {rc}")
     return x, {"iters": info.iters, "relres_recur": info.relres_recur,
-               "relres_true": info.relres_true, "status": info.status}
+               "relres_true": info.relres_true, "status": info.status,
+               "loop_seconds": info.loop_seconds}
 
 
 def sine_mode_factor(k: tuple, n: tuple, r: float) -> float:

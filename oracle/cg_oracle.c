@@ -34,6 +34,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -54,6 +55,7 @@ typedef struct {
     double relres_recur;   /* sqrt(r.r)/||b|| from the recurrence at exit */
     double relres_true;    /* ||b - A x|| / ||b|| recomputed at exit      */
     int32_t status;        /* 0 converged, 1 max_iter reached, -1 breakdown */
+    double loop_seconds;   /* wall time of the iteration loop alone         */
 } oracle_cg_info;
 
 /* y = A p for the matrix-free 7-point Dirichlet Laplacian. */
@@ -148,6 +150,8 @@ int oracle_cg(const oracle_op* A, const double* b, double* x, double rtol, int32
     int32_t it = 0;
     int32_t status = 1;
     if (relres <= rtol) status = 0;
+    struct timespec t0, t1;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
     while (status == 1 && it < max_iter) {
         apply_op(A, p, q, nthreads);
         const double pq = oracle_dot(n, p, q);
@@ -163,6 +167,7 @@ int oracle_cg(const oracle_op* A, const double* b, double* x, double rtol, int32
         for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
         rho = rho_new;
     }
+    clock_gettime(CLOCK_MONOTONIC, &t1);
 
     apply_op(A, x, q, nthreads);              /* true residual b - A x */
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
@@ -170,6 +175,7 @@ int oracle_cg(const oracle_op* A, const double* b, double* x, double rtol, int32
     info->relres_recur = relres;
     info->relres_true = sqrt(oracle_dot(n, r, r)) / bnorm;
     info->status = status;
+    info->loop_seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
     free(r); free(p); free(q);
     return 0;
 }

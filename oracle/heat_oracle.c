@@ -36,6 +36,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -75,8 +76,27 @@ static void heat_one_step(const double* src, double* dst, int64_t nx, int64_t ny
  * the final field to u_out (both nx*ny*nz, x fastest).  u0 and u_out may
  * alias.  Returns 0, or -1 on a bad argument, -2 when memory runs out.
  */
+int oracle_heat_run_timed(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_steps,
+                          const double* u0, double* u_out, int32_t nthreads, double* loop_seconds);
+
 int oracle_heat_run(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_steps,
                     const double* u0, double* u_out, int32_t nthreads)
+{
+    return oracle_heat_run_timed(nx, ny, nz, r, n_steps, u0, u_out, nthreads, NULL);
+}
+
+static double now_seconds(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* As oracle_heat_run; if loop_seconds is not NULL it receives the wall time
+ * of the step loop alone (no allocation or copies), as the paper times only
+ * its time-stepping loop (Algorithm "1-GPU Baseline"). */
+int oracle_heat_run_timed(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_steps,
+                          const double* u0, double* u_out, int32_t nthreads, double* loop_seconds)
 {
     if (nx < 1 || ny < 1 || nz < 1 || n_steps < 0 || !u0 || !u_out) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -92,10 +112,12 @@ int oracle_heat_run(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_step
             memcpy(b + pad_index(1, j + 1, k + 1, nx, ny), row, sizeof(double) * nx);
         }
 
+    const double t0 = now_seconds();
     for (int64_t m = 0; m < n_steps; ++m) {
         heat_one_step(a, b, nx, ny, nz, r, nthreads);
         double* t = a; a = b; b = t;   /* pointer swap, no data movement */
     }
+    if (loop_seconds) *loop_seconds = now_seconds() - t0;
 
     for (int64_t k = 0; k < nz; ++k)
         for (int64_t j = 0; j < ny; ++j)

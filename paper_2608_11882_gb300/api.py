@@ -1,0 +1,197 @@
+"""Convenience classes over the C ABI: Heat (a resident field), Operator and
+CG.  They take numpy arrays (host) or torch tensors (host or device) and pass
+raw pointers and the current torch CUDA stream to libheatcg.so.  Torch is used
+for device memory and streams only; no arithmetic of the method runs here."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native as native
+from ._native import (HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_F32, HS_F64, HS_OP_CSR,
+                      HS_OP_STENCIL7, HS_SCHED_FULL, HeatCGError)
+
+__all__ = ["Heat", "Operator", "CG", "native", "HeatCGError", "HS_F64", "HS_F32",
+           "HS_ALLOW_UNSTABLE", "HS_EXACT_ROUNDING", "HS_SCHED_FULL", "HS_OP_STENCIL7", "HS_OP_CSR"]
+
+_DTYPES = {"f64": (HS_F64, np.float64), "f32": (HS_F32, np.float32)}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _buffer(arr, np_dtype, count: int):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor of count elements."""
+    if isinstance(arr, np.ndarray):
+        if arr.dtype != np_dtype or not arr.flags["C_CONTIGUOUS"] or arr.size != count:
+            raise ValueError(f"expected a C-contiguous {np.dtype(np_dtype).name} array of {count} elements")
+        return arr.ctypes.data, False, arr
+    torch = _torch()
+    if isinstance(arr, torch.Tensor):
+        want = torch.float64 if np_dtype == np.float64 else torch.float32
+        if arr.dtype != want or not arr.is_contiguous() or arr.numel() != count:
+            raise ValueError(f"expected a contiguous {want} tensor of {count} elements")
+        return arr.data_ptr(), bool(arr.is_cuda), arr
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class Heat:
+    """A resident heat field (heat_create / heat_upload / heat_step / heat_read)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
+                 stream=None):
+        self.shape = (nz, ny, nx)
+        self.dtype_code, self.np_dtype = _DTYPES[dtype]
+        self.stream = _stream_handle(stream)
+        desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,
+                                   reserved0=0, stream=self.stream)
+        self.handle = native.heat_create(desc)
+
+    @property
+    def count(self) -> int:
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    def upload(self, u) -> "Heat":
+        ptr, dev, keep = _buffer(u, self.np_dtype, self.count)
+        native.heat_upload(self.handle, ptr, dev)
+        self._keep = keep   # the copy may still be in flight on the stream
+        return self
+
+    def step(self, n_steps: int) -> "Heat":
+        native.heat_step(self.handle, n_steps)
+        return self
+
+    def interior(self):
+        native.heat_interior(self.handle)
+
+    def boundary(self):
+        native.heat_boundary(self.handle)
+
+    def swap(self):
+        native.heat_swap(self.handle)
+
+    def read(self, out=None):
+        """Interior field as a new numpy array (nz, ny, nx), or into ``out``
+        (numpy array or torch tensor, host or device)."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.np_dtype)
+        ptr, dev, _ = _buffer(out, self.np_dtype, self.count)
+        native.heat_read(self.handle, ptr, dev)
+        return out
+
+    @property
+    def steps_done(self) -> int:
+        return native.heat_steps_done(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.heat_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """The CG operator: matrix-free 7-point stencil or CSR arrays (torch CUDA
+    tensors, or numpy arrays that cg_create copies to the device)."""
+
+    def __init__(self, op: native.hs_op, keep=()):
+        self.op = op
+        self._keep = keep
+
+    @classmethod
+    def stencil(cls, nx: int, ny: int, nz: int) -> "Operator":
+        return cls(native.hs_op(kind=HS_OP_STENCIL7, nx=nx, ny=ny, nz=nz, n=nx * ny * nz, nnz=0,
+                                dtype=HS_F64, host=0))
+
+    @classmethod
+    def csr(cls, rowptr, col, val) -> "Operator":
+        n = len(rowptr) - 1
+        nnz = len(col)
+        if isinstance(rowptr, np.ndarray):
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            ptrs, host = (rowptr.ctypes.data, col.ctypes.data, val.ctypes.data), 1
+        else:
+            torch = _torch()
+            if rowptr.dtype != torch.int32 or col.dtype != torch.int32 or val.dtype != torch.float64:
+                raise ValueError("CSR tensors must be int32, int32, float64")
+            ptrs, host = (rowptr.data_ptr(), col.data_ptr(), val.data_ptr()), 0 if rowptr.is_cuda else 1
+        op = native.hs_op(kind=HS_OP_CSR, nx=0, ny=0, nz=0, n=n, nnz=nnz, rowptr=ptrs[0], col=ptrs[1],
+                          val=ptrs[2], dtype=HS_F64, host=host)
+        return cls(op, (rowptr, col, val))
+
+    @property
+    def n(self) -> int:
+        return int(self.op.n)
+
+    def apply(self, p, y, stream=None):
+        """y = A p for torch CUDA tensors of n float64 values."""
+        pp, pd, _ = _buffer(p, np.float64, self.n)
+        yp, yd, _ = _buffer(y, np.float64, self.n)
+        if not (pd and yd):
+            raise ValueError("op_apply takes device tensors")
+        native.op_apply(self.op, pp, yp, _stream_handle(stream))
+        return y
+
+
+class CG:
+    """A CG context with resident workspace (cg_create / cg_run / cg_destroy)."""
+
+    def __init__(self, op: Operator, stream=None):
+        self.op = op
+        self.stream = _stream_handle(stream)
+        self.handle = native.cg_create(op.op, self.stream)
+
+    def run(self, b, x=None, rtol: float = 1e-8, max_iter: int = 10000):
+        """Solve A x = b.  b and x are numpy arrays (host path: the library
+        copies them) or torch CUDA tensors.  x (if given) is the start vector
+        and receives the solution.  Returns (x, info dict)."""
+        n = self.op.n
+        if x is None:
+            if isinstance(b, np.ndarray):
+                x = np.zeros(n)
+            else:
+                x = _torch().zeros(n, dtype=_torch().float64, device=b.device)
+        bp, bd, _ = _buffer(b, np.float64, n)
+        xp, xd, _ = _buffer(x, np.float64, n)
+        if bd != xd:
+            raise ValueError("b and x must both be host or both be device buffers")
+        rc, info = native.cg_run(self.handle, bp, xp, not bd, rtol, max_iter)
+        return x, {"iters": info.iters, "status": info.status, "relres_recur": info.relres_recur,
+                   "relres_true": info.relres_true, "converged": rc == native.HS_OK}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.cg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

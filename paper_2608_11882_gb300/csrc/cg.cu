@@ -1,0 +1,535 @@
+// Conjugate gradients on the 7-point Dirichlet Laplacian (Section 7.5):
+// SpMV fused with the p.q dot product, the x/r update fused with r.r, the
+// p update, deterministic grid reductions, and the cg_* / op_apply entry
+// points of the C ABI.
+//
+// CG in the textbook form (unpreconditioned, FP64):
+//     r0 = b - A x0, p0 = r0, rho0 = r0.r0
+//     q = A p;  alpha = rho / p.q;  x += alpha p;  r -= alpha q;  rho' = r.r
+//     stop when sqrt(rho') / ||b|| <= rtol, else p = r + (rho'/rho) p.
+//
+// Reductions: every block writes one partial sum; the last block to finish
+// (a ticket counter) adds the partials in index order with a fixed tree, and
+// updates the device scalars (alpha, beta, rho, the stop flag).  The grid size
+// depends only on n, so results repeat bit for bit from run to run.  Kernels
+// read the stop flag on entry and return at once after convergence, so the
+// host can enqueue several iterations between convergence checks without the
+// extra ones changing anything.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace hcg {
+
+struct CgScalars {
+    double rho;        // r.r of the current residual
+    double pq;         // p.q
+    double alpha;
+    double beta;
+    double bnorm;      // ||b||
+    double rtol;
+    double relres;     // sqrt(rho)/||b|| at the last check
+    double rr_true;    // ||b - A x||^2 at exit
+    int32_t done;      // 1: converged (or nothing to do); 2: breakdown (p.q <= 0)
+    int32_t iters;
+    uint32_t ticket;   // blocks finished in the running reduction
+    int32_t zero_rhs;  // ||b|| == 0
+};
+
+constexpr int kCgBlock = 256;
+
+struct OpDev {
+    int32_t kind;
+    int32_t nx, ny, nz;
+    int64_t n;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+};
+
+// (A p)[row] for the matrix-free 7-point operator: 6 p - sum of the interior
+// face neighbours; missing neighbours (outside the box) are Dirichlet zeros.
+__device__ __forceinline__ double apply_stencil_row(const OpDev& A, const double* __restrict__ p,
+                                                    int64_t row)
+{
+    const int nx = A.nx, ny = A.ny;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int i = (int)(row % nx);
+    const int64_t jk = row / nx;
+    const int j = (int)(jk % ny);
+    const int k = (int)(jk / ny);
+    const double zm = k > 0 ? __ldg(p + row - sxy) : 0.0;
+    const double ym = j > 0 ? __ldg(p + row - nx) : 0.0;
+    const double xm = i > 0 ? __ldg(p + row - 1) : 0.0;
+    const double xp = i < nx - 1 ? __ldg(p + row + 1) : 0.0;
+    const double yp = j < ny - 1 ? __ldg(p + row + nx) : 0.0;
+    const double zp = k < A.nz - 1 ? __ldg(p + row + sxy) : 0.0;
+    const double s = ((zm + ym) + (xm + xp)) + (yp + zp);
+    return __fma_rn(6.0, __ldg(p + row), -s);
+}
+
+// (A p)[row] for CSR: the row loop of Algorithm "spmv" (b), accumulated with FMA.
+__device__ __forceinline__ double apply_csr_row(const OpDev& A, const double* __restrict__ p,
+                                                int64_t row)
+{
+    double s = 0.0;
+    const int e = __ldg(A.rowptr + row + 1);
+    for (int t = __ldg(A.rowptr + row); t < e; ++t)
+        s = __fma_rn(__ldg(A.val + t), __ldg(p + __ldg(A.col + t)), s);
+    return s;
+}
+
+template <int KIND>
+__device__ __forceinline__ double apply_row(const OpDev& A, const double* __restrict__ p,
+                                            int64_t row)
+{
+    if (KIND == HS_OP_STENCIL7) return apply_stencil_row(A, p, row);
+    return apply_csr_row(A, p, row);
+}
+
+// Writes this block's partial and returns true in every thread of the last
+// block to finish, after which partials[0..gridDim.x) are all visible.
+__device__ __forceinline__ bool arrive_last(double block_total, double* partials,
+                                            uint32_t* ticket)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = block_total;
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Sum of partials[0..m) in a fixed order by the whole block; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* partials, int m, double* sh)
+{
+    double v = 0.0;
+    for (int t = threadIdx.x; t < m; t += kCgBlock) v += __ldcg(partials + t);
+    return block_sum<kCgBlock>(v, sh);
+}
+
+// y = A p (no reduction).
+template <int KIND>
+__global__ void __launch_bounds__(kCgBlock)
+    k_apply(OpDev A, const double* __restrict__ p, double* __restrict__ y)
+{
+    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
+         row += (int64_t)gridDim.x * kCgBlock)
+        y[row] = apply_row<KIND>(A, p, row);
+}
+
+// r = b - q, p = r; rho = r.r, ||b||; decides whether x0 already meets rtol.
+__global__ void __launch_bounds__(kCgBlock)
+    k_cg_start(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
+               double* __restrict__ r, double* __restrict__ p, double* partials, CgScalars* S)
+{
+    __shared__ double sh[kCgBlock / 32];
+    double rr = 0.0, bb = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock) {
+        const double bt = b[t];
+        const double rt = bt - q[t];
+        r[t] = rt;
+        p[t] = rt;
+        rr = __fma_rn(rt, rt, rr);
+        bb = __fma_rn(bt, bt, bb);
+    }
+    const double rr_blk = block_sum<kCgBlock>(rr, sh);
+    const double bb_blk = block_sum<kCgBlock>(bb, sh);
+    // two partial arrays: [0, G) for r.r and [G, 2G) for b.b
+    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = bb_blk;
+    if (!arrive_last(rr_blk, partials, &S->ticket)) return;
+    const double rho = sum_partials(partials, gridDim.x, sh);
+    const double bnorm2 = sum_partials(partials + gridDim.x, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->rho = rho;
+        S->bnorm = sqrt(bnorm2);
+        S->iters = 0;
+        S->zero_rhs = (bnorm2 == 0.0);
+        if (bnorm2 == 0.0) {
+            S->relres = 0.0;
+            S->done = 1;
+        } else {
+            S->relres = sqrt(rho) / S->bnorm;
+            S->done = (S->relres <= S->rtol) ? 1 : 0;
+        }
+    }
+}
+
+// q = A p fused with p.q; the last block forms alpha = rho / p.q.
+template <int KIND>
+__global__ void __launch_bounds__(kCgBlock)
+    k_cg_spmv_dot(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
+                  CgScalars* S)
+{
+    if (*(volatile int32_t*)&S->done) return;
+    __shared__ double sh[kCgBlock / 32];
+    double pq = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
+         row += (int64_t)gridDim.x * kCgBlock) {
+        const double qv = apply_row<KIND>(A, p, row);
+        q[row] = qv;
+        pq = __fma_rn(__ldg(p + row), qv, pq);
+    }
+    const double blk = block_sum<kCgBlock>(pq, sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double tot = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->pq = tot;
+        if (!(tot > 0.0)) {
+            S->done = 2;   // breakdown: A is not positive definite on p
+        } else {
+            S->alpha = S->rho / tot;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q fused with r.r; the last block tests convergence
+// and forms beta.
+__global__ void __launch_bounds__(kCgBlock)
+    k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                const double* __restrict__ p, const double* __restrict__ q, double* partials,
+                CgScalars* S)
+{
+    if (*(volatile int32_t*)&S->done) return;
+    __shared__ double sh[kCgBlock / 32];
+    const double alpha = S->alpha;
+    double rr = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock) {
+        x[t] = __fma_rn(alpha, p[t], x[t]);
+        const double rt = __fma_rn(-alpha, q[t], r[t]);
+        r[t] = rt;
+        rr = __fma_rn(rt, rt, rr);
+    }
+    const double blk = block_sum<kCgBlock>(rr, sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double rho_new = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->iters += 1;
+        S->relres = sqrt(rho_new) / S->bnorm;
+        if (S->relres <= S->rtol) {
+            S->done = 1;
+        } else {
+            S->beta = rho_new / S->rho;
+        }
+        S->rho = rho_new;
+    }
+}
+
+// p = r + beta p.
+__global__ void __launch_bounds__(kCgBlock)
+    k_cg_pupdate(int64_t n, const double* __restrict__ r, double* __restrict__ p, CgScalars* S)
+{
+    if (*(volatile int32_t*)&S->done) return;
+    const double beta = S->beta;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock)
+        p[t] = __fma_rn(beta, p[t], r[t]);
+}
+
+// ||b - q||^2 into S->rr_true (q = A x).
+__global__ void __launch_bounds__(kCgBlock)
+    k_resid_norm(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
+                 double* partials, CgScalars* S)
+{
+    __shared__ double sh[kCgBlock / 32];
+    double rr = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock) {
+        const double d = b[t] - q[t];
+        rr = __fma_rn(d, d, rr);
+    }
+    const double blk = block_sum<kCgBlock>(rr, sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double tot = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->rr_true = tot;
+    }
+}
+
+}  // namespace hcg
+
+using namespace hcg;
+
+struct hs_cg {
+    OpDev A;
+    cudaStream_t stream;
+    int grid;
+    double* r;
+    double* p;
+    double* q;
+    double* partials;      // 2 * grid doubles
+    CgScalars* S;          // device scalars
+    CgScalars* S_host;     // pinned mirror
+    void* owned[3];        // device copies of host CSR arrays
+    double* bx_dev[2];     // device staging of host b and x (allocated on demand)
+    int64_t staged_n;
+};
+
+namespace {
+
+int check_op(const hs_op* A)
+{
+    if (!A) return fail(HS_EINVAL, "cg: operator is NULL");
+    if (A->dtype != HS_F64) return fail(HS_EINVAL, "cg: operator dtype must be HS_F64");
+    if (A->kind == HS_OP_STENCIL7) {
+        if (A->nx < 1 || A->ny < 1 || A->nz < 1)
+            return fail(HS_EINVAL, "cg: stencil grid %d x %d x %d invalid", A->nx, A->ny, A->nz);
+        const int64_t n = (int64_t)A->nx * A->ny * A->nz;
+        if (A->n != 0 && A->n != n) return fail(HS_EINVAL, "cg: n does not match nx*ny*nz");
+        return HS_OK;
+    }
+    if (A->kind == HS_OP_CSR) {
+        if (A->n < 1 || A->n >= ((int64_t)1 << 31)) return fail(HS_EINVAL, "cg: CSR n out of range");
+        if (A->nnz < 0 || A->nnz >= ((int64_t)1 << 31))
+            return fail(HS_EINVAL, "cg: CSR nnz out of range for int32 indices");
+        if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val)))
+            return fail(HS_EINVAL, "cg: CSR arrays missing");
+        return HS_OK;
+    }
+    return fail(HS_EINVAL, "cg: unknown operator kind %d", A->kind);
+}
+
+OpDev to_dev(const hs_op* A)
+{
+    OpDev d;
+    d.kind = A->kind;
+    d.nx = A->nx;
+    d.ny = A->ny;
+    d.nz = A->nz;
+    d.n = A->kind == HS_OP_STENCIL7 ? (int64_t)A->nx * A->ny * A->nz : A->n;
+    d.rowptr = A->rowptr;
+    d.col = A->col;
+    d.val = (const double*)A->val;
+    return d;
+}
+
+int grid_for(int64_t n)
+{
+    int64_t g = (n + kCgBlock - 1) / kCgBlock;
+    const int64_t cap = (int64_t)kNumSMs * 8;   // 8 blocks of 256 threads fill an SM
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+int launch_apply(const OpDev& A, const double* p, double* y, cudaStream_t s)
+{
+    const int g = grid_for(A.n);
+    if (A.kind == HS_OP_STENCIL7)
+        k_apply<HS_OP_STENCIL7><<<g, kCgBlock, 0, s>>>(A, p, y);
+    else
+        k_apply<HS_OP_CSR><<<g, kCgBlock, 0, s>>>(A, p, y);
+    HS_CHECK_LAUNCH("cg: operator kernel");
+    return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int op_apply(const hs_op* A, const void* p, void* y, void* stream)
+{
+    int rc = check_op(A);
+    if (rc != HS_OK) return rc;
+    if (A->host) return fail(HS_EINVAL, "op_apply: operator arrays must be device memory");
+    if (!p || !y) return fail(HS_EINVAL, "op_apply: NULL vector");
+    return launch_apply(to_dev(A), (const double*)p, (double*)y, (cudaStream_t)stream);
+}
+
+int cg_destroy(hs_cg_t c)
+{
+    if (!c) return HS_OK;
+    int rc = HS_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cg_destroy: stream synchronize");
+    cudaFree(c->r);
+    cudaFree(c->p);
+    cudaFree(c->q);
+    cudaFree(c->partials);
+    cudaFree(c->S);
+    if (c->S_host) cudaFreeHost(c->S_host);
+    for (void* o : c->owned) cudaFree(o);
+    cudaFree(c->bx_dev[0]);
+    cudaFree(c->bx_dev[1]);
+    delete c;
+    return rc;
+}
+
+int cg_create(hs_cg_t* out, const hs_op* A, void* stream)
+{
+    if (!out) return fail(HS_EINVAL, "cg_create: out is NULL");
+    *out = nullptr;
+    int rc = check_op(A);
+    if (rc != HS_OK) return rc;
+    hs_cg* c = new (std::nothrow) hs_cg();
+    if (!c) return fail(HS_ENOMEM, "cg_create: host allocation failed");
+    c->stream = (cudaStream_t)stream;
+    c->A = to_dev(A);
+    const int64_t n = c->A.n;
+    c->grid = grid_for(n);
+#define CG_ALLOC(ptr, bytes)                                                 \
+    do {                                                                     \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                \
+        if (e_ != cudaSuccess) {                                             \
+            rc = cuda_fail(e_, "cg_create: cudaMalloc");                     \
+            cg_destroy(c);                                                   \
+            return rc;                                                       \
+        }                                                                    \
+    } while (0)
+    CG_ALLOC(c->r, sizeof(double) * n);
+    CG_ALLOC(c->p, sizeof(double) * n);
+    CG_ALLOC(c->q, sizeof(double) * n);
+    CG_ALLOC(c->partials, sizeof(double) * 2 * c->grid);
+    CG_ALLOC(c->S, sizeof(CgScalars));
+    {
+        cudaError_t e = cudaMallocHost((void**)&c->S_host, sizeof(CgScalars));
+        if (e != cudaSuccess) {
+            c->S_host = nullptr;
+            rc = cuda_fail(e, "cg_create: cudaMallocHost");
+            cg_destroy(c);
+            return rc;
+        }
+    }
+    if (A->kind == HS_OP_CSR && A->host) {
+        const size_t bytes[3] = {sizeof(int32_t) * (size_t)(n + 1), sizeof(int32_t) * (size_t)A->nnz,
+                                 sizeof(double) * (size_t)A->nnz};
+        const void* src[3] = {A->rowptr, A->col, A->val};
+        for (int t = 0; t < 3; ++t) {
+            CG_ALLOC(c->owned[t], bytes[t] ? bytes[t] : 1);
+            if (bytes[t]) {
+                cudaError_t e = cudaMemcpyAsync(c->owned[t], src[t], bytes[t],
+                                                cudaMemcpyHostToDevice, c->stream);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "cg_create: copy of CSR arrays");
+                    cg_destroy(c);
+                    return rc;
+                }
+            }
+        }
+        c->A.rowptr = (const int32_t*)c->owned[0];
+        c->A.col = (const int32_t*)c->owned[1];
+        c->A.val = (const double*)c->owned[2];
+    }
+#undef CG_ALLOC
+    cudaError_t e = cudaMemsetAsync(c->S, 0, sizeof(CgScalars), c->stream);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "cg_create: memset");
+        cg_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HS_OK;
+}
+
+int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double rtol,
+           int32_t max_iter, hs_cg_info* info)
+{
+    if (!c || !b_in || !x_inout) return fail(HS_EINVAL, "cg_run: NULL argument");
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) return fail(HS_EINVAL, "cg_run: rtol must be finite and >= 0");
+    if (max_iter < 0) return fail(HS_EINVAL, "cg_run: max_iter < 0");
+    const int64_t n = c->A.n;
+    const size_t vbytes = sizeof(double) * (size_t)n;
+    const double* b = (const double*)b_in;
+    double* x = (double*)x_inout;
+    if (host_buffers) {
+        for (int t = 0; t < 2; ++t)
+            if (!c->bx_dev[t]) HS_TRY_CUDA(cudaMalloc((void**)&c->bx_dev[t], vbytes), "cg_run: staging buffer");
+        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[0], b_in, vbytes, cudaMemcpyHostToDevice, c->stream),
+                    "cg_run: copy of b");
+        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[1], x_inout, vbytes, cudaMemcpyHostToDevice, c->stream),
+                    "cg_run: copy of x0");
+        b = c->bx_dev[0];
+        x = c->bx_dev[1];
+    }
+    // device scalars: rtol, cleared flags
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    init.rtol = rtol;
+    *c->S_host = init;
+    HS_TRY_CUDA(cudaMemcpyAsync(c->S, c->S_host, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream),
+                "cg_run: scalar init");
+    int rc = launch_apply(c->A, x, c->q, c->stream);   // q = A x0
+    if (rc != HS_OK) return rc;
+    k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S);
+    HS_CHECK_LAUNCH("cg: start kernel");
+
+    // Iterate in chunks, reading the stop flag and count between chunks.
+    int32_t enqueued = 0;
+    int chunk = 4;
+    for (;;) {
+        HS_TRY_CUDA(cudaMemcpyAsync(c->S_host, c->S, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream),
+                    "cg_run: scalar readback");
+        HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
+        if (c->S_host->done || enqueued >= max_iter) break;
+        const int32_t todo = (max_iter - enqueued < chunk) ? max_iter - enqueued : chunk;
+        for (int32_t t = 0; t < todo; ++t) {
+            // x lives either in the caller's buffer or in the staging buffer
+            const int64_t nn = n;
+            if (c->A.kind == HS_OP_STENCIL7)
+                k_cg_spmv_dot<HS_OP_STENCIL7><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q,
+                                                                                   c->partials, c->S);
+            else
+                k_cg_spmv_dot<HS_OP_CSR><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q,
+                                                                              c->partials, c->S);
+            HS_CHECK_LAUNCH("cg: spmv+dot kernel");
+            k_cg_update<<<c->grid, kCgBlock, 0, c->stream>>>(nn, x, c->r, c->p, c->q, c->partials, c->S);
+            HS_CHECK_LAUNCH("cg: update kernel");
+            k_cg_pupdate<<<c->grid, kCgBlock, 0, c->stream>>>(nn, c->r, c->p, c->S);
+            HS_CHECK_LAUNCH("cg: p update kernel");
+        }
+        enqueued += todo;
+        if (chunk < 32) chunk *= 2;
+    }
+    const CgScalars s = *c->S_host;
+    if (s.zero_rhs) HS_TRY_CUDA(cudaMemsetAsync(x, 0, vbytes, c->stream), "cg_run: zero solution");
+    // true residual ||b - A x|| / ||b||
+    rc = launch_apply(c->A, x, c->q, c->stream);
+    if (rc != HS_OK) return rc;
+    k_resid_norm<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->partials, c->S);
+    HS_CHECK_LAUNCH("cg: residual norm kernel");
+    HS_TRY_CUDA(cudaMemcpyAsync(c->S_host, c->S, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream),
+                "cg_run: scalar readback");
+    if (host_buffers)
+        HS_TRY_CUDA(cudaMemcpyAsync(x_inout, x, vbytes, cudaMemcpyDeviceToHost, c->stream),
+                    "cg_run: copy of x");
+    HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
+    const CgScalars f = *c->S_host;
+    const bool converged = (f.done == 1);
+    if (f.done == 2) return fail(HS_ECUDA, "cg_run: breakdown, p.q <= 0 (operator not positive definite?)");
+    if (info) {
+        info->iters = f.iters;
+        info->relres_recur = f.relres;
+        info->relres_true = f.zero_rhs ? 0.0 : sqrt(f.rr_true) / f.bnorm;
+        info->status = converged ? HS_OK : HS_ENOCONV;
+    }
+    if (!converged) {
+        set_error("cg_run: no convergence to rtol %g within %d iterations (relres %g)", rtol,
+                  max_iter, f.relres);
+        return HS_ENOCONV;
+    }
+    return HS_OK;
+}
+
+int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
+             hs_cg_info* info, void* stream)
+{
+    if (A && A->host) return fail(HS_EINVAL, "cg_solve: operator arrays must be device memory");
+    hs_cg_t c = nullptr;
+    int rc = cg_create(&c, A, stream);
+    if (rc != HS_OK) return rc;
+    rc = cg_run(c, b, x, 0, rtol, max_iter, info);
+    const int rc2 = cg_destroy(c);
+    return rc != HS_OK ? rc : rc2;
+}
+
+}  // extern "C"

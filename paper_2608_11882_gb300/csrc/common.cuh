@@ -1,0 +1,68 @@
+// Shared host/device helpers of the heat + CG library (status handling,
+// launch accounting, deterministic block reductions).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "heatcg.h"
+
+namespace hcg {
+
+// Records a printf-style message as the calling thread's last error.
+void set_error(const char* fmt, ...);
+// Records a failed CUDA call and maps it to HS_ENOMEM or HS_ECUDA.
+int cuda_fail(cudaError_t e, const char* what);
+// Returns code after recording msg (for argument errors).
+int fail(int code, const char* fmt, ...);
+
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace hcg
+
+#define HS_TRY_CUDA(call, what)                                          \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::hcg::cuda_fail(e_, what);        \
+    } while (0)
+
+// Checks the launch just issued and counts it.
+#define HS_CHECK_LAUNCH(what)                                            \
+    do {                                                                 \
+        cudaError_t e_ = cudaPeekAtLastError();                          \
+        if (e_ != cudaSuccess) {                                         \
+            (void)cudaGetLastError();                                    \
+            return ::hcg::cuda_fail(e_, what);                           \
+        }                                                                \
+        ::hcg::count_launch();                                           \
+    } while (0)
+
+namespace hcg {
+
+constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
+
+// Sum of v over a block of BLOCK threads, in a fixed order (warp shuffles,
+// then warp 0 over the per-warp sums).  The result is valid in thread 0.
+// sh must hold BLOCK/32 doubles.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = 0.0;
+    if (warp == 0) {
+        v = (lane < BLOCK / 32) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+}  // namespace hcg

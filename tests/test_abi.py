@@ -1,0 +1,49 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/heatcg.h declares; the binding mirrors the
+header's structs.  No compute call is made (no GPU here)."""
+import ctypes
+import re
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def declared_functions():
+    text = (ROOT / "include" / "heatcg.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2608_11882_gb300.build import build
+    lib = ctypes.CDLL(str(build()))
+    names = declared_functions()
+    assert "heat_create" in names and "cg_solve" in names and "heat_interior" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_struct_sizes_match_header_layout():
+    from paper_2608_11882_gb300 import _native as nat
+    # hs_heat_desc: 3*int32 + pad, double, uint32, int32, int32 + pad, void*
+    assert ctypes.sizeof(nat.hs_heat_desc) == 48
+    assert ctypes.sizeof(nat.hs_op) == 64
+    assert ctypes.sizeof(nat.hs_cg_info) == 24
+
+
+def test_version_and_error_string_without_gpu():
+    from paper_2608_11882_gb300 import _native as nat
+    assert nat.lib.hs_version() >= 100
+    assert isinstance(nat.last_error(), str)
+    # argument validation happens before any CUDA call
+    desc = nat.hs_heat_desc(nx=0, ny=1, nz=1, r=0.1, flags=0, dtype=0, reserved0=0, stream=None)
+    h = ctypes.c_void_p()
+    assert nat.lib.heat_create(ctypes.byref(h), ctypes.byref(desc)) == nat.HS_EINVAL
+    assert "interior" in nat.last_error()
+    desc = nat.hs_heat_desc(nx=4, ny=4, nz=4, r=0.2, flags=0, dtype=0, reserved0=0, stream=None)
+    assert nat.lib.heat_create(ctypes.byref(h), ctypes.byref(desc)) == nat.HS_EUNSTABLE
+    size = ctypes.c_size_t()
+    desc.r = 0.1
+    assert nat.lib.heat_device_bytes(ctypes.byref(desc), ctypes.byref(size)) == 0
+    # 2 buffers x 6 planes x 6 rows x 16-element (128-byte) rows of doubles
+    assert size.value == 2 * 6 * 6 * 16 * 8
