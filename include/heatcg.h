@@ -183,6 +183,33 @@ int cg_destroy(hs_cg_t c);
 int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
              hs_cg_info* info, void* stream);
 
+/* ---- allocation-free CG (the paper has no counterpart) ------------------- */
+/* Largest system cg_solve_noalloc accepts: 2,097,152 unknowns (a 128^3 grid). */
+#define HS_NOALLOC_MAX_N 2097152
+
+/* cg_solve for callers that cannot allocate memory while they solve -- for
+ * example a serving loop that reserved its device memory up front and must
+ * not let cudaMalloc/cudaFree synchronise the device under its other streams,
+ * or code running under another framework's memory manager or fixed budget.
+ * Same arguments, same kernels and the same results as cg_solve; it calls no
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.  The
+ * solver's scratch (r, p, q, reduction partials, device scalars) lives in one
+ * fixed array of about 50 MB inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   - A's arrays, b and x must be device memory (A->host == 0).
+ *   - n > HS_NOALLOC_MAX_N is rejected with HS_EINVAL before any work.
+ *   - The first call on a device does a one-time set-up on that device (it
+ *     looks up the scratch array's device address); make that first call
+ *     before any stream capture.
+ *   - Every call, on any stream, uses the same scratch array.  Calls whose
+ *     work overlaps on the GPU race and corrupt each other's results:
+ *     serialise them (one stream, or events between streams).  Each call
+ *     clears what must start at zero, so it does not depend on what an
+ *     earlier call left behind.
+ *   - Synchronises the stream.  Returns HS_OK, HS_ENOCONV, or an error code. */
+int cg_solve_noalloc(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
+                     hs_cg_info* info, void* stream);
+
 /* ---- misc ---------------------------------------------------------------- */
 /* Message describing the last error on the calling thread ("" if none). */
 const char* hs_last_error(void);

@@ -172,3 +172,23 @@ def cg_solve(op: hs_op, b_ptr: int, x_ptr: int, rtol: float, max_iter: int, stre
                       ctypes.byref(info), stream)
     check(rc, "cg_solve", ok=(HS_OK, HS_ENOCONV))
     return rc, info
+
+
+# ---- allocation-free CG (cg_solve_noalloc) ----------------------------------------
+HS_NOALLOC_MAX_N = 2097152
+lib.cg_solve_noalloc.argtypes = [ctypes.POINTER(hs_op), ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_double, ctypes.c_int32, ctypes.POINTER(hs_cg_info),
+                                 ctypes.c_void_p]
+lib.cg_solve_noalloc.restype = ctypes.c_int
+
+
+def cg_solve_noalloc(op: hs_op, b_ptr: int, x_ptr: int, rtol: float, max_iter: int,
+                     stream: int = 0):
+    """cg_solve without allocating: for callers that cannot allocate device
+    memory while they solve (scratch comes from a fixed array in the library;
+    at most HS_NOALLOC_MAX_N unknowns; overlapping calls race)."""
+    info = hs_cg_info()
+    rc = lib.cg_solve_noalloc(ctypes.byref(op), b_ptr, x_ptr, float(rtol), int(max_iter),
+                              ctypes.byref(info), stream)
+    check(rc, "cg_solve_noalloc", ok=(HS_OK, HS_ENOCONV))
+    return rc, info

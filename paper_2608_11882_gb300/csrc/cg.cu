@@ -17,6 +17,7 @@
 // extra ones changing anything.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -530,6 +531,86 @@ int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_it
     rc = cg_run(c, b, x, 0, rtol, max_iter, info);
     const int rc2 = cg_destroy(c);
     return rc != HS_OK ? rc : rc2;
+}
+
+}  // extern "C"
+
+// ---- allocation-free CG ---------------------------------------------------------
+// Some callers must not allocate while they solve: a serving loop that reserved
+// all of its device memory up front and cannot let cudaMalloc/cudaFree (which
+// may synchronise the whole device) stall the other streams it keeps busy;
+// code that runs under another framework's memory manager or inside one of its
+// allocation hooks, where a fresh allocation would fail, fragment the pool or
+// re-enter the allocator; processes held to a fixed device-memory budget.
+// cg_solve_noalloc serves them.  It runs exactly the kernels and host loop of
+// cg_run, with the solver's scratch (r, p, q, the reduction partials and the
+// device scalars) taken from one fixed array in the library's own device
+// memory instead of from cudaMalloc, and its scalar read-backs going through a
+// variable on the caller's stack instead of pinned memory.
+namespace hcg {
+
+constexpr int64_t kNoAllocMaxN = HS_NOALLOC_MAX_N;          // 2,097,152 unknowns = 128^3
+constexpr int64_t kNoAllocMaxGrid = (int64_t)kNumSMs * 8;   // the largest grid grid_for() picks
+constexpr size_t kNoAllocScalarDoubles = (sizeof(CgScalars) + sizeof(double) - 1) / sizeof(double);
+constexpr size_t kNoAllocDoubles =
+    3 * (size_t)kNoAllocMaxN + 2 * (size_t)kNoAllocMaxGrid + kNoAllocScalarDoubles;
+
+// About 50 MB.  Every GPU that loads this library holds it until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch per device (host code may not use the
+// symbol itself: on the host it names a stand-in, not device memory).
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[kNoAllocMaxDevices];
+
+}  // namespace hcg
+
+extern "C" {
+
+int cg_solve_noalloc(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
+                     hs_cg_info* info, void* stream)
+{
+    int rc = check_op(A);
+    if (rc != HS_OK) return rc;
+    if (A->host) return fail(HS_EINVAL, "cg_solve_noalloc: operator arrays must be device memory");
+    if (!b || !x) return fail(HS_EINVAL, "cg_solve_noalloc: NULL vector");
+    hs_cg c{};
+    c.A = to_dev(A);
+    if (c.A.n > kNoAllocMaxN)
+        return fail(HS_EINVAL, "cg_solve_noalloc: %lld unknowns exceed the fixed scratch of %lld",
+                    (long long)c.A.n, (long long)kNoAllocMaxN);
+    int dev = 0;
+    HS_TRY_CUDA(cudaGetDevice(&dev), "cg_solve_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(HS_EINVAL, "cg_solve_noalloc: device ordinal %d out of range", dev);
+    double* base = nullptr;
+    {
+        // Set-up, once per device, with that device current: look up where
+        // the scratch array lives on it.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cg_solve_noalloc: cudaGetSymbolAddress");
+            g_noalloc_addr[dev] = (double*)p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    c.stream = (cudaStream_t)stream;
+    c.grid = grid_for(c.A.n);
+    c.r = base;
+    c.p = base + kNoAllocMaxN;
+    c.q = base + 2 * kNoAllocMaxN;
+    c.partials = base + 3 * kNoAllocMaxN;
+    c.S = (CgScalars*)(c.partials + 2 * kNoAllocMaxGrid);
+    // cg_run clears the device scalars (stop flag, iteration count and the
+    // reduction ticket, which must start at zero) before the first kernel;
+    // r, p and q are written before they are read.  The copies through this
+    // pageable variable are synchronous and allocate nothing.
+    CgScalars host_scalars;
+    c.S_host = &host_scalars;
+    return cg_run(&c, b, x, 0, rtol, max_iter, info);
 }
 
 }  // extern "C"
