@@ -37,6 +37,14 @@ BYTES_PER_LUP_F64 = 16          # read u once, write u' once
 # FP64 issue peak derived from the nominal 1.25 TFLOP/s (FMA = 2 flops): 0.625e12 instr/s
 FP64_INSTR_PEAK_T = 0.625
 
+# heat arithmetic modes: Heat() keywords, the arithmetic type, algorithmic bytes per LUP,
+# and the roof that binds the Interior kernel
+HEAT_MODES = {
+    "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "alu"},
+    "fixed64": {"dtype": "f64", "flags": "HS_FIXED64", "arith": "int64", "bytes": 16, "bound": "hbm"},
+    "f32": {"dtype": "f32", "flags": "", "arith": "f32", "bytes": 8, "bound": "hbm"},
+}
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -51,6 +59,10 @@ def parse_args():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--heat-mode", choices=sorted(HEAT_MODES), default="f64",
+                    help="arithmetic of the timed heat segment")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the untimed one-solve runs of the other heat modes")
     return ap.parse_args()
 
 
@@ -120,6 +132,25 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.rows)}
+
+
+def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind):
+    """Roofline object of the Interior kernel from its mean launch time (ms)."""
+    spec = HEAT_MODES[mode_name]
+    lup = float(n) * n * max(n - 2, 0)
+    hbm_rate = lup * spec["bytes"] / (int_ms * 1e-3) / 1e9
+    name = {"f64": "k_heat_interior<double> (FP64, 7 instr/LUP)",
+            "fixed64": "k_heat_interior<long long> (64-bit fixed point)",
+            "f32": "k_heat_interior<float>"}[mode_name]
+    if spec["bound"] == "alu":
+        rate = lup * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": rate, "peak": FP64_INSTR_PEAK_T,
+                "unit": "T FP64-instr/s", "frac": rate / FP64_INSTR_PEAK_T, "traffic": None,
+                "hbm_achieved_gbs": hbm_rate, "hbm_peak_gbs": hbm_gbs, "hbm_frac": hbm_rate / hbm_gbs,
+                "hbm_peak_kind": peak_kind, "interior_ms_per_launch": int_ms}
+    return {"bound": "hbm", "kernel": name, "achieved": hbm_rate, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": hbm_rate / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
+            "bytes_per_lup": spec["bytes"], "interior_ms_per_launch": int_ms}
 
 
 # ---------------------------------------------------------------------------------
@@ -226,7 +257,17 @@ def run_ours(args):
     x_mf = torch.zeros(m ** 3, dtype=torch.float64, device="cuda")
     x_csr = torch.zeros_like(x_mf)
 
-    heat = pkg.Heat(n, n, n, args.r, dtype="f64", stream=stream)
+    def make_heat(mode):
+        spec = HEAT_MODES[mode]
+        flags = getattr(pkg, spec["flags"]) if spec["flags"] else 0
+        return pkg.Heat(n, n, n, args.r, dtype=spec["dtype"], flags=flags, stream=stream)
+
+    mode = HEAT_MODES[args.heat_mode]
+    heat = make_heat(args.heat_mode)
+    if mode["dtype"] == "f32":
+        u0_dev = u0_dev.float()
+        u0_host = u0_host.float().pin_memory()
+        u_out_dev = torch.empty_like(u0_dev)
     cg_mf = pkg.CG(pkg.Operator.stencil(m, m, m), stream=stream)
     cg_csr = pkg.CG(pkg.Operator.csr(*csr_dev), stream=stream)
     torch.cuda.synchronize()
@@ -296,17 +337,9 @@ def run_ours(args):
     value = world * lup_step * args.steps / (heat_ms * 1e-3) / 1e9
     hbm_gbs, peak_kind = measured_peaks()
 
-    # dominant kernel: the FP64 Interior kernel (ALU bound on GB300's FP64 pipe)
+    # dominant kernel: the Interior kernel of the timed heat mode
     int_ms = statistics.mean(interior_ms)
-    lup_interior = float(n) * n * max(n - 2, 0)
-    instr_rate = lup_interior * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
-    hbm_rate = lup_interior * BYTES_PER_LUP_F64 / (int_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_heat_interior<double> (FP64, 7 instr/LUP)",
-                "achieved": instr_rate, "peak": FP64_INSTR_PEAK_T, "unit": "T FP64-instr/s",
-                "frac": instr_rate / FP64_INSTR_PEAK_T, "traffic": None,
-                "hbm_achieved_gbs": hbm_rate, "hbm_peak_gbs": hbm_gbs,
-                "hbm_frac": hbm_rate / hbm_gbs, "hbm_peak_kind": peak_kind,
-                "interior_ms_per_launch": int_ms}
+    roofline = interior_roofline(args.heat_mode, n, int_ms, hbm_gbs, peak_kind)
 
     def pct(v, q):
         v = sorted(v)
@@ -317,8 +350,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"heat {n}^3 FP64 r={args.r} {hsteps} steps (u0 = 8 sine modes k in "
+        "scaling": "weak", "vs_baseline": None, "dtype": mode["arith"], "data": "synthetic",
+        "config": {"workload": f"heat {n}^3 {args.heat_mode} r={args.r} {hsteps} steps (u0 = 8 sine modes k in "
                                f"[1,16] + 1e-3 U[-1,1]) + CG {m}^3 FP64 7-pt Dirichlet Laplacian, "
                                f"matrix-free and CSR int32 (nnz {nnz}), b ~ N(0,1), rtol {args.rtol}",
                    "value_covers": "heat segment (upload + steps + device readback), device time",
@@ -362,10 +395,55 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_t = float(t[0])
         line["e2e"] = {"value": world * lup_step * args.steps / e2e_t / 1e9, "unit": "GLUP/s",
-                       "h2d_bytes_per_step": int(u0_host.numel() * 8),
-                       "d2h_bytes_per_step": int(u_back.numel() * 8),
+                       "h2d_bytes_per_step": int(u0_host.numel() * u0_host.element_size()),
+                       "d2h_bytes_per_step": int(u_back.numel() * u_back.element_size()),
                        "covers": "heat: heat_upload from pinned host, heat_step, heat_read to pinned host",
                        "cg_matrix_free_host_buffers_its_per_s": it_mf[-1] / statistics.median(e2e_cg)}
+
+    # ---- the other heat modes, one untimed-region solve each -------------------
+    if not args.no_side:
+        def solve_once(h, src):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            h.upload(src)
+            for s in range(hsteps):
+                h.boundary()
+                pairs[s][0].record(stream)
+                h.interior()
+                pairs[s][1].record(stream)
+                h.swap()
+            out = torch.empty_like(src)
+            h.read(out)
+            ev1.record(stream)
+            ev1.synchronize()
+            return ev0.elapsed_time(ev1), sum(a.elapsed_time(b) for a, b in pairs) / hsteps, out
+
+        fields = {args.heat_mode: u_out_dev}
+        side = {}
+        for name in ["f64"] + [k for k in sorted(HEAT_MODES) if k != "f64"]:
+            if name == args.heat_mode:
+                continue
+            spec = HEAT_MODES[name]
+            src = torch.from_numpy(u0_np).cuda()
+            if spec["dtype"] == "f32":
+                src = src.float()
+            h2 = make_heat(name)
+            seg_ms, ims, out = solve_once(h2, src)
+            h2.close()
+            fields[name] = out
+            side[name] = {"glups": lup_step / (seg_ms * 1e-3) / 1e9, "arith": spec["arith"],
+                          "roofline": interior_roofline(name, n, ims, hbm_gbs, peak_kind)}
+            del src
+        ref = fields["f64"].double()
+        refmax = float(ref.abs().max())
+        for name, f in fields.items():
+            if name == "f64":
+                continue
+            err = float((f.double() - ref).abs().max())
+            entry = side.setdefault(name, {"glups": value / world, "arith": HEAT_MODES[name]["arith"]})
+            entry["max_abs_diff_vs_f64_gpu"] = err
+            entry["max_rel_diff_vs_f64_gpu"] = err / refmax
+        line["heat_modes"] = side
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, host_cores())

@@ -66,6 +66,18 @@ extern "C" {
  * COMPUTE_SINGLE_GPU) instead of the Interior + Boundary pair (Algorithms
  * INTERIOR and BOUNDARY).  Results are bitwise identical either way. */
 #define HS_SCHED_FULL       0x4u
+/* HS_F64 only: keep the FP64 interface (upload and read are doubles) but hold
+ * the field as 64-bit fixed-point integers U = round(u 2^E), with E chosen at
+ * each upload from max|u0| so that 12 max|U| < 2^61.  Every step is exact
+ * integer arithmetic -- the neighbour sum and S - 6U exactly, r held as
+ * R = round(r 2^64) (exact for r >= 2^-11) -- with one rounding per point, of
+ * R (S - 6U) / 2^64 to the nearest integer.  Requires r <= 1/6 (the update is
+ * then a convex combination and |U| never grows, so nothing overflows);
+ * excludes HS_EXACT_ROUNDING and HS_ALLOW_UNSTABLE.  heat_read returns the
+ * nearest doubles; it reports HS_ERANGE if the uploaded field held NaN or Inf.
+ * Per step this costs integer instructions instead of FP64 ones, so on GPUs
+ * whose FP64 pipe is narrow it runs at memory speed. */
+#define HS_FIXED64          0x8u
 
 typedef struct hs_heat* hs_heat_t;
 

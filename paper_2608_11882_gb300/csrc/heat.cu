@@ -6,6 +6,25 @@
 //     u' = u + r * (((u[i-1] + u[i+1]) + (u[j-1] + u[j+1])) + (u[k-1] + u[k+1]) - 6 u)
 // on interior points; the boundary layer stays zero (Dirichlet).
 //
+// Arithmetic, chosen per handle:
+//   FP64      the update in double precision with two fused multiply-adds;
+//   FP64 exact one rounding per operation in the written order (no FMA), the
+//             oracle's rounding sequence bit for bit;
+//   FP32      the update in single precision (storage and arithmetic);
+//   FIXED64   FP64 interface, field held as 64-bit fixed-point integers
+//             U = round(u 2^E).  The six-neighbour sum and S - 6U are exact;
+//             r is held as R = r 2^64 (exactly for r >= 2^-11); the one rounding
+//             per point is of R (S - 6U) / 2^64 to the nearest integer.  E is set
+//             at upload from max|u0| so that 12 max|U| < 2^61, and grows during
+//             the run: every step's kernels track max|U| of their output, and
+//             when the field has shrunk the next step shifts all values left by
+//             k bits (exact), keeping max|U| in [2^56, 2^57) -- about 57
+//             significant bits relative to the current maximum.  For r <= 1/6
+//             the update is a convex combination, so |U| never grows and
+//             nothing overflows.  GB300's integer pipes run about 60x the rate
+//             of its FP64 pipe, which makes this the FP64-accuracy form that is
+//             bound by HBM rather than by FP64 issue.
+//
 // Layout in HBM: each field buffer holds (nz+2) planes of (ny+2) rows.  A row
 // has `pitch` elements (a multiple of 128 bytes); interior x = 0 sits at
 // element `lead` (32 bytes in), so interior rows start 32-byte aligned, and
@@ -15,6 +34,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <new>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -46,17 +66,77 @@ static HeatGeom make_geom(int nx, int ny, int nz, size_t elem)
     return g;
 }
 
+// Fixed-point bookkeeping of a FIXED64 field (device memory).  The field at
+// step m has scale E_m (U = round(u 2^E_m)) and integer max M_m = max|U|, kept
+// in slot m % 3.  The kernels of step m read slot m % 3, write slot (m+1) % 3
+// (atomic max of their outputs, and E_{m+1}) and clear slot (m+2) % 3, which no
+// kernel of step m reads -- so no kernel ever races on a slot.
+struct FxSlot {
+    unsigned long long maxU;   // max |U| of the field
+    int32_t E;                 // scale exponent of the field
+    int32_t pad;
+};
+
+struct FxState {
+    unsigned long long maxabs_bits;   // bit pattern of max|u0| (non-negative doubles order like integers)
+    int32_t nonfinite;                // 1 if the uploaded field held NaN or Inf
+    int32_t pad;
+    FxSlot slot[3];
+};
+
+// Left shift that keeps a shrinking field near full precision: the largest k
+// with M 2^k < 2^57, so |S - 6U| 2^k <= 12 M 2^k < 2^61 never overflows.
+__device__ __forceinline__ int fx_shift(const FxState* fx, int m3)
+{
+    const unsigned long long M = fx->slot[m3].maxU;
+    if (M == 0) return 0;
+    const int k = 57 - (64 - __clzll((long long)M));
+    return k > 0 ? k : 0;
+}
+
+__device__ __forceinline__ unsigned long long fx_abs(long long v)
+{
+    return v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+}
+
+// Block-wide max of the outputs into slot (m3+1) % 3; the grid leader also
+// records E_{m+1} = E_m + k and clears slot (m3+2) % 3 for the next step.
+template <int NT>
+__device__ __forceinline__ void fx_finish(unsigned long long m, FxState* fx, int m3, int k,
+                                          bool leader)
+{
+    __shared__ unsigned long long wmax[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < NT / 32; ++w) b = wmax[w] > b ? wmax[w] : b;
+        atomicMax(&fx->slot[(m3 + 1) % 3].maxU, b);
+        if (leader) {
+            fx->slot[(m3 + 1) % 3].E = fx->slot[m3].E + k;
+            fx->slot[(m3 + 2) % 3].maxU = 0;
+        }
+    }
+}
+
 // ---- the point update -------------------------------------------------------
-// Default: the six-neighbour sum in the written order, then two fused
-// multiply-adds: t = s - 6u, u' = u + r t (7 FP64 instructions per point).
-// Exact: one rounding per operation in the written order, no fusion.
+// k is the FIXED64 rescaling shift of this step (unused by the floating types).
 template <typename T, bool EXACT>
 struct Point;
 
 template <bool EXACT>
 struct Point<double, EXACT> {
+    // Default: the six-neighbour sum in the written order, then two fused
+    // multiply-adds t = s - 6u, u' = u + r t (7 FP64 instructions per point).
+    // Exact: one rounding per operation in the written order, no fusion.
     static __device__ __forceinline__ double update(double c, double xm, double xp, double ym,
-                                                    double yp, double zm, double zp, double r)
+                                                    double yp, double zm, double zp, double r, int)
     {
         const double s = __dadd_rn(__dadd_rn(__dadd_rn(xm, xp), __dadd_rn(ym, yp)),
                                    __dadd_rn(zm, zp));
@@ -68,7 +148,7 @@ struct Point<double, EXACT> {
 template <bool EXACT>
 struct Point<float, EXACT> {
     static __device__ __forceinline__ float update(float c, float xm, float xp, float ym, float yp,
-                                                   float zm, float zp, float r)
+                                                   float zm, float zp, float r, int)
     {
         const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)),
                                   __fadd_rn(zm, zp));
@@ -76,6 +156,28 @@ struct Point<float, EXACT> {
         return __fmaf_rn(r, __fmaf_rn(-6.0f, c, s), c);
     }
 };
+
+template <bool EXACT>
+struct Point<long long, EXACT> {
+    // FIXED64: R = r 2^64 (a non-negative int64: r <= 1/6 < 1/2).  S - 6U is
+    // exact; it and U are moved to the new scale by the exact shift k; then
+    // t R / 2^64 is rounded to nearest (ties up): floor((t R + 2^63) / 2^64)
+    // = high word of t R plus the top bit of its low word.
+    static __device__ __forceinline__ long long update(long long c, long long xm, long long xp,
+                                                       long long ym, long long yp, long long zm,
+                                                       long long zp, long long R, int k)
+    {
+        const long long s = ((xm + xp) + (ym + yp)) + (zm + zp);
+        const long long t = (long long)((unsigned long long)(s - 6 * c) << k);
+        const long long cs = (long long)((unsigned long long)c << k);
+        const long long hi = __mul64hi(t, R);
+        const unsigned long long lo = (unsigned long long)t * (unsigned long long)R;
+        return cs + hi + (long long)(lo >> 63);
+    }
+};
+
+template <typename T>
+constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
 // ---- Interior kernel ----------------------------------------------------------
 // One thread per (i, j) column marches up a chunk of k-planes, keeping the
@@ -87,27 +189,38 @@ constexpr int kBX = 32, kBY = 8;
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(kBX* kBY)
     k_heat_interior(const T* __restrict__ src, T* __restrict__ dst, HeatGeom g, T r, int kbeg,
-                    int kend, int kchunk)
+                    int kend, int kchunk, FxState* fx, int m3)
 {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
     const int k0 = kbeg + (int)blockIdx.z * kchunk;
     const int k1 = min(k0 + kchunk, kend);
-    if (k0 >= k1) return;
-    const int64_t P = g.plane, Y = g.pitch;
-    int64_t c = g.at(i, j, k0);
-    T below = __ldg(src + c - P);
-    T cur = __ldg(src + c);
-    for (int k = k0; k < k1; ++k) {
-        const T above = __ldg(src + c + P);
-        const T xm = __ldg(src + c - 1), xp = __ldg(src + c + 1);
-        const T ym = __ldg(src + c - Y), yp = __ldg(src + c + Y);
-        dst[c] = Point<T, EXACT>::update(cur, xm, xp, ym, yp, below, above, r);
-        below = cur;
-        cur = above;
-        c += P;
+    int ks = 0;
+    if constexpr (kIsFixed<T>) ks = fx_shift(fx, m3);
+    unsigned long long mx = 0;
+    if (i < g.nx && j < g.ny && k0 < k1) {
+        const int64_t P = g.plane, Y = g.pitch;
+        int64_t c = g.at(i, j, k0);
+        T below = __ldg(src + c - P);
+        T cur = __ldg(src + c);
+        for (int k = k0; k < k1; ++k) {
+            const T above = __ldg(src + c + P);
+            const T xm = __ldg(src + c - 1), xp = __ldg(src + c + 1);
+            const T ym = __ldg(src + c - Y), yp = __ldg(src + c + Y);
+            const T v = Point<T, EXACT>::update(cur, xm, xp, ym, yp, below, above, r, ks);
+            dst[c] = v;
+            if constexpr (kIsFixed<T>) {
+                const unsigned long long a = fx_abs(v);
+                mx = a > mx ? a : mx;
+            }
+            below = cur;
+            cur = above;
+            c += P;
+        }
     }
+    if constexpr (kIsFixed<T>)
+        fx_finish<kBX * kBY>(mx, fx, m3, ks,
+                             blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
 // ---- Boundary kernel ------------------------------------------------------------
@@ -115,17 +228,27 @@ __global__ void __launch_bounds__(kBX* kBY)
 // across devices would exchange.  blockIdx.z selects the plane.
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_heat_boundary(const T* __restrict__ src, T* __restrict__ dst, HeatGeom g, T r)
+    k_heat_boundary(const T* __restrict__ src, T* __restrict__ dst, HeatGeom g, T r, FxState* fx,
+                    int m3)
 {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
-    const int64_t P = g.plane, Y = g.pitch;
-    const int64_t c = g.at(i, j, k);
-    dst[c] = Point<T, EXACT>::update(__ldg(src + c), __ldg(src + c - 1), __ldg(src + c + 1),
-                                     __ldg(src + c - Y), __ldg(src + c + Y), __ldg(src + c - P),
-                                     __ldg(src + c + P), r);
+    int ks = 0;
+    if constexpr (kIsFixed<T>) ks = fx_shift(fx, m3);
+    unsigned long long mx = 0;
+    if (i < g.nx && j < g.ny) {
+        const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
+        const int64_t P = g.plane, Y = g.pitch;
+        const int64_t c = g.at(i, j, k);
+        const T v = Point<T, EXACT>::update(__ldg(src + c), __ldg(src + c - 1), __ldg(src + c + 1),
+                                            __ldg(src + c - Y), __ldg(src + c + Y),
+                                            __ldg(src + c - P), __ldg(src + c + P), r, ks);
+        dst[c] = v;
+        if constexpr (kIsFixed<T>) mx = fx_abs(v);
+    }
+    if constexpr (kIsFixed<T>)
+        fx_finish<kBX * kBY>(mx, fx, m3, ks,
+                             blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
 // ---- full-step kernel -------------------------------------------------------------
@@ -134,10 +257,14 @@ __global__ void __launch_bounds__(kBX* kBY)
 // Interior/Boundary pair, used to cross-check it bit for bit.
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(256)
-    k_heat_full(const T* __restrict__ src, T* __restrict__ dst, HeatGeom g, T r)
+    k_heat_full(const T* __restrict__ src, T* __restrict__ dst, HeatGeom g, T r, FxState* fx,
+                int m3)
 {
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
     const int64_t P = g.plane, Y = g.pitch;
+    int ks = 0;
+    if constexpr (kIsFixed<T>) ks = fx_shift(fx, m3);
+    unsigned long long mx = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.nx);
@@ -145,8 +272,95 @@ __global__ void __launch_bounds__(256)
         const int j = (int)(jk % g.ny);
         const int k = (int)(jk / g.ny);
         const int64_t c = g.at(i, j, k);
-        dst[c] = Point<T, EXACT>::update(src[c], src[c - 1], src[c + 1], src[c - Y], src[c + Y],
-                                         src[c - P], src[c + P], r);
+        const T v = Point<T, EXACT>::update(src[c], src[c - 1], src[c + 1], src[c - Y], src[c + Y],
+                                            src[c - P], src[c + P], r, ks);
+        dst[c] = v;
+        if constexpr (kIsFixed<T>) {
+            const unsigned long long a = fx_abs(v);
+            mx = a > mx ? a : mx;
+        }
+    }
+    if constexpr (kIsFixed<T>) fx_finish<256>(mx, fx, m3, ks, blockIdx.x == 0);
+}
+
+// ---- FIXED64 conversions (at upload and read only) --------------------------------
+// Grid-stride over the interior points of a padded buffer.
+__global__ void __launch_bounds__(256) k_fx_maxabs(const double* __restrict__ buf, HeatGeom g,
+                                                   FxState* st)
+{
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    unsigned long long m = 0;
+    int bad = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const int64_t jk = t / g.nx;
+        const double v = buf[g.at(i, (int)(jk % g.ny), (int)(jk / g.ny))];
+        if (!isfinite(v)) bad = 1;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+        bad |= __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->maxabs_bits, m);
+        if (bad) atomicOr(&st->nonfinite, 1);
+    }
+}
+
+// E such that 12 max|u| 2^E < 2^61: with 12 M = f 2^e, f in [0.5, 1), E = 61 - e.
+__device__ __forceinline__ int fx_scale_exp(const FxState* st)
+{
+    const double m = __longlong_as_double((long long)st->maxabs_bits);
+    if (st->nonfinite || !(m > 0.0)) return 0;
+    int e = 0;
+    (void)frexp(12.0 * m, &e);
+    return 61 - e;
+}
+
+// In place: the interior doubles of buf become round(u 2^E); slot 0 describes
+// the encoded field, slot 1 is cleared for the first step.
+__global__ void __launch_bounds__(256) k_fx_encode(double* __restrict__ buf, HeatGeom g,
+                                                   FxState* st)
+{
+    const int E = fx_scale_exp(st);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double m = __longlong_as_double((long long)st->maxabs_bits);
+        st->slot[0].E = E;
+        st->slot[0].maxU = (st->nonfinite || !(m > 0.0))
+                               ? 0ull
+                               : (unsigned long long)__double2ll_rn(scalbn(m, E));
+        st->slot[1].maxU = 0;
+    }
+    long long* out = reinterpret_cast<long long*>(buf);
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const int64_t jk = t / g.nx;
+        const int64_t c = g.at(i, (int)(jk % g.ny), (int)(jk / g.ny));
+        const double v = buf[c];
+        out[c] = isfinite(v) ? __double2ll_rn(scalbn(v, E)) : 0;
+    }
+}
+
+// The interior of src (fixed point, the field of slot m3) as doubles u = U 2^-E in dst.
+__global__ void __launch_bounds__(256) k_fx_decode(const long long* __restrict__ src,
+                                                   double* __restrict__ dst, HeatGeom g,
+                                                   const FxState* st, int m3)
+{
+    const int E = st->slot[m3].E;
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const int64_t jk = t / g.nx;
+        const int64_t c = g.at(i, (int)(jk % g.ny), (int)(jk / g.ny));
+        dst[c] = scalbn(__ll2double_rn(src[c]), -E);
     }
 }
 
@@ -154,14 +368,19 @@ __global__ void __launch_bounds__(256)
 
 using namespace hcg;
 
+enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3 };
+
 struct hs_heat {
     HeatGeom g;
     int32_t dtype;
+    Arith arith;
     size_t elem;
     double r;
+    long long R;       // FIXED64: r 2^64
     uint32_t flags;
     cudaStream_t stream;
     void* buf[2];
+    FxState* fx;       // FIXED64 only
     int cur;           // buffer holding the current time level
     int64_t steps;     // steps since the last upload
     int kchunk;        // planes per Interior-kernel block
@@ -169,7 +388,7 @@ struct hs_heat {
 
 namespace {
 
-constexpr uint32_t kKnownFlags = HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL;
+constexpr uint32_t kKnownFlags = HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64;
 
 int check_desc(const hs_heat_desc* d)
 {
@@ -186,6 +405,13 @@ int check_desc(const hs_heat_desc* d)
         return fail(HS_EINVAL, "heat: dtype %d is not HS_F64 or HS_F32", d->dtype);
     if ((d->flags & HS_EXACT_ROUNDING) && d->dtype != HS_F64)
         return fail(HS_EINVAL, "heat: HS_EXACT_ROUNDING applies to HS_F64 only");
+    if (d->flags & HS_FIXED64) {
+        if (d->dtype != HS_F64) return fail(HS_EINVAL, "heat: HS_FIXED64 applies to HS_F64 only");
+        if (d->flags & HS_EXACT_ROUNDING)
+            return fail(HS_EINVAL, "heat: HS_FIXED64 and HS_EXACT_ROUNDING exclude each other");
+        if (d->flags & HS_ALLOW_UNSTABLE)
+            return fail(HS_EINVAL, "heat: HS_FIXED64 needs r <= 1/6 (a growing field would overflow)");
+    }
     if (d->reserved0 != 0) return fail(HS_EINVAL, "heat: reserved0 must be 0");
     // Three-dimensional stability of the explicit update: r <= 1/6.
     if (d->r > 1.0 / 6.0 && !(d->flags & HS_ALLOW_UNSTABLE))
@@ -208,8 +434,8 @@ int pick_kchunk(const HeatGeom& g)
     return (int)kc;
 }
 
-template <typename T>
-int launch_interior(hs_heat* h)
+template <typename T, bool EXACT>
+int launch_interior_t(hs_heat* h, T param)
 {
     const HeatGeom& g = h->g;
     if (g.nz < 3) return HS_OK;   // no plane lies strictly between the boundary planes
@@ -217,60 +443,58 @@ int launch_interior(hs_heat* h)
     const int nchunks = (kend - kbeg + h->kchunk - 1) / h->kchunk;
     dim3 block(kBX, kBY, 1);
     dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, nchunks);
-    const T* src = (const T*)h->buf[h->cur];
-    T* dst = (T*)h->buf[1 - h->cur];
-    if (h->flags & HS_EXACT_ROUNDING)
-        k_heat_interior<T, true><<<grid, block, 0, h->stream>>>(src, dst, g, (T)h->r, kbeg, kend,
-                                                                 h->kchunk);
-    else
-        k_heat_interior<T, false><<<grid, block, 0, h->stream>>>(src, dst, g, (T)h->r, kbeg, kend,
-                                                                  h->kchunk);
+    k_heat_interior<T, EXACT><<<grid, block, 0, h->stream>>>(
+        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, kbeg, kend, h->kchunk, h->fx,
+        (int)(h->steps % 3));
     HS_CHECK_LAUNCH("heat interior kernel");
     return HS_OK;
 }
 
-template <typename T>
-int launch_boundary(hs_heat* h)
+template <typename T, bool EXACT>
+int launch_boundary_t(hs_heat* h, T param)
 {
     const HeatGeom& g = h->g;
     dim3 block(kBX, kBY, 1);
     dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz >= 2 ? 2 : 1);
-    const T* src = (const T*)h->buf[h->cur];
-    T* dst = (T*)h->buf[1 - h->cur];
-    if (h->flags & HS_EXACT_ROUNDING)
-        k_heat_boundary<T, true><<<grid, block, 0, h->stream>>>(src, dst, g, (T)h->r);
-    else
-        k_heat_boundary<T, false><<<grid, block, 0, h->stream>>>(src, dst, g, (T)h->r);
+    k_heat_boundary<T, EXACT><<<grid, block, 0, h->stream>>>(
+        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->steps % 3));
     HS_CHECK_LAUNCH("heat boundary kernel");
     return HS_OK;
 }
 
-template <typename T>
-int launch_full(hs_heat* h)
+template <typename T, bool EXACT>
+int launch_full_t(hs_heat* h, T param)
 {
     const HeatGeom& g = h->g;
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
     int64_t blocks = (n + 255) / 256;
     if (blocks > (int64_t)kNumSMs * 64) blocks = (int64_t)kNumSMs * 64;
-    const T* src = (const T*)h->buf[h->cur];
-    T* dst = (T*)h->buf[1 - h->cur];
-    if (h->flags & HS_EXACT_ROUNDING)
-        k_heat_full<T, true><<<(unsigned)blocks, 256, 0, h->stream>>>(src, dst, g, (T)h->r);
-    else
-        k_heat_full<T, false><<<(unsigned)blocks, 256, 0, h->stream>>>(src, dst, g, (T)h->r);
+    k_heat_full<T, EXACT><<<(unsigned)blocks, 256, 0, h->stream>>>(
+        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->steps % 3));
     HS_CHECK_LAUNCH("heat full-step kernel");
     return HS_OK;
 }
 
-int do_interior(hs_heat* h)
+enum Part { P_INTERIOR, P_BOUNDARY, P_FULL };
+
+template <typename T, bool EXACT>
+int launch_part(hs_heat* h, Part p, T param)
 {
-    return h->dtype == HS_F64 ? launch_interior<double>(h) : launch_interior<float>(h);
+    if (p == P_INTERIOR) return launch_interior_t<T, EXACT>(h, param);
+    if (p == P_BOUNDARY) return launch_boundary_t<T, EXACT>(h, param);
+    return launch_full_t<T, EXACT>(h, param);
 }
-int do_boundary(hs_heat* h)
+
+int do_part(hs_heat* h, Part p)
 {
-    return h->dtype == HS_F64 ? launch_boundary<double>(h) : launch_boundary<float>(h);
+    switch (h->arith) {
+    case A_F64: return launch_part<double, false>(h, p, h->r);
+    case A_F64_EXACT: return launch_part<double, true>(h, p, h->r);
+    case A_F32: return launch_part<float, false>(h, p, (float)h->r);
+    case A_FX64: return launch_part<long long, false>(h, p, h->R);
+    }
+    return fail(HS_EINVAL, "heat: unknown arithmetic");
 }
-int do_full(hs_heat* h) { return h->dtype == HS_F64 ? launch_full<double>(h) : launch_full<float>(h); }
 
 // Copies between a dense nx*ny*nz array and the interior of a padded buffer.
 int copy_interior(hs_heat* h, void* buf, const void* dense, void* dense_out, cudaMemcpyKind kind)
@@ -297,6 +521,14 @@ int copy_interior(hs_heat* h, void* buf, const void* dense, void* dense_out, cud
     return HS_OK;
 }
 
+unsigned conv_blocks(const HeatGeom& g)
+{
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = (int64_t)kNumSMs * 16;
+    return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
 }  // namespace
 
 extern "C" {
@@ -308,6 +540,7 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
     if (!bytes) return fail(HS_EINVAL, "heat_device_bytes: bytes is NULL");
     const HeatGeom g = make_geom(desc->nx, desc->ny, desc->nz, elem_size(desc->dtype));
     *bytes = 2 * (size_t)g.total * elem_size(desc->dtype);
+    if (desc->flags & HS_FIXED64) *bytes += sizeof(FxState);
     return HS_OK;
 }
 
@@ -324,6 +557,14 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     h->g = make_geom(desc->nx, desc->ny, desc->nz, h->elem);
     h->r = desc->r;
     h->flags = desc->flags;
+    h->arith = (desc->flags & HS_FIXED64)          ? A_FX64
+               : (desc->flags & HS_EXACT_ROUNDING) ? A_F64_EXACT
+               : (desc->dtype == HS_F32)           ? A_F32
+                                                   : A_F64;
+    // r <= 1/6 < 1/2, so r 2^64 < 2^63.  For r >= 2^-11 it is an integer (r's
+    // last bit is worth at least 2^-64), so R holds r exactly; a smaller r is
+    // rounded to the nearest multiple of 2^-64.
+    h->R = (h->arith == A_FX64) ? std::llrint(std::ldexp(desc->r, 64)) : 0;
     h->stream = (cudaStream_t)desc->stream;
     h->cur = 0;
     h->steps = 0;
@@ -344,6 +585,15 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             return rc;
         }
     }
+    if (h->arith == A_FX64) {
+        cudaError_t e = cudaMalloc((void**)&h->fx, sizeof(FxState));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "heat_create: fixed-point state");
+            heat_destroy(h);
+            return rc;
+        }
+    }
     *out = h;
     return HS_OK;
 }
@@ -358,6 +608,14 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
     // paper reaches by uploading u_old and u_new alike.
     int rc = copy_interior(h, h->buf[0], u, nullptr, kind);
     if (rc != HS_OK) return rc;
+    if (h->arith == A_FX64) {
+        HS_TRY_CUDA(cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream), "heat_upload: memset");
+        const unsigned blocks = conv_blocks(h->g);
+        k_fx_maxabs<<<blocks, 256, 0, h->stream>>>((const double*)h->buf[0], h->g, h->fx);
+        HS_CHECK_LAUNCH("heat_upload: max|u| kernel");
+        k_fx_encode<<<blocks, 256, 0, h->stream>>>((double*)h->buf[0], h->g, h->fx);
+        HS_CHECK_LAUNCH("heat_upload: fixed-point encode kernel");
+    }
     h->cur = 0;
     h->steps = 0;
     return HS_OK;
@@ -366,13 +624,13 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
 int heat_interior(hs_heat_t h)
 {
     if (!h) return fail(HS_EINVAL, "heat_interior: NULL handle");
-    return do_interior(h);
+    return do_part(h, P_INTERIOR);
 }
 
 int heat_boundary(hs_heat_t h)
 {
     if (!h) return fail(HS_EINVAL, "heat_boundary: NULL handle");
-    return do_boundary(h);
+    return do_part(h, P_BOUNDARY);
 }
 
 int heat_swap(hs_heat_t h)
@@ -390,10 +648,10 @@ int heat_step(hs_heat_t h, int64_t n_steps)
     for (int64_t m = 0; m < n_steps; ++m) {
         int rc;
         if (h->flags & HS_SCHED_FULL) {
-            rc = do_full(h);
+            rc = do_part(h, P_FULL);
         } else {
-            rc = do_boundary(h);
-            if (rc == HS_OK) rc = do_interior(h);
+            rc = do_part(h, P_BOUNDARY);
+            if (rc == HS_OK) rc = do_part(h, P_INTERIOR);
         }
         if (rc != HS_OK) return rc;
         h->cur = 1 - h->cur;
@@ -406,9 +664,26 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device)
 {
     if (!h || !dst) return fail(HS_EINVAL, "heat_read: NULL handle or destination");
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    int rc = copy_interior(h, h->buf[h->cur], nullptr, dst, kind);
+    void* src = h->buf[h->cur];
+    if (h->arith == A_FX64) {
+        // Decode into the spare buffer's interior; the next step overwrites
+        // all of it, and its boundary layer stays zero.
+        k_fx_decode<<<conv_blocks(h->g), 256, 0, h->stream>>>(
+            (const long long*)h->buf[h->cur], (double*)h->buf[1 - h->cur], h->g, h->fx,
+            (int)(h->steps % 3));
+        HS_CHECK_LAUNCH("heat_read: fixed-point decode kernel");
+        src = h->buf[1 - h->cur];
+    }
+    int rc = copy_interior(h, src, nullptr, dst, kind);
     if (rc != HS_OK) return rc;
     HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
+    if (h->arith == A_FX64) {
+        FxState st;
+        HS_TRY_CUDA(cudaMemcpy(&st, h->fx, sizeof(st), cudaMemcpyDeviceToHost), "heat_read: state");
+        if (st.nonfinite)
+            return fail(HS_ERANGE, "heat_read: the uploaded field held NaN or Inf, which the "
+                                   "fixed-point form cannot carry");
+    }
     return HS_OK;
 }
 
@@ -429,6 +704,7 @@ int heat_destroy(hs_heat_t h)
     }
     for (int b = 0; b < 2; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->fx) cudaFree(h->fx);
     delete h;
     return rc;
 }
