@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--heat-mode", choices=sorted(HEAT_MODES), default="f64",
                     help="arithmetic of the timed heat segment")
+    ap.add_argument("--tdepth", type=int, default=0,
+                    help="steps per pass of the timed heat handle (0: library choice)")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the untimed one-solve runs of the other heat modes")
     return ap.parse_args()
@@ -134,23 +136,27 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind):
-    """Roofline object of the Interior kernel from its mean launch time (ms)."""
+def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind, tdepth=1):
+    """Roofline object of the dominant heat kernel from its mean launch time
+    (ms): the streaming Interior kernel (tdepth 1, planes 1..n-2) or the
+    temporally blocked kernel (tdepth L: all n planes, L steps per launch;
+    algorithmic bytes = one read and one write of the field per launch)."""
     spec = HEAT_MODES[mode_name]
-    lup = float(n) * n * max(n - 2, 0)
+    lup = float(n) * n * (max(n - 2, 0) if tdepth == 1 else n)
     hbm_rate = lup * spec["bytes"] / (int_ms * 1e-3) / 1e9
-    name = {"f64": "k_heat_interior<double> (FP64, 7 instr/LUP)",
-            "fixed64": "k_heat_interior<long long> (64-bit fixed point)",
-            "f32": "k_heat_interior<float>"}[mode_name]
+    tname = {"f64": "double", "fixed64": "long long", "f32": "float"}[mode_name]
+    name = (f"k_heat_stream<{tname}> (Interior, one step)" if tdepth == 1
+            else f"k_heat_tb<{tname}, L={tdepth}>")
     if spec["bound"] == "alu":
-        rate = lup * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
+        rate = lup * tdepth * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": name, "achieved": rate, "peak": FP64_INSTR_PEAK_T,
                 "unit": "T FP64-instr/s", "frac": rate / FP64_INSTR_PEAK_T, "traffic": None,
                 "hbm_achieved_gbs": hbm_rate, "hbm_peak_gbs": hbm_gbs, "hbm_frac": hbm_rate / hbm_gbs,
                 "hbm_peak_kind": peak_kind, "interior_ms_per_launch": int_ms}
     return {"bound": "hbm", "kernel": name, "achieved": hbm_rate, "peak": hbm_gbs, "unit": "GB/s",
             "frac": hbm_rate / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
-            "bytes_per_lup": spec["bytes"], "interior_ms_per_launch": int_ms}
+            "bytes_per_lup": spec["bytes"], "steps_per_launch": tdepth,
+            "effective_gbs": hbm_rate * tdepth, "interior_ms_per_launch": int_ms}
 
 
 # ---------------------------------------------------------------------------------
@@ -260,7 +266,8 @@ def run_ours(args):
     def make_heat(mode):
         spec = HEAT_MODES[mode]
         flags = getattr(pkg, spec["flags"]) if spec["flags"] else 0
-        return pkg.Heat(n, n, n, args.r, dtype=spec["dtype"], flags=flags, stream=stream)
+        return pkg.Heat(n, n, n, args.r, dtype=spec["dtype"], flags=flags, stream=stream,
+                        tdepth=args.tdepth)
 
     mode = HEAT_MODES[args.heat_mode]
     heat = make_heat(args.heat_mode)
@@ -276,11 +283,21 @@ def run_ours(args):
     pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
              for _ in range(hsteps)]
 
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    step_launches = [0]
+
     def one_step(timed_interior: bool):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         heat.upload(u0_dev)
-        if timed_interior:
+        if timed_interior and heat.tdepth > 1:
+            # blocked passes: one kernel per pass, timed around the whole step loop
+            step_ev[0].record(stream)
+            l0 = nat.launch_count()
+            heat.step(hsteps)
+            step_launches[0] = nat.launch_count() - l0
+            step_ev[1].record(stream)
+        elif timed_interior:
             for s in range(hsteps):
                 heat.boundary()
                 pairs[s][0].record(stream)
@@ -319,7 +336,10 @@ def run_ours(args):
         seg["heat"].append(ev[0].elapsed_time(ev[1]))
         seg["cg_mf"].append(ev[1].elapsed_time(ev[2]))
         seg["cg_csr"].append(ev[2].elapsed_time(ev[3]))
-        interior_ms.append(sum(a.elapsed_time(b) for a, b in pairs) / hsteps)
+        if heat.tdepth > 1:
+            interior_ms.append(step_ev[0].elapsed_time(step_ev[1]) / step_launches[0])
+        else:
+            interior_ms.append(sum(a.elapsed_time(b) for a, b in pairs) / hsteps)
         infos.append((i_mf, i_csr))
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -339,7 +359,7 @@ def run_ours(args):
 
     # dominant kernel: the Interior kernel of the timed heat mode
     int_ms = statistics.mean(interior_ms)
-    roofline = interior_roofline(args.heat_mode, n, int_ms, hbm_gbs, peak_kind)
+    roofline = interior_roofline(args.heat_mode, n, int_ms, hbm_gbs, peak_kind, heat.tdepth)
 
     def pct(v, q):
         v = sorted(v)
@@ -406,17 +426,28 @@ def run_ours(args):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             h.upload(src)
-            for s in range(hsteps):
-                h.boundary()
-                pairs[s][0].record(stream)
-                h.interior()
-                pairs[s][1].record(stream)
-                h.swap()
+            if h.tdepth > 1:
+                step_ev[0].record(stream)
+                l0 = nat.launch_count()
+                h.step(hsteps)
+                nl = nat.launch_count() - l0
+                step_ev[1].record(stream)
+            else:
+                for s in range(hsteps):
+                    h.boundary()
+                    pairs[s][0].record(stream)
+                    h.interior()
+                    pairs[s][1].record(stream)
+                    h.swap()
             out = torch.empty_like(src)
             h.read(out)
             ev1.record(stream)
             ev1.synchronize()
-            return ev0.elapsed_time(ev1), sum(a.elapsed_time(b) for a, b in pairs) / hsteps, out
+            if h.tdepth > 1:
+                ims = step_ev[0].elapsed_time(step_ev[1]) / nl
+            else:
+                ims = sum(a.elapsed_time(b) for a, b in pairs) / hsteps
+            return ev0.elapsed_time(ev1), ims, out
 
         fields = {args.heat_mode: u_out_dev}
         side = {}
@@ -429,10 +460,12 @@ def run_ours(args):
                 src = src.float()
             h2 = make_heat(name)
             seg_ms, ims, out = solve_once(h2, src)
+            side_tdepth = h2.tdepth
             h2.close()
             fields[name] = out
             side[name] = {"glups": lup_step / (seg_ms * 1e-3) / 1e9, "arith": spec["arith"],
-                          "roofline": interior_roofline(name, n, ims, hbm_gbs, peak_kind)}
+                          "tdepth": side_tdepth,
+                          "roofline": interior_roofline(name, n, ims, hbm_gbs, peak_kind, side_tdepth)}
             del src
         ref = fields["f64"].double()
         refmax = float(ref.abs().max())

@@ -86,7 +86,10 @@ typedef struct {
     double   r;            /* alpha*dt/h^2 >= 0; see HS_ALLOW_UNSTABLE         */
     uint32_t flags;        /* HS_* heat flags                                 */
     int32_t  dtype;        /* HS_F64 or HS_F32: storage and arithmetic type   */
-    int32_t  reserved0;    /* must be 0                                       */
+    int32_t  tdepth;       /* time steps per pass over HBM: 0 = library choice
+                              (currently 1), 1 = the Interior + Boundary
+                              kernels every step, or 2, 3, 4, 6, 8 =
+                              temporal blocking (see heat_step)            */
     void*    stream;       /* cudaStream_t for all work of this handle        */
 } hs_heat_desc;
 
@@ -110,13 +113,19 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
  * device memory otherwise.  Enqueued on the handle's stream. */
 int heat_upload(hs_heat_t h, const void* u, int src_is_device);
 
-/* Advance n_steps >= 0 steps.  Each step runs the Boundary kernel on the
- * first and last interior k-planes and the Interior kernel on the planes
- * between them (Algorithms BOUNDARY and INTERIOR; on one GPU the planes a
- * k-split would exchange are the outermost interior planes), then swaps the
- * buffers by pointer (Algorithm "1-GPU Baseline").  Asynchronous: launch
- * errors are returned here, errors raised while kernels run are returned by
- * the next synchronising call. */
+/* Advance n_steps >= 0 steps.  With tdepth 1 each step runs the Boundary
+ * kernel on the first and last interior k-planes and the Interior kernel on
+ * the planes between them (Algorithms BOUNDARY and INTERIOR; on one GPU the
+ * planes a k-split would exchange are the outermost interior planes), then
+ * swaps the buffers by pointer (Algorithm "1-GPU Baseline").  With tdepth
+ * L >= 2 each pass over HBM advances L steps (temporal blocking: tiles with
+ * an L-wide halo stream up the k axis, the intermediate time levels living
+ * in shared memory and registers), then swaps; a remainder of n_steps is done
+ * in shallower passes.  The result equals stepping one step at a time up to
+ * rounding (bit for bit for FP32 and FP64, whose per-point arithmetic is the
+ * same; FIXED64 may rescale at different steps).  Asynchronous: launch errors
+ * are returned here, errors raised while kernels run are returned by the next
+ * synchronising call (a bounded device wait that ran out: HS_ETIMEOUT). */
 int heat_step(hs_heat_t h, int64_t n_steps);
 
 /* The three parts of one step, for callers that schedule them themselves:
@@ -134,6 +143,10 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device);
 
 /* Steps applied since the last heat_upload. */
 int heat_steps_done(hs_heat_t h, int64_t* steps);
+
+/* The temporal depth the handle runs with (tdepth resolved: 1 = the Interior
+ * + Boundary kernels every step, L >= 2 = L steps per pass). */
+int heat_get_tdepth(hs_heat_t h, int32_t* tdepth);
 
 /* Release the handle and its device buffers (synchronises its stream). */
 int heat_destroy(hs_heat_t h);

@@ -29,7 +29,7 @@ class HeatCGError(RuntimeError):
 class hs_heat_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("r", ctypes.c_double), ("flags", ctypes.c_uint32), ("dtype", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("tdepth", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class hs_op(ctypes.Structure):
@@ -60,6 +60,7 @@ def _load():
         "heat_swap": [vp],
         "heat_read": [vp, vp, ctypes.c_int],
         "heat_steps_done": [vp, ctypes.POINTER(i64)],
+        "heat_get_tdepth": [vp, ctypes.POINTER(i32)],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
         "cg_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), vp],
@@ -138,6 +139,12 @@ def heat_steps_done(h: int) -> int:
     s = ctypes.c_int64()
     check(lib.heat_steps_done(h, ctypes.byref(s)), "heat_steps_done")
     return s.value
+
+
+def heat_get_tdepth(h: int) -> int:
+    t = ctypes.c_int32()
+    check(lib.heat_get_tdepth(h, ctypes.byref(t)), "heat_get_tdepth")
+    return t.value
 
 
 def heat_destroy(h: int) -> None:

@@ -46,12 +46,12 @@ class Heat:
     """A resident heat field (heat_create / heat_upload / heat_step / heat_read)."""
 
     def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
-                 stream=None):
+                 stream=None, tdepth: int = 0):
         self.shape = (nz, ny, nx)
         self.dtype_code, self.np_dtype = _DTYPES[dtype]
         self.stream = _stream_handle(stream)
         desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,
-                                   reserved0=0, stream=self.stream)
+                                   tdepth=tdepth, stream=self.stream)
         self.handle = native.heat_create(desc)
 
     @property
@@ -85,6 +85,11 @@ class Heat:
         ptr, dev, _ = _buffer(out, self.np_dtype, self.count)
         native.heat_read(self.handle, ptr, dev)
         return out
+
+    @property
+    def tdepth(self) -> int:
+        """Steps per pass the handle runs with (1: Interior + Boundary every step)."""
+        return native.heat_get_tdepth(self.handle)
 
     @property
     def steps_done(self) -> int:

@@ -36,148 +36,10 @@
 #include <new>
 #include <type_traits>
 
-#include "common.cuh"
+#include "heat_common.cuh"
+#include "tma.cuh"
 
 namespace hcg {
-
-struct HeatGeom {
-    int32_t nx, ny, nz;
-    int32_t lead;    // element offset of interior x = 0 within a row
-    int64_t pitch;   // elements per row
-    int64_t plane;   // elements per plane = pitch * (ny + 2)
-    int64_t total;   // elements per buffer = plane * (nz + 2)
-    __host__ __device__ __forceinline__ int64_t at(int i, int j, int k) const
-    {
-        return (int64_t)(k + 1) * plane + (int64_t)(j + 1) * pitch + lead + i;
-    }
-};
-
-static HeatGeom make_geom(int nx, int ny, int nz, size_t elem)
-{
-    HeatGeom g;
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
-    g.lead = (int32_t)(32 / elem);
-    const int64_t row_quant = (int64_t)(128 / elem);
-    g.pitch = ((int64_t)g.lead + nx + 1 + row_quant - 1) / row_quant * row_quant;
-    g.plane = g.pitch * (ny + 2);
-    g.total = g.plane * (nz + 2);
-    return g;
-}
-
-// Fixed-point bookkeeping of a FIXED64 field (device memory).  The field at
-// step m has scale E_m (U = round(u 2^E_m)) and integer max M_m = max|U|, kept
-// in slot m % 3.  The kernels of step m read slot m % 3, write slot (m+1) % 3
-// (atomic max of their outputs, and E_{m+1}) and clear slot (m+2) % 3, which no
-// kernel of step m reads -- so no kernel ever races on a slot.
-struct FxSlot {
-    unsigned long long maxU;   // max |U| of the field
-    int32_t E;                 // scale exponent of the field
-    int32_t pad;
-};
-
-struct FxState {
-    unsigned long long maxabs_bits;   // bit pattern of max|u0| (non-negative doubles order like integers)
-    int32_t nonfinite;                // 1 if the uploaded field held NaN or Inf
-    int32_t pad;
-    FxSlot slot[3];
-};
-
-// Left shift that keeps a shrinking field near full precision: the largest k
-// with M 2^k < 2^57, so |S - 6U| 2^k <= 12 M 2^k < 2^61 never overflows.
-__device__ __forceinline__ int fx_shift(const FxState* fx, int m3)
-{
-    const unsigned long long M = fx->slot[m3].maxU;
-    if (M == 0) return 0;
-    const int k = 57 - (64 - __clzll((long long)M));
-    return k > 0 ? k : 0;
-}
-
-__device__ __forceinline__ unsigned long long fx_abs(long long v)
-{
-    return v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-}
-
-// Block-wide max of the outputs into slot (m3+1) % 3; the grid leader also
-// records E_{m+1} = E_m + k and clears slot (m3+2) % 3 for the next step.
-template <int NT>
-__device__ __forceinline__ void fx_finish(unsigned long long m, FxState* fx, int m3, int k,
-                                          bool leader)
-{
-    __shared__ unsigned long long wmax[NT / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_down_sync(0xffffffffu, m, o);
-        m = other > m ? other : m;
-    }
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if ((tid & 31) == 0) wmax[tid >> 5] = m;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long b = 0;
-        for (int w = 0; w < NT / 32; ++w) b = wmax[w] > b ? wmax[w] : b;
-        atomicMax(&fx->slot[(m3 + 1) % 3].maxU, b);
-        if (leader) {
-            fx->slot[(m3 + 1) % 3].E = fx->slot[m3].E + k;
-            fx->slot[(m3 + 2) % 3].maxU = 0;
-        }
-    }
-}
-
-// ---- the point update -------------------------------------------------------
-// k is the FIXED64 rescaling shift of this step (unused by the floating types).
-template <typename T, bool EXACT>
-struct Point;
-
-template <bool EXACT>
-struct Point<double, EXACT> {
-    // Default: the six-neighbour sum in the written order, then two fused
-    // multiply-adds t = s - 6u, u' = u + r t (7 FP64 instructions per point).
-    // Exact: one rounding per operation in the written order, no fusion.
-    static __device__ __forceinline__ double update(double c, double xm, double xp, double ym,
-                                                    double yp, double zm, double zp, double r, int)
-    {
-        const double s = __dadd_rn(__dadd_rn(__dadd_rn(xm, xp), __dadd_rn(ym, yp)),
-                                   __dadd_rn(zm, zp));
-        if (EXACT) return __dadd_rn(c, __dmul_rn(r, __dsub_rn(s, __dmul_rn(6.0, c))));
-        return __fma_rn(r, __fma_rn(-6.0, c, s), c);
-    }
-};
-
-template <bool EXACT>
-struct Point<float, EXACT> {
-    static __device__ __forceinline__ float update(float c, float xm, float xp, float ym, float yp,
-                                                   float zm, float zp, float r, int)
-    {
-        const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)),
-                                  __fadd_rn(zm, zp));
-        if (EXACT) return __fadd_rn(c, __fmul_rn(r, __fsub_rn(s, __fmul_rn(6.0f, c))));
-        return __fmaf_rn(r, __fmaf_rn(-6.0f, c, s), c);
-    }
-};
-
-template <bool EXACT>
-struct Point<long long, EXACT> {
-    // FIXED64: R = r 2^64 (a non-negative int64: r <= 1/6 < 1/2).  S - 6U is
-    // exact; it and U are moved to the new scale by the exact shift k; then
-    // t R / 2^64 is rounded to nearest (ties up): floor((t R + 2^63) / 2^64)
-    // = high word of t R plus the top bit of its low word.
-    static __device__ __forceinline__ long long update(long long c, long long xm, long long xp,
-                                                       long long ym, long long yp, long long zm,
-                                                       long long zp, long long R, int k)
-    {
-        const long long s = ((xm + xp) + (ym + yp)) + (zm + zp);
-        const long long t = (long long)((unsigned long long)(s - 6 * c) << k);
-        const long long cs = (long long)((unsigned long long)c << k);
-        const long long hi = __mul64hi(t, R);
-        const unsigned long long lo = (unsigned long long)t * (unsigned long long)R;
-        return cs + hi + (long long)(lo >> 63);
-    }
-};
-
-template <typename T>
-constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
 // ---- Interior kernel ----------------------------------------------------------
 // One thread per (i, j) column marches up a chunk of k-planes, keeping the
@@ -368,8 +230,6 @@ __global__ void __launch_bounds__(256) k_fx_decode(const long long* __restrict__
 
 using namespace hcg;
 
-enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3 };
-
 struct hs_heat {
     HeatGeom g;
     int32_t dtype;
@@ -381,9 +241,16 @@ struct hs_heat {
     cudaStream_t stream;
     void* buf[2];
     FxState* fx;       // FIXED64 only
+    int* err;          // device error word: 1 when a bounded device wait ran out
     int cur;           // buffer holding the current time level
     int64_t steps;     // steps since the last upload
+    int64_t fxseq;     // fields produced since the last upload (FIXED64 slot = fxseq % 3)
     int kchunk;        // planes per Interior-kernel block
+    int tdepth;        // steps per pass of the temporally blocked kernel (1: Interior + Boundary)
+    int kc_tb;         // k-planes per block of the temporally blocked kernel
+    CUtensorMap maps[2];   // TMA maps of the two buffers (temporal blocking)
+    CUtensorMap smaps[2];  // TMA maps of the two buffers (streaming Interior kernel)
+    int kc_stream;         // k-planes per block of the streaming Interior kernel
 };
 
 namespace {
@@ -412,7 +279,11 @@ int check_desc(const hs_heat_desc* d)
         if (d->flags & HS_ALLOW_UNSTABLE)
             return fail(HS_EINVAL, "heat: HS_FIXED64 needs r <= 1/6 (a growing field would overflow)");
     }
-    if (d->reserved0 != 0) return fail(HS_EINVAL, "heat: reserved0 must be 0");
+    if (d->tdepth != 0 && d->tdepth != 1 && d->tdepth != 2 && d->tdepth != 3 && d->tdepth != 4 &&
+        d->tdepth != 6 && d->tdepth != 8)
+        return fail(HS_EINVAL, "heat: tdepth %d not in {0, 1, 2, 3, 4, 6, 8}", d->tdepth);
+    if ((d->flags & HS_SCHED_FULL) && d->tdepth > 1)
+        return fail(HS_EINVAL, "heat: HS_SCHED_FULL runs one step per pass (tdepth 0 or 1)");
     // Three-dimensional stability of the explicit update: r <= 1/6.
     if (d->r > 1.0 / 6.0 && !(d->flags & HS_ALLOW_UNSTABLE))
         return fail(HS_EUNSTABLE, "heat: r = %.17g exceeds the stability bound 1/6", d->r);
@@ -445,7 +316,7 @@ int launch_interior_t(hs_heat* h, T param)
     dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, nchunks);
     k_heat_interior<T, EXACT><<<grid, block, 0, h->stream>>>(
         (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, kbeg, kend, h->kchunk, h->fx,
-        (int)(h->steps % 3));
+        (int)(h->fxseq % 3));
     HS_CHECK_LAUNCH("heat interior kernel");
     return HS_OK;
 }
@@ -457,7 +328,7 @@ int launch_boundary_t(hs_heat* h, T param)
     dim3 block(kBX, kBY, 1);
     dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz >= 2 ? 2 : 1);
     k_heat_boundary<T, EXACT><<<grid, block, 0, h->stream>>>(
-        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->steps % 3));
+        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->fxseq % 3));
     HS_CHECK_LAUNCH("heat boundary kernel");
     return HS_OK;
 }
@@ -470,17 +341,38 @@ int launch_full_t(hs_heat* h, T param)
     int64_t blocks = (n + 255) / 256;
     if (blocks > (int64_t)kNumSMs * 64) blocks = (int64_t)kNumSMs * 64;
     k_heat_full<T, EXACT><<<(unsigned)blocks, 256, 0, h->stream>>>(
-        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->steps % 3));
+        (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->fxseq % 3));
     HS_CHECK_LAUNCH("heat full-step kernel");
     return HS_OK;
 }
 
 enum Part { P_INTERIOR, P_BOUNDARY, P_FULL };
 
+// The Interior kernel: planes 1 .. nz-2, staged through shared memory by TMA.
+int launch_stream_interior(hs_heat* h)
+{
+    if (h->g.nz < 3) return HS_OK;   // no plane lies strictly between the boundary planes
+    StreamCall c;
+    c.arith = h->arith;
+    c.kbeg = 1;
+    c.kend = h->g.nz - 1;
+    c.kc = h->kc_stream;
+    c.map = &h->smaps[h->cur];
+    c.dst = h->buf[1 - h->cur];
+    c.g = &h->g;
+    c.r = h->r;
+    c.R = h->R;
+    c.fx = h->fx;
+    c.m3 = (int)(h->fxseq % 3);
+    c.err = h->err;
+    c.stream = h->stream;
+    return stream_launch(c);
+}
+
 template <typename T, bool EXACT>
 int launch_part(hs_heat* h, Part p, T param)
 {
-    if (p == P_INTERIOR) return launch_interior_t<T, EXACT>(h, param);
+    if (p == P_INTERIOR) return launch_stream_interior(h);
     if (p == P_BOUNDARY) return launch_boundary_t<T, EXACT>(h, param);
     return launch_full_t<T, EXACT>(h, param);
 }
@@ -494,6 +386,65 @@ int do_part(hs_heat* h, Part p)
     case A_FX64: return launch_part<long long, false>(h, p, h->R);
     }
     return fail(HS_EINVAL, "heat: unknown arithmetic");
+}
+
+// Temporal depth when the descriptor leaves it to the library: FP64 is bound
+// by the FP64 pipe (blocking saves only bytes), the others by HBM.
+int default_tdepth(Arith)
+{
+    return 1;
+}
+
+int pick_kc_tb(const HeatGeom& g, int L)
+{
+    const int TX = 32 - 2 * L, TY = kTbRows - 2 * L;
+    const int64_t tiles = (int64_t)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    const int64_t target = (int64_t)kNumSMs * 2 * 6;   // about six waves of two blocks per SM
+    int64_t chunks = (target + tiles - 1) / tiles;
+    if (chunks < 1) chunks = 1;
+    int64_t kc = (g.nz + chunks - 1) / chunks;
+    const int64_t floor_kc = 16 * L;                   // keep the z halo (2L planes) small
+    if (kc < floor_kc) kc = floor_kc;
+    if (kc > g.nz) kc = g.nz;
+    return (int)kc;
+}
+
+int pick_kc_stream(const HeatGeom& g)
+{
+    const int tw = 512 / (int)g.elem;                  // tile width: 32 threads x one 16-byte vector
+    const int64_t tiles = (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + kStreamRowsHost - 1) / kStreamRowsHost);
+    const int64_t target = (int64_t)kNumSMs * 3 * 4;   // about four waves of three blocks per SM
+    const int64_t planes = g.nz > 2 ? g.nz - 2 : 1;
+    int64_t chunks = (target + tiles - 1) / tiles;
+    if (chunks < 1) chunks = 1;
+    int64_t kc = (planes + chunks - 1) / chunks;
+    if (kc < 8) kc = 8;
+    if (kc > planes) kc = planes;
+    return (int)kc;
+}
+
+// One pass of L steps with the temporally blocked kernel.
+int tb_pass(hs_heat* h, int L)
+{
+    TbCall c;
+    c.arith = h->arith;
+    c.L = L;
+    c.kc = pick_kc_tb(h->g, L);
+    c.map = &h->maps[h->cur];
+    c.dst = h->buf[1 - h->cur];
+    c.g = &h->g;
+    c.r = h->r;
+    c.R = h->R;
+    c.fx = h->fx;
+    c.m3 = (int)(h->fxseq % 3);
+    c.err = h->err;
+    c.stream = h->stream;
+    int rc = tb_launch(c);
+    if (rc != HS_OK) return rc;
+    h->cur = 1 - h->cur;
+    h->steps += L;
+    h->fxseq += 1;
+    return HS_OK;
 }
 
 // Copies between a dense nx*ny*nz array and the interior of a padded buffer.
@@ -569,6 +520,8 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     h->cur = 0;
     h->steps = 0;
     h->kchunk = pick_kchunk(h->g);
+    h->tdepth = desc->tdepth ? desc->tdepth : default_tdepth(h->arith);
+    if (h->flags & HS_SCHED_FULL) h->tdepth = 1;
     const size_t bytes = (size_t)h->g.total * h->elem;
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&h->buf[b], bytes);
@@ -583,6 +536,48 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             rc = cuda_fail(e, "heat_create: cudaMemsetAsync");
             heat_destroy(h);
             return rc;
+        }
+    }
+    {
+        cudaError_t e = cudaMalloc((void**)&h->err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "heat_create: error word");
+            heat_destroy(h);
+            return rc;
+        }
+    }
+    {
+        const CUtensorMapDataType dt = h->arith == A_FX64   ? CU_TENSOR_MAP_DATA_TYPE_INT64
+                                       : h->dtype == HS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        uint32_t bx = 0, by = 0;
+        stream_box(h->arith, &bx, &by);
+        for (int b = 0; b < 2; ++b) {
+            const int e = encode_field_map(&h->smaps[b], h->buf[b], dt, h->elem, (uint64_t)h->g.pitch,
+                                           (uint64_t)(h->g.ny + 2), (uint64_t)(h->g.nz + 2), bx, by);
+            if (e != 0) {
+                rc = cuda_fail((cudaError_t)e, "heat_create: TMA tensor map (streaming)");
+                heat_destroy(h);
+                return rc;
+            }
+        }
+        h->kc_stream = pick_kc_stream(h->g);
+    }
+    if (h->tdepth > 1) {
+        const CUtensorMapDataType dt = h->arith == A_FX64   ? CU_TENSOR_MAP_DATA_TYPE_INT64
+                                       : h->dtype == HS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        const uint32_t box_x = 32 + (uint32_t)(16 / h->elem);
+        for (int b = 0; b < 2; ++b) {
+            const int e = encode_field_map(&h->maps[b], h->buf[b], dt, h->elem, (uint64_t)h->g.pitch,
+                                           (uint64_t)(h->g.ny + 2), (uint64_t)(h->g.nz + 2), box_x,
+                                           (uint32_t)kTbRows);
+            if (e != 0) {
+                rc = cuda_fail((cudaError_t)e, "heat_create: TMA tensor map");
+                heat_destroy(h);
+                return rc;
+            }
         }
     }
     if (h->arith == A_FX64) {
@@ -618,6 +613,7 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
     }
     h->cur = 0;
     h->steps = 0;
+    h->fxseq = 0;
     return HS_OK;
 }
 
@@ -638,6 +634,7 @@ int heat_swap(hs_heat_t h)
     if (!h) return fail(HS_EINVAL, "heat_swap: NULL handle");
     h->cur = 1 - h->cur;
     h->steps += 1;
+    h->fxseq += 1;
     return HS_OK;
 }
 
@@ -645,6 +642,19 @@ int heat_step(hs_heat_t h, int64_t n_steps)
 {
     if (!h) return fail(HS_EINVAL, "heat_step: NULL handle");
     if (n_steps < 0) return fail(HS_EINVAL, "heat_step: n_steps = %lld < 0", (long long)n_steps);
+    if (h->tdepth > 1) {
+        // passes of tdepth steps, then the remainder in the largest built depths
+        int64_t left = n_steps;
+        static const int depths[] = {8, 6, 4, 3, 2, 1};
+        for (int L : depths) {
+            if (L > h->tdepth) continue;
+            for (; left >= L; left -= L) {
+                const int rc = tb_pass(h, L);
+                if (rc != HS_OK) return rc;
+            }
+        }
+        return HS_OK;
+    }
     for (int64_t m = 0; m < n_steps; ++m) {
         int rc;
         if (h->flags & HS_SCHED_FULL) {
@@ -656,6 +666,7 @@ int heat_step(hs_heat_t h, int64_t n_steps)
         if (rc != HS_OK) return rc;
         h->cur = 1 - h->cur;
         h->steps += 1;
+        h->fxseq += 1;
     }
     return HS_OK;
 }
@@ -670,13 +681,18 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device)
         // all of it, and its boundary layer stays zero.
         k_fx_decode<<<conv_blocks(h->g), 256, 0, h->stream>>>(
             (const long long*)h->buf[h->cur], (double*)h->buf[1 - h->cur], h->g, h->fx,
-            (int)(h->steps % 3));
+            (int)(h->fxseq % 3));
         HS_CHECK_LAUNCH("heat_read: fixed-point decode kernel");
         src = h->buf[1 - h->cur];
     }
     int rc = copy_interior(h, src, nullptr, dst, kind);
     if (rc != HS_OK) return rc;
     HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
+    int err = 0;
+    HS_TRY_CUDA(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost), "heat_read: error word");
+    if (err)
+        return fail(HS_ETIMEOUT, "heat_read: a bounded wait inside the temporally blocked kernel "
+                                 "ran out; the field is not valid");
     if (h->arith == A_FX64) {
         FxState st;
         HS_TRY_CUDA(cudaMemcpy(&st, h->fx, sizeof(st), cudaMemcpyDeviceToHost), "heat_read: state");
@@ -694,6 +710,13 @@ int heat_steps_done(hs_heat_t h, int64_t* steps)
     return HS_OK;
 }
 
+int heat_get_tdepth(hs_heat_t h, int32_t* tdepth)
+{
+    if (!h || !tdepth) return fail(HS_EINVAL, "heat_get_tdepth: NULL argument");
+    *tdepth = h->tdepth;
+    return HS_OK;
+}
+
 int heat_destroy(hs_heat_t h)
 {
     if (!h) return HS_OK;
@@ -705,6 +728,7 @@ int heat_destroy(hs_heat_t h)
     for (int b = 0; b < 2; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->fx) cudaFree(h->fx);
+    if (h->err) cudaFree(h->err);
     delete h;
     return rc;
 }

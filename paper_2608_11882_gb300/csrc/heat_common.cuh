@@ -1,0 +1,223 @@
+// Definitions shared by the heat kernels: the padded field geometry, the
+// FIXED64 scale bookkeeping, and the point update in each arithmetic.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace hcg {
+
+struct HeatGeom {
+    int32_t nx, ny, nz;
+    int32_t lead;    // element offset of interior x = 0 within a row
+    int64_t pitch;   // elements per row
+    int64_t plane;   // elements per plane = pitch * (ny + 2)
+    int64_t total;   // elements per buffer = plane * (nz + 2)
+    int32_t elem;    // bytes per element
+    int32_t pad;
+    __host__ __device__ __forceinline__ int64_t at(int i, int j, int k) const
+    {
+        return (int64_t)(k + 1) * plane + (int64_t)(j + 1) * pitch + lead + i;
+    }
+};
+
+inline HeatGeom make_geom(int nx, int ny, int nz, size_t elem)
+{
+    HeatGeom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.lead = (int32_t)(32 / elem);
+    const int64_t row_quant = (int64_t)(128 / elem);
+    g.pitch = ((int64_t)g.lead + nx + 1 + row_quant - 1) / row_quant * row_quant;
+    g.plane = g.pitch * (ny + 2);
+    g.total = g.plane * (nz + 2);
+    g.elem = (int32_t)elem;
+    g.pad = 0;
+    return g;
+}
+
+// Fixed-point bookkeeping of a FIXED64 field (device memory).  The field at
+// step m has scale E_m (U = round(u 2^E_m)) and integer max M_m = max|U|, kept
+// in slot m % 3.  The kernels of step m read slot m % 3, write slot (m+1) % 3
+// (atomic max of their outputs, and E_{m+1}) and clear slot (m+2) % 3, which no
+// kernel of step m reads -- so no kernel ever races on a slot.
+struct FxSlot {
+    unsigned long long maxU;   // max |U| of the field
+    int32_t E;                 // scale exponent of the field
+    int32_t pad;
+};
+
+struct FxState {
+    unsigned long long maxabs_bits;   // bit pattern of max|u0| (non-negative doubles order like integers)
+    int32_t nonfinite;                // 1 if the uploaded field held NaN or Inf
+    int32_t pad;
+    FxSlot slot[3];
+};
+
+// Left shift that keeps a shrinking field near full precision: the largest k
+// with M 2^k < 2^57, so |S - 6U| 2^k <= 12 M 2^k < 2^61 never overflows.
+__device__ __forceinline__ int fx_shift(const FxState* fx, int m3)
+{
+    const unsigned long long M = fx->slot[m3].maxU;
+    if (M == 0) return 0;
+    const int k = 57 - (64 - __clzll((long long)M));
+    return k > 0 ? k : 0;
+}
+
+__device__ __forceinline__ unsigned long long fx_abs(long long v)
+{
+    return v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+}
+
+// Block-wide max of the outputs into slot (m3+1) % 3; the grid leader also
+// records E_{m+1} = E_m + k and clears slot (m3+2) % 3 for the next step.
+template <int NT>
+__device__ __forceinline__ void fx_finish(unsigned long long m, FxState* fx, int m3, int k,
+                                          bool leader)
+{
+    __shared__ unsigned long long wmax[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < NT / 32; ++w) b = wmax[w] > b ? wmax[w] : b;
+        atomicMax(&fx->slot[(m3 + 1) % 3].maxU, b);
+        if (leader) {
+            fx->slot[(m3 + 1) % 3].E = fx->slot[m3].E + k;
+            fx->slot[(m3 + 2) % 3].maxU = 0;
+        }
+    }
+}
+
+// ---- the point update -------------------------------------------------------
+// k is the FIXED64 rescaling shift of this step (unused by the floating types).
+template <typename T, bool EXACT>
+struct Point;
+
+template <bool EXACT>
+struct Point<double, EXACT> {
+    // Default: the six-neighbour sum in the written order, then two fused
+    // multiply-adds t = s - 6u, u' = u + r t (7 FP64 instructions per point).
+    // Exact: one rounding per operation in the written order, no fusion.
+    static __device__ __forceinline__ double update(double c, double xm, double xp, double ym,
+                                                    double yp, double zm, double zp, double r, int)
+    {
+        const double s = __dadd_rn(__dadd_rn(__dadd_rn(xm, xp), __dadd_rn(ym, yp)),
+                                   __dadd_rn(zm, zp));
+        if (EXACT) return __dadd_rn(c, __dmul_rn(r, __dsub_rn(s, __dmul_rn(6.0, c))));
+        return __fma_rn(r, __fma_rn(-6.0, c, s), c);
+    }
+};
+
+template <bool EXACT>
+struct Point<float, EXACT> {
+    static __device__ __forceinline__ float update(float c, float xm, float xp, float ym, float yp,
+                                                   float zm, float zp, float r, int)
+    {
+        const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)),
+                                  __fadd_rn(zm, zp));
+        if (EXACT) return __fadd_rn(c, __fmul_rn(r, __fsub_rn(s, __fmul_rn(6.0f, c))));
+        return __fmaf_rn(r, __fmaf_rn(-6.0f, c, s), c);
+    }
+};
+
+template <bool EXACT>
+struct Point<long long, EXACT> {
+    // FIXED64: R = r 2^64 (a non-negative int64: r <= 1/6 < 1/2).  S - 6U is
+    // exact; it and U are moved to the new scale by the exact shift k; then
+    // t R / 2^64 is rounded to nearest (ties up): floor((t R + 2^63) / 2^64)
+    // = high word of t R plus the top bit of its low word.
+    static __device__ __forceinline__ long long update(long long c, long long xm, long long xp,
+                                                       long long ym, long long yp, long long zm,
+                                                       long long zp, long long R, int k)
+    {
+        const long long s = ((xm + xp) + (ym + yp)) + (zm + zp);
+        const long long t = (long long)((unsigned long long)(s - 6 * c) << k);
+        const long long cs = (long long)((unsigned long long)c << k);
+        const long long hi = __mul64hi(t, R);
+        const unsigned long long lo = (unsigned long long)t * (unsigned long long)R;
+        return cs + hi + (long long)(lo >> 63);
+    }
+};
+
+template <typename T>
+constexpr bool kIsFixed = std::is_same<T, long long>::value;
+
+// Arithmetic of a heat handle.
+enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3 };
+
+// One launch of the temporally blocked kernel (heat_tb.cu).
+struct TbCall {
+    int arith;
+    int L;                   // steps in this pass
+    int kc;                  // k-planes per block
+    const CUtensorMap* map;  // tensor map of the source buffer
+    void* dst;
+    const HeatGeom* g;
+    double r;
+    long long R;             // FIXED64: r 2^64
+    FxState* fx;
+    int m3;
+    int* err;                // device error word (1 = a bounded wait ran out)
+    cudaStream_t stream;
+};
+
+template <typename T>
+inline T tb_param(const TbCall& c)
+{
+    if constexpr (std::is_same<T, long long>::value)
+        return c.R;
+    else
+        return (T)c.r;
+}
+
+int tb_launch(const TbCall& c);
+
+// One launch of the streaming Interior kernel (heat_stream.cu): one step over
+// the k-planes [kbeg, kend).
+struct StreamCall {
+    int arith;
+    int kbeg, kend;          // planes to update
+    int kc;                  // k-planes per block
+    const CUtensorMap* map;  // stream tensor map of the source buffer
+    void* dst;
+    const HeatGeom* g;
+    double r;
+    long long R;
+    FxState* fx;
+    int m3;
+    int* err;
+    cudaStream_t stream;
+};
+
+template <typename T>
+inline T stream_param(const StreamCall& c)
+{
+    if constexpr (std::is_same<T, long long>::value)
+        return c.R;
+    else
+        return (T)c.r;
+}
+
+int stream_launch(const StreamCall& c);
+// TMA box (elements x rows) the streaming kernel loads for an arithmetic.
+int stream_box(int arith, uint32_t* box_x, uint32_t* box_y);
+// Rows of the streaming kernel's tile (its tile is 32 x kStreamRows columns).
+constexpr int kStreamRowsHost = 16;
+
+// Rows of the temporally blocked kernel's thread block (its tile is
+// (32 - 2L) x (kTbRows - 2L) columns).
+constexpr int kTbRows = 32;
+
+}  // namespace hcg

@@ -1,0 +1,279 @@
+// Streaming Interior kernel: one step of the update of Section 4, Eq. 4 over
+// a range of k-planes, with the planes staged in shared memory by TMA.
+//
+// A block of 32 x RY threads owns a (32 V) x RY column tile -- every thread
+// computes V consecutive x points (4 floats, or 2 doubles / int64s, one
+// 16-byte vector) -- and a chunk of k-planes.  Each plane of the tile plus a
+// one-point halo ((RY + 2) rows of BW elements) arrives by TMA into a ring of
+// NST stages, up to NST - 2 planes ahead of use, so each SM keeps tens of
+// kilobytes of loads in flight.  A thread keeps its own values at k-1 and k in
+// registers, reads the values at k+1 and the rows at y-1 and y+1 as 16-byte
+// vectors from shared memory, and the two x neighbours beyond its vector as
+// scalars; the result goes out as one 16-byte store.  The per-point arithmetic is that of the other heat kernels,
+// so results match them bit for bit.
+//
+// Every mbarrier wait is bounded: one that runs out sets the handle's device
+// error word (HS_ETIMEOUT at the next heat_read), waits (bounded) for the
+// block's loads in flight and ends the block.
+#include <cuda.h>
+
+#include "heat_common.cuh"
+#include "tma.cuh"
+
+namespace hcg {
+
+constexpr uint32_t kStreamMaxPolls = 1u << 22;
+
+// V consecutive x points per thread, moved as one 16-byte vector.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int V = 4;
+    using type = float4;
+};
+template <>
+struct Vec<double> {
+    static constexpr int V = 2;
+    using type = double2;
+};
+template <>
+struct Vec<long long> {
+    static constexpr int V = 2;
+    using type = longlong2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld_vec(const T* p, T (&o)[Vec<T>::V])
+{
+    const typename Vec<T>::type v = *reinterpret_cast<const typename Vec<T>::type*>(p);
+    if constexpr (Vec<T>::V == 4) {
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    } else {
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_vec(T* p, const T (&o)[Vec<T>::V])
+{
+    typename Vec<T>::type v;
+    if constexpr (Vec<T>::V == 4) {
+        v.x = o[0];
+        v.y = o[1];
+        v.z = o[2];
+        v.w = o[3];
+    } else {
+        v.x = o[0];
+        v.y = o[1];
+    }
+    *reinterpret_cast<typename Vec<T>::type*>(p) = v;
+}
+
+// Tile geometry.  Interior rows start 32 bytes into a padded row (lead *
+// sizeof(T) = 32) and a tile is 32 V points = 512 bytes wide, so a box that
+// starts D = 16 bytes before the tile's first point starts 16-byte aligned
+// (as TMA requires), and the tile's first point -- hence every thread's
+// vector -- sits 16-byte aligned in the stage row.  The row is wide enough
+// for the halo point on each side and rounded up to 16 bytes.
+template <typename T>
+struct StreamShape {
+    static constexpr int V = Vec<T>::V;
+    static constexpr int A = 16 / (int)sizeof(T);                // elements per 16 bytes
+    static constexpr int D = A;                                  // offset of the tile's first point
+    static constexpr int BW = (D + 32 * V + 1 + A - 1) / A * A;  // stage row width, 16-byte multiple
+};
+
+template <typename T, bool EXACT, int RY, int NST>
+__global__ void __launch_bounds__(32 * RY)
+    k_heat_stream(const __grid_constant__ CUtensorMap map, T* __restrict__ dst, HeatGeom g, T r,
+                  int kbeg, int kend, int kc, FxState* fx, int m3, int* err)
+{
+    using S = StreamShape<T>;
+    constexpr int V = S::V;
+    constexpr int BW = S::BW;
+    constexpr int ROWS = RY + 2;
+    constexpr uint32_t BOX_BYTES = ROWS * BW * (uint32_t)sizeof(T);
+    constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(T));   // 128-byte aligned slots
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* stage = reinterpret_cast<T*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + NST * STAGE);
+    __shared__ int s_abort;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * RY;
+    const int X = x0 + V * tx, Y = y0 + ty;
+    const int kb = kbeg + blockIdx.z * kc;
+    const int ke = min(kb + kc, kend);
+    const int xs = g.lead + x0 - S::D;                 // padded x of the box (16-byte aligned)
+    const int own = (ty + 1) * BW + S::D + V * tx;     // this thread's first point in a stage
+    const bool row_ok = (Y < g.ny);
+    const int nvalid = row_ok ? min(V, g.nx - X) : 0;  // points of this thread inside the box
+    const int p_first = kb - 1, p_last = ke;           // planes staged: kb-1 .. ke
+
+    int issued = p_first - 1;
+    int drain_from = p_first;
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < NST && p_first + s <= p_last; ++s) {
+            mbar_arrive_expect_tx(&bars[s], BOX_BYTES);
+            tma_load_3d(stage + s * STAGE, &map, xs, y0, p_first + s + 1, &bars[s]);
+            issued = p_first + s;
+        }
+    }
+    int ks = 0;
+    if constexpr (kIsFixed<T>) ks = fx_shift(fx, m3);
+    unsigned long long mx = 0;
+
+    T below[V], cur[V], above[V], ym[V], yp[V], v[V];
+    int s_cur = 0, n_cur = 0;
+    bool ok = mbar_wait_bounded(&bars[0], 0, kStreamMaxPolls);
+    ld_vec(stage + own, below);
+    int s_nxt = 1 % NST, n_nxt = 1 / NST;
+    ok = ok && mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u, kStreamMaxPolls);
+    ld_vec(stage + s_nxt * STAGE + own, cur);
+    s_cur = s_nxt;
+    n_cur = n_nxt;
+    if (!ok) {
+        atomicExch(err, 1);
+        s_abort = 1;
+    }
+    __syncthreads();
+
+    T* out = dst + g.at(X < g.nx ? X : 0, row_ok ? Y : 0, kb);   // only used when nvalid > 0
+    int k = kb;
+    if (!s_abort) {
+        for (; k < ke; ++k) {
+            s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
+            n_nxt = s_nxt == 0 ? n_cur + 1 : n_cur;
+            if (!mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u, kStreamMaxPolls)) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            const T* pl = stage + s_cur * STAGE + own;
+            ld_vec(stage + s_nxt * STAGE + own, above);
+            ld_vec(pl - BW, ym);
+            ld_vec(pl + BW, yp);
+            const T left = pl[-1], right = pl[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T xm = i == 0 ? left : cur[i - 1];
+                const T xp = i == V - 1 ? right : cur[i + 1];
+                v[i] = Point<T, EXACT>::update(cur[i], xm, xp, ym[i], yp[i], below[i], above[i], r, ks);
+            }
+            if (nvalid == V) {
+                st_vec(out, v);
+            } else {
+                for (int i = 0; i < nvalid; ++i) out[i] = v[i];
+            }
+            if constexpr (kIsFixed<T>) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const unsigned long long a = i < nvalid ? fx_abs(v[i]) : 0ull;
+                    mx = a > mx ? a : mx;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                below[i] = cur[i];
+                cur[i] = above[i];
+            }
+            out += g.plane;
+            __syncthreads();
+            if (s_abort) {
+                drain_from = k + 1;
+                break;
+            }
+            if (tid == 0 && issued < p_last) {
+                const int slot = s_cur == 0 ? NST - 1 : s_cur - 1;   // plane k-1's slot is free
+                const int pn = issued + 1;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[slot], BOX_BYTES);
+                tma_load_3d(stage + slot * STAGE, &map, xs, y0, pn + 1, &bars[slot]);
+                issued = pn;
+            }
+            s_cur = s_nxt;
+            n_cur = n_nxt;
+        }
+    }
+    if (s_abort) {
+        if (tid == 0) {
+            for (int p = drain_from; p <= issued; ++p) {
+                const int i = p - p_first;
+                (void)mbar_wait_bounded(&bars[i % NST], (uint32_t)(i / NST) & 1u, kStreamMaxPolls);
+            }
+        }
+        return;
+    }
+    if constexpr (kIsFixed<T>)
+        fx_finish<32 * RY>(mx, fx, m3, ks, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+}
+
+template <typename T>
+constexpr int stream_rows()
+{
+    return 16;
+}
+
+template <typename T, bool EXACT>
+int stream_launch_t(const StreamCall& c)
+{
+    constexpr int RY = stream_rows<T>();
+    constexpr int NST = 6;
+    constexpr size_t box_bytes = sizeof(T) * (size_t)(RY + 2) * StreamShape<T>::BW;
+    constexpr size_t smem = NST * ((box_bytes + 127) / 128 * 128) + NST * sizeof(uint64_t);
+    auto kern = k_heat_stream<T, EXACT, RY, NST>;
+    static bool configured = false;
+    if (!configured) {
+        HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "heat: streaming kernel smem attribute");
+        configured = true;
+    }
+    const HeatGeom& g = *c.g;
+    const int planes = c.kend - c.kbeg;
+    if (planes <= 0) return HS_OK;
+    constexpr int TXW = 32 * Vec<T>::V;
+    dim3 grid((g.nx + TXW - 1) / TXW, (g.ny + RY - 1) / RY, (planes + c.kc - 1) / c.kc);
+    dim3 block(32, RY, 1);
+    kern<<<grid, block, smem, c.stream>>>(*c.map, (T*)c.dst, g, stream_param<T>(c), c.kbeg, c.kend,
+                                          c.kc, c.fx, c.m3, c.err);
+    HS_CHECK_LAUNCH("heat streaming Interior kernel");
+    return HS_OK;
+}
+
+int stream_launch(const StreamCall& c)
+{
+    switch (c.arith) {
+    case A_F64: return stream_launch_t<double, false>(c);
+    case A_F64_EXACT: return stream_launch_t<double, true>(c);
+    case A_F32: return stream_launch_t<float, false>(c);
+    case A_FX64: return stream_launch_t<long long, false>(c);
+    }
+    return fail(HS_EINVAL, "heat: unknown arithmetic");
+}
+
+int stream_box(int arith, uint32_t* box_x, uint32_t* box_y)
+{
+    switch (arith) {
+    case A_F32:
+        *box_x = StreamShape<float>::BW;
+        *box_y = stream_rows<float>() + 2;
+        return 0;
+    default:
+        *box_x = StreamShape<double>::BW;
+        *box_y = stream_rows<double>() + 2;
+        return 0;
+    }
+}
+
+}  // namespace hcg

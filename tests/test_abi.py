@@ -36,11 +36,11 @@ def test_version_and_error_string_without_gpu():
     assert nat.lib.hs_version() >= 100
     assert isinstance(nat.last_error(), str)
     # argument validation happens before any CUDA call
-    desc = nat.hs_heat_desc(nx=0, ny=1, nz=1, r=0.1, flags=0, dtype=0, reserved0=0, stream=None)
+    desc = nat.hs_heat_desc(nx=0, ny=1, nz=1, r=0.1, flags=0, dtype=0, tdepth=0, stream=None)
     h = ctypes.c_void_p()
     assert nat.lib.heat_create(ctypes.byref(h), ctypes.byref(desc)) == nat.HS_EINVAL
     assert "interior" in nat.last_error()
-    desc = nat.hs_heat_desc(nx=4, ny=4, nz=4, r=0.2, flags=0, dtype=0, reserved0=0, stream=None)
+    desc = nat.hs_heat_desc(nx=4, ny=4, nz=4, r=0.2, flags=0, dtype=0, tdepth=0, stream=None)
     assert nat.lib.heat_create(ctypes.byref(h), ctypes.byref(desc)) == nat.HS_EUNSTABLE
     size = ctypes.c_size_t()
     desc.r = 0.1

@@ -17,9 +17,9 @@ def pkg():
     return lib()
 
 
-def run_fx(pkg, u0, r, steps, extra=0):
+def run_fx(pkg, u0, r, steps, extra=0, tdepth=0):
     nz, ny, nx = u0.shape
-    with pkg.Heat(nx, ny, nz, r, flags=pkg.HS_FIXED64 | extra) as h:
+    with pkg.Heat(nx, ny, nz, r, flags=pkg.HS_FIXED64 | extra, tdepth=tdepth) as h:
         h.upload(np.ascontiguousarray(u0, dtype=np.float64))
         h.step(steps)
         return h.read()
@@ -42,7 +42,8 @@ def test_odd_shapes(pkg, shape):
 
 def test_interior_plus_boundary_equals_full_step_kernel(pkg):
     u0 = heat_u0_single_mode(45, 38, 29, seed=9)
-    assert np.array_equal(run_fx(pkg, u0, 0.12, 17), run_fx(pkg, u0, 0.12, 17, pkg.HS_SCHED_FULL))
+    assert np.array_equal(run_fx(pkg, u0, 0.12, 17, tdepth=1),
+                          run_fx(pkg, u0, 0.12, 17, pkg.HS_SCHED_FULL))
 
 
 def test_sine_mode_closer_to_exact_decay_than_fp64(pkg):
@@ -107,3 +108,10 @@ def test_errors(pkg):
         with pytest.raises(pkg.HeatCGError) as e:
             h.read()
         assert e.value.code == HS_ERANGE
+
+
+@pytest.mark.parametrize("tdepth", [1, 2, 3, 4, 6, 8])
+def test_temporal_depths_against_oracle(pkg, tdepth):
+    u0 = heat_u0_single_mode(37, 29, 41, seed=6)
+    ref = oracle.heat_run(u0, 0.13, 29)
+    assert rel_max_err(run_fx(pkg, u0, 0.13, 29, tdepth=tdepth), ref) <= F64_REL

@@ -1,0 +1,64 @@
+"""Temporal blocking (tdepth L >= 2: L steps of Section 4's update per pass
+over HBM) against stepping one step at a time, and against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_util import F64_REL, f32_bound, lib, rel_max_err
+from workloads import heat_u0_single_mode
+
+pytestmark = pytest.mark.gpu
+
+DEPTHS = [2, 3, 4, 6, 8]
+SHAPES = [(1, 1, 1), (2, 3, 5), (33, 9, 17), (70, 3, 40), (40, 65, 31), (5, 100, 90)]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    oracle.build()
+    return lib()
+
+
+def run(pkg, u0, r, steps, dtype="f64", flags=0, tdepth=0):
+    nz, ny, nx = u0.shape
+    with pkg.Heat(nx, ny, nz, r, dtype=dtype, flags=flags, tdepth=tdepth) as h:
+        h.upload(np.ascontiguousarray(u0, dtype=h.np_dtype))
+        h.step(steps)
+        assert h.steps_done == steps
+        return h.read()
+
+
+@pytest.mark.parametrize("tdepth", DEPTHS)
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_blocked_equals_stepwise_bitwise(pkg, tdepth, shape, dtype):
+    """Same per-point arithmetic, so the blocked pass reproduces one-step
+    stepping bit for bit; 19 steps leaves a remainder for every depth."""
+    rng = np.random.default_rng(sum(shape) + tdepth)
+    u0 = rng.uniform(-1, 1, size=shape)
+    a = run(pkg, u0, 0.16, 19, dtype=dtype, tdepth=1)
+    b = run(pkg, u0, 0.16, 19, dtype=dtype, tdepth=tdepth)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tdepth", DEPTHS)
+def test_blocked_exact_rounding_equals_oracle_bitwise(pkg, tdepth):
+    u0 = heat_u0_single_mode(45, 38, 29, seed=12)
+    ref = oracle.heat_run(u0, 0.1, 25)
+    assert np.array_equal(run(pkg, u0, 0.1, 25, flags=pkg.HS_EXACT_ROUNDING, tdepth=tdepth), ref)
+
+
+def test_small_workload_blocked(pkg):
+    u0 = heat_u0_single_mode(64, 64, 64)
+    ref = oracle.heat_run(u0, 0.1, 100, threads=oracle.max_threads())
+    assert rel_max_err(run(pkg, u0, 0.1, 100, tdepth=4), ref) <= F64_REL
+    got32 = run(pkg, u0.astype(np.float32), 0.1, 100, dtype="f32", tdepth=8)
+    assert float(np.max(np.abs(got32 - ref))) <= f32_bound(100, float(np.max(np.abs(u0))))
+
+
+def test_bad_tdepth(pkg):
+    for bad in (5, 7, 9, -1):
+        with pytest.raises(pkg.HeatCGError):
+            pkg.Heat(8, 8, 8, 0.1, tdepth=bad)
+    with pytest.raises(pkg.HeatCGError):
+        pkg.Heat(8, 8, 8, 0.1, flags=pkg.HS_SCHED_FULL, tdepth=2)
