@@ -250,6 +250,8 @@ struct hs_heat {
     int kc_tb;         // k-planes per block of the temporally blocked kernel
     CUtensorMap maps[2];   // TMA maps of the two buffers (temporal blocking)
     CUtensorMap smaps[2];  // TMA maps of the two buffers (streaming Interior kernel)
+    uint32_t tbox[2];      // box of maps[]
+    uint32_t sbox[2];      // box of smaps[]
     int kc_stream;         // k-planes per block of the streaming Interior kernel
 };
 
@@ -279,9 +281,8 @@ int check_desc(const hs_heat_desc* d)
         if (d->flags & HS_ALLOW_UNSTABLE)
             return fail(HS_EINVAL, "heat: HS_FIXED64 needs r <= 1/6 (a growing field would overflow)");
     }
-    if (d->tdepth != 0 && d->tdepth != 1 && d->tdepth != 2 && d->tdepth != 3 && d->tdepth != 4 &&
-        d->tdepth != 6 && d->tdepth != 8)
-        return fail(HS_EINVAL, "heat: tdepth %d not in {0, 1, 2, 3, 4, 6, 8}", d->tdepth);
+    if (d->tdepth < 0 || d->tdepth > 4)
+        return fail(HS_EINVAL, "heat: tdepth %d not in {0, 1, 2, 3, 4}", d->tdepth);
     if ((d->flags & HS_SCHED_FULL) && d->tdepth > 1)
         return fail(HS_EINVAL, "heat: HS_SCHED_FULL runs one step per pass (tdepth 0 or 1)");
     // Three-dimensional stability of the explicit update: r <= 1/6.
@@ -366,13 +367,19 @@ int launch_stream_interior(hs_heat* h)
     c.m3 = (int)(h->fxseq % 3);
     c.err = h->err;
     c.stream = h->stream;
+    c.box[0] = h->sbox[0];
+    c.box[1] = h->sbox[1];
     return stream_launch(c);
 }
 
 template <typename T, bool EXACT>
 int launch_part(hs_heat* h, Part p, T param)
 {
-    if (p == P_INTERIOR) return launch_stream_interior(h);
+    // FP64 is bound by the FP64 pipe, where the register z-march issues the
+    // fewest extra instructions; the HBM-bound arithmetics stream through TMA.
+    if (p == P_INTERIOR)
+        return std::is_same<T, double>::value ? launch_interior_t<T, EXACT>(h, param)
+                                              : launch_stream_interior(h);
     if (p == P_BOUNDARY) return launch_boundary_t<T, EXACT>(h, param);
     return launch_full_t<T, EXACT>(h, param);
 }
@@ -439,6 +446,8 @@ int tb_pass(hs_heat* h, int L)
     c.m3 = (int)(h->fxseq % 3);
     c.err = h->err;
     c.stream = h->stream;
+    c.box[0] = h->tbox[0];
+    c.box[1] = h->tbox[1];
     int rc = tb_launch(c);
     if (rc != HS_OK) return rc;
     h->cur = 1 - h->cur;
@@ -553,6 +562,8 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
         uint32_t bx = 0, by = 0;
         stream_box(h->arith, &bx, &by);
+        h->sbox[0] = bx;
+        h->sbox[1] = by;
         for (int b = 0; b < 2; ++b) {
             const int e = encode_field_map(&h->smaps[b], h->buf[b], dt, h->elem, (uint64_t)h->g.pitch,
                                            (uint64_t)(h->g.ny + 2), (uint64_t)(h->g.nz + 2), bx, by);
@@ -568,11 +579,14 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
         const CUtensorMapDataType dt = h->arith == A_FX64   ? CU_TENSOR_MAP_DATA_TYPE_INT64
                                        : h->dtype == HS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-        const uint32_t box_x = 32 + (uint32_t)(16 / h->elem);
+        uint32_t box_x = 0, box_y = 0;
+        tb_box(h->arith, &box_x, &box_y);
+        h->tbox[0] = box_x;
+        h->tbox[1] = box_y;
         for (int b = 0; b < 2; ++b) {
             const int e = encode_field_map(&h->maps[b], h->buf[b], dt, h->elem, (uint64_t)h->g.pitch,
                                            (uint64_t)(h->g.ny + 2), (uint64_t)(h->g.nz + 2), box_x,
-                                           (uint32_t)kTbRows);
+                                           box_y);
             if (e != 0) {
                 rc = cuda_fail((cudaError_t)e, "heat_create: TMA tensor map");
                 heat_destroy(h);
@@ -645,13 +659,21 @@ int heat_step(hs_heat_t h, int64_t n_steps)
     if (h->tdepth > 1) {
         // passes of tdepth steps, then the remainder in the largest built depths
         int64_t left = n_steps;
-        static const int depths[] = {8, 6, 4, 3, 2, 1};
+        static const int depths[] = {4, 3, 2};
         for (int L : depths) {
             if (L > h->tdepth) continue;
             for (; left >= L; left -= L) {
                 const int rc = tb_pass(h, L);
                 if (rc != HS_OK) return rc;
             }
+        }
+        for (; left > 0; --left) {   // a last single step: Boundary + Interior
+            int rc = do_part(h, P_BOUNDARY);
+            if (rc == HS_OK) rc = do_part(h, P_INTERIOR);
+            if (rc != HS_OK) return rc;
+            h->cur = 1 - h->cur;
+            h->steps += 1;
+            h->fxseq += 1;
         }
         return HS_OK;
     }

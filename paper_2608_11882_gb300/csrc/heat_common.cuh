@@ -154,6 +154,56 @@ struct Point<long long, EXACT> {
 template <typename T>
 constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
+// V consecutive x points per thread, moved as one 16-byte vector.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int V = 4;
+    using type = float4;
+};
+template <>
+struct Vec<double> {
+    static constexpr int V = 2;
+    using type = double2;
+};
+template <>
+struct Vec<long long> {
+    static constexpr int V = 2;
+    using type = longlong2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld_vec(const T* p, T (&o)[Vec<T>::V])
+{
+    const typename Vec<T>::type v = *reinterpret_cast<const typename Vec<T>::type*>(p);
+    if constexpr (Vec<T>::V == 4) {
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    } else {
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_vec(T* p, const T (&o)[Vec<T>::V])
+{
+    typename Vec<T>::type v;
+    if constexpr (Vec<T>::V == 4) {
+        v.x = o[0];
+        v.y = o[1];
+        v.z = o[2];
+        v.w = o[3];
+    } else {
+        v.x = o[0];
+        v.y = o[1];
+    }
+    *reinterpret_cast<typename Vec<T>::type*>(p) = v;
+}
+
 // Arithmetic of a heat handle.
 enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3 };
 
@@ -171,6 +221,7 @@ struct TbCall {
     int m3;
     int* err;                // device error word (1 = a bounded wait ran out)
     cudaStream_t stream;
+    uint32_t box[2];         // box the map was encoded with (checked against the kernel's)
 };
 
 template <typename T>
@@ -183,6 +234,8 @@ inline T tb_param(const TbCall& c)
 }
 
 int tb_launch(const TbCall& c);
+// TMA box (elements x rows) the temporally blocked kernel loads for an arithmetic.
+int tb_box(int arith, uint32_t* box_x, uint32_t* box_y);
 
 // One launch of the streaming Interior kernel (heat_stream.cu): one step over
 // the k-planes [kbeg, kend).
@@ -199,6 +252,7 @@ struct StreamCall {
     int m3;
     int* err;
     cudaStream_t stream;
+    uint32_t box[2];         // box the map was encoded with (checked against the kernel's)
 };
 
 template <typename T>

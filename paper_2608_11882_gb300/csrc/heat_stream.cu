@@ -22,57 +22,6 @@
 
 namespace hcg {
 
-constexpr uint32_t kStreamMaxPolls = 1u << 22;
-
-// V consecutive x points per thread, moved as one 16-byte vector.
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-    static constexpr int V = 4;
-    using type = float4;
-};
-template <>
-struct Vec<double> {
-    static constexpr int V = 2;
-    using type = double2;
-};
-template <>
-struct Vec<long long> {
-    static constexpr int V = 2;
-    using type = longlong2;
-};
-
-template <typename T>
-__device__ __forceinline__ void ld_vec(const T* p, T (&o)[Vec<T>::V])
-{
-    const typename Vec<T>::type v = *reinterpret_cast<const typename Vec<T>::type*>(p);
-    if constexpr (Vec<T>::V == 4) {
-        o[0] = v.x;
-        o[1] = v.y;
-        o[2] = v.z;
-        o[3] = v.w;
-    } else {
-        o[0] = v.x;
-        o[1] = v.y;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void st_vec(T* p, const T (&o)[Vec<T>::V])
-{
-    typename Vec<T>::type v;
-    if constexpr (Vec<T>::V == 4) {
-        v.x = o[0];
-        v.y = o[1];
-        v.z = o[2];
-        v.w = o[3];
-    } else {
-        v.x = o[0];
-        v.y = o[1];
-    }
-    *reinterpret_cast<typename Vec<T>::type*>(p) = v;
-}
 
 // Tile geometry.  Interior rows start 32 bytes into a padded row (lead *
 // sizeof(T) = 32) and a tile is 32 V points = 512 bytes wide, so a box that
@@ -119,11 +68,13 @@ __global__ void __launch_bounds__(32 * RY)
     int issued = p_first - 1;
     int drain_from = p_first;
     if (tid == 0) {
-        s_abort = 0;
+        // a block that starts after another one gave up does no work at all
+        s_abort = *(volatile int*)err;
         for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (s_abort) return;
     if (tid == 0) {
         for (int s = 0; s < NST && p_first + s <= p_last; ++s) {
             mbar_arrive_expect_tx(&bars[s], BOX_BYTES);
@@ -137,10 +88,10 @@ __global__ void __launch_bounds__(32 * RY)
 
     T below[V], cur[V], above[V], ym[V], yp[V], v[V];
     int s_cur = 0, n_cur = 0;
-    bool ok = mbar_wait_bounded(&bars[0], 0, kStreamMaxPolls);
+    bool ok = mbar_wait_bounded(&bars[0], 0);
     ld_vec(stage + own, below);
     int s_nxt = 1 % NST, n_nxt = 1 / NST;
-    ok = ok && mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u, kStreamMaxPolls);
+    ok = ok && mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u);
     ld_vec(stage + s_nxt * STAGE + own, cur);
     s_cur = s_nxt;
     n_cur = n_nxt;
@@ -156,7 +107,7 @@ __global__ void __launch_bounds__(32 * RY)
         for (; k < ke; ++k) {
             s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
             n_nxt = s_nxt == 0 ? n_cur + 1 : n_cur;
-            if (!mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u, kStreamMaxPolls)) {
+            if (!mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u)) {
                 atomicExch(err, 1);
                 s_abort = 1;
             }
@@ -208,9 +159,10 @@ __global__ void __launch_bounds__(32 * RY)
     }
     if (s_abort) {
         if (tid == 0) {
+            const long long t0 = clock64();   // one time budget for the whole drain
             for (int p = drain_from; p <= issued; ++p) {
                 const int i = p - p_first;
-                (void)mbar_wait_bounded(&bars[i % NST], (uint32_t)(i / NST) & 1u, kStreamMaxPolls);
+                (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
             }
         }
         return;
@@ -232,6 +184,9 @@ int stream_launch_t(const StreamCall& c)
     constexpr int NST = 6;
     constexpr size_t box_bytes = sizeof(T) * (size_t)(RY + 2) * StreamShape<T>::BW;
     constexpr size_t smem = NST * ((box_bytes + 127) / 128 * 128) + NST * sizeof(uint64_t);
+    if (c.box[0] != (uint32_t)StreamShape<T>::BW || c.box[1] != (uint32_t)(RY + 2))
+        return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
+                    c.box[1], StreamShape<T>::BW, RY + 2);
     auto kern = k_heat_stream<T, EXACT, RY, NST>;
     static bool configured = false;
     if (!configured) {

@@ -1,9 +1,10 @@
 // Temporally blocked heat kernel: L steps of the update of Section 4, Eq. 4
 // per pass over HBM.
 //
-// A block owns an output tile of TX x TY = (32 - 2L) x (RY - 2L) columns and
-// a chunk of k-planes, and streams up the chunk.  Its 32 x RY threads each own
-// one (x, y) position of the tile plus an L-wide halo.  Level-0 planes (the
+// A block owns an output tile of TX x TY columns and a chunk of k-planes, and
+// streams up the chunk.  Its 32 x RY threads each own one 16-byte vector of x
+// points (4 floats, or 2 doubles / int64s) in one row of the tile plus its
+// halo.  Level-0 planes (the
 // field in HBM) arrive by TMA into a ring of NST shared-memory stages, several
 // planes ahead of use, each completing on its own mbarrier.  Level t (1..L)
 // is computed one plane behind level t-1: a thread keeps level t-1's values
@@ -48,124 +49,163 @@ int encode_field_map(CUtensorMap* out, void* base, CUtensorMapDataType dt, size_
     return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
 
-constexpr uint32_t kMaxPolls = 1u << 22;   // bounded mbarrier wait (well over a second)
+// Geometry of one pass: every thread holds V consecutive x points (one
+// 16-byte vector) of one row.  The x halo H is L rounded up to whole vectors,
+// so the tile and every thread's vector stay 16-byte aligned; rows carry the
+// exact halo L.  Stage and level planes share one layout: RY + 2 rows of
+// RW + 2A elements, the data in rows 1..RY and columns A..A+RW-1, so the
+// neighbour reads of the edge threads land in slack, never outside.
+template <typename T, int L, int RY>
+struct TbShape {
+    static constexpr int V = Vec<T>::V;
+    static constexpr int A = 16 / (int)sizeof(T);
+    static constexpr int H = (L + V - 1) / V * V;
+    static constexpr int RW = 32 * V;
+    static constexpr int TX = RW - 2 * H;
+    static constexpr int TY = RY - 2 * L;
+    static constexpr int BW = RW + 2 * A;
+    static constexpr int ROWS = RY + 2;
+    static constexpr uint32_t BOX_BYTES = ROWS * BW * (uint32_t)sizeof(T);
+    static constexpr int PLANE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(T));
+};
 
 template <typename T, bool EXACT, int L, int RY, int NST>
 __global__ void __launch_bounds__(32 * RY, 1)
     k_heat_tb(const __grid_constant__ CUtensorMap map, T* __restrict__ dst, HeatGeom g, T r, int kc,
               FxState* fx, int m3, int* err)
 {
-    constexpr int A = 16 / (int)sizeof(T);   // TMA x start must be 16-byte aligned
-    constexpr int BW = 32 + A;               // stage row width (box width)
-    constexpr int TX = 32 - 2 * L, TY = RY - 2 * L;
-    constexpr int STAGE = RY * BW;           // elements per stage
-    constexpr int LEV = 32 * RY;             // elements per level plane
-    static_assert(TY > 0, "tile too small for the temporal depth");
+    using S = TbShape<T, L, RY>;
+    constexpr int V = S::V, A = S::A, H = S::H, TX = S::TX, TY = S::TY, BW = S::BW;
+    constexpr int PLANE = S::PLANE;
+    static_assert(TY > 0 && TX > 0, "tile too small for the temporal depth");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* stage = reinterpret_cast<T*>(smem_raw);
-    T* lev = stage + NST * STAGE;   // level t (1..L-1) buffer b at lev + ((t-1)*2 + b) * LEV
-    uint64_t* bars = reinterpret_cast<uint64_t*>(lev + (L > 1 ? (L - 1) * 2 * LEV : 0));
+    T* lev = stage + NST * PLANE;   // level t (1..L-1), buffer b: lev + ((t-1)*2 + b) * PLANE
+    uint64_t* bars = reinterpret_cast<uint64_t*>(lev + (L - 1) * 2 * PLANE);
     __shared__ int s_abort;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int X = x0 - L + tx, Y = y0 - L + ty;
+    const int X = x0 - H + V * tx, Y = y0 - L + ty;
     const int kb = blockIdx.z * kc;
     const int ke = min(kb + kc, g.nz);
     const int q0 = kb - L, qlast = ke + L - 1;
-    const int xpad = g.lead + x0 - L;
-    const int xs = xpad & ~(A - 1);
-    const int d = xpad - xs;
-    const int ybox = y0 - L + 1;   // padded row of the region's first row
-    const bool inside = (X >= 0 && X < g.nx && Y >= 0 && Y < g.ny);
-    const bool out_tile = (tx >= L && tx < L + TX && ty >= L && ty < L + TY && inside);
+    const int xs = g.lead + x0 - H - A;   // padded x of the box: 16-byte aligned
+    const int ybox = y0 - L;              // padded row of the slack row above the region
+    const int own = (ty + 1) * BW + A + V * tx;
+    const bool row_in = (Y >= 0 && Y < g.ny);
+    bool in_x[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) in_x[i] = (X + i >= 0 && X + i < g.nx);
+    const bool out_rows = (ty >= L && ty < L + TY && row_in);
+    const bool out_cols = (V * tx >= H && V * tx < H + TX);
+    const int nvalid = (out_rows && out_cols) ? min(V, g.nx - X) : 0;
 
-    int issued = q0 - 1;   // last plane whose load thread 0 has issued
+    int issued = q0 - 1;
+    int drain_from = q0;
     if (tid == 0) {
-        s_abort = 0;
+        // a block that starts after another one gave up does no work at all
+        s_abort = *(volatile int*)err;
         for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (s_abort) return;
     if (tid == 0) {
         for (int s = 0; s < NST && q0 + s <= qlast; ++s) {
-            mbar_arrive_expect_tx(&bars[s], STAGE * (uint32_t)sizeof(T));
-            tma_load_3d(stage + s * STAGE, &map, xs, ybox, q0 + s + 1, &bars[s]);
+            mbar_arrive_expect_tx(&bars[s], S::BOX_BYTES);
+            tma_load_3d(stage + s * PLANE, &map, xs, ybox, q0 + s + 1, &bars[s]);
             issued = q0 + s;
         }
     }
     int ks = 0;
     if constexpr (kIsFixed<T>) ks = fx_shift(fx, m3);
-    T zb[L], zc[L];   // level t-1 (index t-1): values at planes below and at the centre
+    T zb[L][V], zc[L][V];   // level t-1: values at the planes below and at the centre
 #pragma unroll
-    for (int t = 0; t < L; ++t) zb[t] = zc[t] = T(0);
+    for (int t = 0; t < L; ++t)
+#pragma unroll
+        for (int i = 0; i < V; ++i) zb[t][i] = zc[t][i] = T(0);
     unsigned long long mx = 0;
+    T* out = dst + g.at(nvalid > 0 ? X : 0, nvalid > 0 ? Y : 0, 0);   // plane 0; used when nvalid > 0
 
+    int s_cur = 0, n_cur = 0;   // slot and use count of plane q
     int q = q0;
     for (; q <= qlast; ++q) {
-        const int s = (q - q0) % NST;
-        const uint32_t par = (uint32_t)((q - q0) / NST) & 1u;
-        if (!mbar_wait_bounded(&bars[s], par, kMaxPolls)) {
+        if (!mbar_wait_bounded(&bars[s_cur], (uint32_t)n_cur & 1u)) {
             atomicExch(err, 1);
             s_abort = 1;
         }
-        const int sp = (q - q0 + NST - 1) % NST;   // stage of plane q-1 (junk at q = q0)
-        const T* st_prev = stage + sp * STAGE + ty * BW + tx + d;
-        T up = stage[s * STAGE + ty * BW + tx + d];   // level 0 at plane q
+        const int s_prev = s_cur == 0 ? NST - 1 : s_cur - 1;   // plane q-1 (junk at q = q0)
+        T up[V];
+        ld_vec(stage + s_cur * PLANE + own, up);
 #pragma unroll
         for (int t = 1; t <= L; ++t) {
             const int p = q - t;
-            T v = T(0);
-            const bool inreg = (tx >= t && tx < 32 - t && ty >= t && ty < RY - t);
-            if (inreg && inside && p >= 0 && p < g.nz) {
-                T xm, xp, ym, yp;
-                if (t == 1) {
-                    xm = st_prev[-1];
-                    xp = st_prev[1];
-                    ym = st_prev[-BW];
-                    yp = st_prev[BW];
-                } else {
-                    const T* b = lev + ((t - 2) * 2 + ((q - 1) & 1)) * LEV + ty * 32 + tx;
-                    xm = b[-1];
-                    xp = b[1];
-                    ym = b[-32];
-                    yp = b[32];
-                }
-                v = Point<T, EXACT>::update(zc[t - 1], xm, xp, ym, yp, zb[t - 1], up, r,
-                                            t == 1 ? ks : 0);
+            const T* src = (t == 1) ? stage + s_prev * PLANE + own
+                                    : lev + ((t - 2) * 2 + ((q - 1) & 1)) * PLANE + own;
+            T ym[V], yp[V], v[V];
+            ld_vec(src - BW, ym);
+            ld_vec(src + BW, yp);
+            const T left = src[-1], right = src[V];
+            const bool zin = row_in && p >= 0 && p < g.nz;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T xm = i == 0 ? left : zc[t - 1][i - 1];
+                const T xp = i == V - 1 ? right : zc[t - 1][i + 1];
+                const T w = Point<T, EXACT>::update(zc[t - 1][i], xm, xp, ym[i], yp[i], zb[t - 1][i],
+                                                    up[i], r, t == 1 ? ks : 0);
+                v[i] = (zin && in_x[i]) ? w : T(0);   // Dirichlet zeros outside the interior
             }
-            zb[t - 1] = zc[t - 1];
-            zc[t - 1] = up;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                zb[t - 1][i] = zc[t - 1][i];
+                zc[t - 1][i] = up[i];
+            }
             if (t < L) {
-                lev[((t - 1) * 2 + (q & 1)) * LEV + ty * 32 + tx] = v;
-                up = v;
-            } else if (out_tile && p >= kb && p < ke) {
-                dst[g.at(X, Y, p)] = v;
+                st_vec(lev + ((t - 1) * 2 + (q & 1)) * PLANE + own, v);
+#pragma unroll
+                for (int i = 0; i < V; ++i) up[i] = v[i];
+            } else if (nvalid > 0 && p >= kb && p < ke) {
+                T* o = out + (int64_t)p * g.plane;
+                if (nvalid == V)
+                    st_vec(o, v);
+                else
+                    for (int i = 0; i < nvalid; ++i) o[i] = v[i];
                 if constexpr (kIsFixed<T>) {
-                    const unsigned long long a = fx_abs(v);
-                    mx = a > mx ? a : mx;
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        const unsigned long long a = i < nvalid ? fx_abs(v[i]) : 0ull;
+                        mx = a > mx ? a : mx;
+                    }
                 }
             }
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            drain_from = q;
+            break;
+        }
         if (tid == 0 && q > q0 && issued < qlast) {
-            // the stage of plane q-1 is free: refill it with the next plane
+            // plane q-1's slot is free: refill it with the next plane
             const int pn = issued + 1;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[sp], STAGE * (uint32_t)sizeof(T));
-            tma_load_3d(stage + sp * STAGE, &map, xs, ybox, pn + 1, &bars[sp]);
+            mbar_arrive_expect_tx(&bars[s_prev], S::BOX_BYTES);
+            tma_load_3d(stage + s_prev * PLANE, &map, xs, ybox, pn + 1, &bars[s_prev]);
             issued = pn;
+        }
+        if (++s_cur == NST) {
+            s_cur = 0;
+            ++n_cur;
         }
     }
     if (s_abort) {
-        // drain: every load still in flight (planes q..issued) must land
-        // before the block's shared memory goes away
+        // drain: every load still in flight must land before shared memory goes away
         if (tid == 0) {
-            for (int p = q; p <= issued; ++p) {
-                const int s = (p - q0) % NST;
-                (void)mbar_wait_bounded(&bars[s], (uint32_t)((p - q0) / NST) & 1u, kMaxPolls);
+            const long long t0 = clock64();   // one time budget for the whole drain
+            for (int p = drain_from; p <= issued; ++p) {
+                const int i = p - q0;
+                (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
             }
         }
         return;
@@ -178,12 +218,13 @@ template <typename T, bool EXACT, int L>
 int tb_launch_t(const TbCall& c)
 {
     constexpr int RY = kTbRows;
-    constexpr int NST = 6;
-    constexpr int A = 16 / (int)sizeof(T);
-    constexpr int BW = 32 + A;
-    constexpr int TX = 32 - 2 * L, TY = RY - 2 * L;
-    const size_t smem = sizeof(T) * ((size_t)NST * RY * BW + (L > 1 ? (size_t)(L - 1) * 2 * 32 * RY : 0)) +
-                        NST * sizeof(uint64_t);
+    constexpr int NST = 4;
+    using S = TbShape<T, L, RY>;
+    constexpr size_t smem =
+        sizeof(T) * (size_t)(NST + 2 * (L - 1)) * S::PLANE + NST * sizeof(uint64_t);
+    if (c.box[0] != (uint32_t)S::BW || c.box[1] != (uint32_t)S::ROWS)
+        return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
+                    c.box[1], S::BW, S::ROWS);
     auto kern = k_heat_tb<T, EXACT, L, RY, NST>;
     static bool configured = false;
     if (!configured) {
@@ -192,10 +233,10 @@ int tb_launch_t(const TbCall& c)
         configured = true;
     }
     const HeatGeom& g = *c.g;
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + c.kc - 1) / c.kc);
+    dim3 grid((g.nx + S::TX - 1) / S::TX, (g.ny + S::TY - 1) / S::TY, (g.nz + c.kc - 1) / c.kc);
     dim3 block(32, RY, 1);
-    kern<<<grid, block, smem, c.stream>>>(*c.map, (T*)c.dst, g, tb_param<T>(c), c.kc, c.fx,
-                                          c.m3, c.err);
+    kern<<<grid, block, smem, c.stream>>>(*c.map, (T*)c.dst, g, tb_param<T>(c), c.kc, c.fx, c.m3,
+                                          c.err);
     HS_CHECK_LAUNCH("heat temporal-blocking kernel");
     return HS_OK;
 }
@@ -204,18 +245,29 @@ template <typename T, bool EXACT>
 int tb_dispatch_L(const TbCall& c)
 {
     switch (c.L) {
-    case 1: return tb_launch_t<T, EXACT, 1>(c);
     case 2: return tb_launch_t<T, EXACT, 2>(c);
     case 3: return tb_launch_t<T, EXACT, 3>(c);
     case 4: return tb_launch_t<T, EXACT, 4>(c);
-    case 6: return tb_launch_t<T, EXACT, 6>(c);
-    case 8: return tb_launch_t<T, EXACT, 8>(c);
     }
-    return fail(HS_EINVAL, "heat: temporal depth %d not built (1, 2, 3, 4, 6 or 8)", c.L);
+    return fail(HS_EINVAL, "heat: temporal depth %d not built (2, 3 or 4)", c.L);
+}
+
+int tb_box(int arith, uint32_t* box_x, uint32_t* box_y)
+{
+    // the box does not depend on the depth L
+    if (arith == A_F32) {
+        *box_x = TbShape<float, 2, kTbRows>::BW;
+        *box_y = TbShape<float, 2, kTbRows>::ROWS;
+    } else {
+        *box_x = TbShape<double, 2, kTbRows>::BW;
+        *box_y = TbShape<double, 2, kTbRows>::ROWS;
+    }
+    return 0;
 }
 
 int tb_launch(const TbCall& c)
 {
+
     switch (c.arith) {
     case A_F64: return tb_dispatch_L<double, false>(c);
     case A_F64_EXACT: return tb_dispatch_L<double, true>(c);

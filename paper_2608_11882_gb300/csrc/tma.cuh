@@ -52,13 +52,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity; gives up after max_polls polls
-// (each try_wait itself suspends for a hardware-defined time) and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_polls)
+// Waits for the phase with the given parity; gives up once max_cycles SM
+// clock cycles have passed since `start` and returns false.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t parity, long long start,
+                                                long long max_cycles)
 {
-    for (uint32_t i = 0; i < max_polls; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - start > max_cycles) return false;
+    return true;
+}
+
+// Bounded wait of its own: about one second at GB300 clocks.
+constexpr long long kWaitCycles = 2000000000ll;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    return mbar_wait_until(bar, parity, clock64(), kWaitCycles);
 }
 
 // 3-D tiled TMA load of one box into shared memory, completing on bar.

@@ -110,7 +110,7 @@ def test_errors(pkg):
         assert e.value.code == HS_ERANGE
 
 
-@pytest.mark.parametrize("tdepth", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("tdepth", [1, 2, 3, 4])
 def test_temporal_depths_against_oracle(pkg, tdepth):
     u0 = heat_u0_single_mode(37, 29, 41, seed=6)
     ref = oracle.heat_run(u0, 0.13, 29)
