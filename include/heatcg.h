@@ -169,11 +169,21 @@ typedef struct {
 } hs_op;
 
 typedef struct {
-    int32_t iters;          /* CG iterations taken                            */
+    int32_t iters;          /* CG iterations taken (mixed: inner iterations)  */
     int32_t status;         /* HS_OK or HS_ENOCONV                            */
     double  relres_recur;   /* sqrt(r.r)/||b|| of the recurrence at exit      */
     double  relres_true;    /* ||b - A x|| / ||b|| recomputed at exit         */
+    int32_t refinements;    /* mixed precision: FP64 refinement steps; 0 for FP64 CG */
+    int32_t reserved;
 } hs_cg_info;
+
+/* Options of the mixed-precision solver (zero fields take the defaults). */
+typedef struct {
+    double  inner_rtol;     /* each FP32 inner solve stops once its residual fell
+                               by this factor; in (0, 1), default 1e-4          */
+    int32_t max_inner;      /* cap on iterations of one inner solve (default 2^20) */
+    int32_t reserved;
+} hs_cg_mixed_opts;
 
 typedef struct hs_cg* hs_cg_t;
 
@@ -200,6 +210,20 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
  * filled), or an error code.  info may be NULL. */
 int cg_run(hs_cg_t c, const void* b, void* x, int host_buffers, double rtol, int32_t max_iter,
            hs_cg_info* info);
+
+/* Create a mixed-precision CG context: cg_run on it solves A x = b to rtol by
+ * FP64 iterative refinement around FP32 CG -- r = b - A x in FP64, an inner CG
+ * with its Krylov vectors (d, r', p, q) and operator in FP32 solves A d = r to
+ * inner_rtol, x += d in FP64, repeat.  Dot products accumulate in FP64 (each
+ * thread promotes after at most 8 FP32 products); alpha, beta and the residual
+ * norms are FP64.  The stop test and info->relres_true use the FP64 residual,
+ * so the returned x meets rtol in FP64 terms; info->iters counts inner
+ * iterations (max_iter bounds them) and info->refinements the inner solves.
+ * A CSR operator's values are rounded to an FP32 copy the context owns.
+ * Refinement converges while cond(A) times 2^-24 is well below one.  Use
+ * cg_run and cg_destroy as for cg_create.  (The precision split follows the
+ * spec extension of the paper's FP64 CG of Section 7.5.) */
+int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, void* stream);
 
 /* Release a CG context (synchronises its stream). */
 int cg_destroy(hs_cg_t c);

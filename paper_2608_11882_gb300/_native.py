@@ -41,7 +41,13 @@ class hs_op(ctypes.Structure):
 
 class hs_cg_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("relres_recur", ctypes.c_double), ("relres_true", ctypes.c_double)]
+                ("relres_recur", ctypes.c_double), ("relres_true", ctypes.c_double),
+                ("refinements", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class hs_cg_mixed_opts(ctypes.Structure):
+    _fields_ = [("inner_rtol", ctypes.c_double), ("max_inner", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def _load():
@@ -64,6 +70,7 @@ def _load():
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
         "cg_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), vp],
+        "cg_create_mixed": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), ctypes.POINTER(hs_cg_mixed_opts), vp],
         "cg_run": [vp, vp, vp, ctypes.c_int, dbl, i32, ctypes.POINTER(hs_cg_info)],
         "cg_destroy": [vp],
         "cg_solve": [ctypes.POINTER(hs_op), vp, vp, dbl, i32, ctypes.POINTER(hs_cg_info), vp],
@@ -158,6 +165,14 @@ def op_apply(op: hs_op, p_ptr: int, y_ptr: int, stream: int = 0) -> None:
 def cg_create(op: hs_op, stream: int = 0) -> int:
     c = ctypes.c_void_p()
     check(lib.cg_create(ctypes.byref(c), ctypes.byref(op), stream), "cg_create")
+    return c.value
+
+
+def cg_create_mixed(op: hs_op, inner_rtol: float = 0.0, max_inner: int = 0, stream: int = 0) -> int:
+    c = ctypes.c_void_p()
+    opts = hs_cg_mixed_opts(inner_rtol=inner_rtol, max_inner=max_inner, reserved=0)
+    check(lib.cg_create_mixed(ctypes.byref(c), ctypes.byref(op), ctypes.byref(opts), stream),
+          "cg_create_mixed")
     return c.value
 
 

@@ -161,10 +161,15 @@ class Operator:
 class CG:
     """A CG context with resident workspace (cg_create / cg_run / cg_destroy)."""
 
-    def __init__(self, op: Operator, stream=None):
+    def __init__(self, op: Operator, stream=None, mixed: bool = False, inner_rtol: float = 0.0,
+                 max_inner: int = 0):
+        """mixed=True: FP64 iterative refinement around FP32 CG (cg_create_mixed)."""
         self.op = op
         self.stream = _stream_handle(stream)
-        self.handle = native.cg_create(op.op, self.stream)
+        if mixed:
+            self.handle = native.cg_create_mixed(op.op, inner_rtol, max_inner, self.stream)
+        else:
+            self.handle = native.cg_create(op.op, self.stream)
 
     def run(self, b, x=None, rtol: float = 1e-8, max_iter: int = 10000):
         """Solve A x = b.  b and x are numpy arrays (host path: the library
@@ -182,7 +187,8 @@ class CG:
             raise ValueError("b and x must both be host or both be device buffers")
         rc, info = native.cg_run(self.handle, bp, xp, not bd, rtol, max_iter)
         return x, {"iters": info.iters, "status": info.status, "relres_recur": info.relres_recur,
-                   "relres_true": info.relres_true, "converged": rc == native.HS_OK}
+                   "relres_true": info.relres_true, "refinements": info.refinements,
+                   "converged": rc == native.HS_OK}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -17,8 +17,9 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libheatcg.so"
-SOURCES = ["api.cu", "heat.cu", "heat_tb.cu", "heat_stream.cu", "cg.cu"]
-HEADERS = [ROOT / "include" / "heatcg.h", CSRC / "common.cuh", CSRC / "heat_common.cuh", CSRC / "tma.cuh"]
+SOURCES = ["api.cu", "heat.cu", "heat_tb.cu", "heat_stream.cu", "cg.cu", "cg_mixed.cu"]
+HEADERS = [ROOT / "include" / "heatcg.h", CSRC / "common.cuh", CSRC / "heat_common.cuh", CSRC / "tma.cuh",
+           CSRC / "cg_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

@@ -20,35 +20,9 @@
 #include <mutex>
 #include <new>
 
-#include "common.cuh"
+#include "cg_common.cuh"
 
 namespace hcg {
-
-struct CgScalars {
-    double rho;        // r.r of the current residual
-    double pq;         // p.q
-    double alpha;
-    double beta;
-    double bnorm;      // ||b||
-    double rtol;
-    double relres;     // sqrt(rho)/||b|| at the last check
-    double rr_true;    // ||b - A x||^2 at exit
-    int32_t done;      // 1: converged (or nothing to do); 2: breakdown (p.q <= 0)
-    int32_t iters;
-    uint32_t ticket;   // blocks finished in the running reduction
-    int32_t zero_rhs;  // ||b|| == 0
-};
-
-constexpr int kCgBlock = 256;
-
-struct OpDev {
-    int32_t kind;
-    int32_t nx, ny, nz;
-    int64_t n;
-    const int32_t* rowptr;
-    const int32_t* col;
-    const double* val;
-};
 
 // (A p)[row] for the matrix-free 7-point operator: 6 p - sum of the interior
 // face neighbours; missing neighbours (outside the box) are Dirichlet zeros.
@@ -88,31 +62,6 @@ __device__ __forceinline__ double apply_row(const OpDev& A, const double* __rest
 {
     if (KIND == HS_OP_STENCIL7) return apply_stencil_row(A, p, row);
     return apply_csr_row(A, p, row);
-}
-
-// Writes this block's partial and returns true in every thread of the last
-// block to finish, after which partials[0..gridDim.x) are all visible.
-__device__ __forceinline__ bool arrive_last(double block_total, double* partials,
-                                            uint32_t* ticket)
-{
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = block_total;
-        __threadfence();
-        const uint32_t t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// Sum of partials[0..m) in a fixed order by the whole block; valid in thread 0.
-__device__ __forceinline__ double sum_partials(const double* partials, int m, double* sh)
-{
-    double v = 0.0;
-    for (int t = threadIdx.x; t < m; t += kCgBlock) v += __ldcg(partials + t);
-    return block_sum<kCgBlock>(v, sh);
 }
 
 // y = A p (no reduction).
@@ -263,22 +212,7 @@ __global__ void __launch_bounds__(kCgBlock)
 
 using namespace hcg;
 
-struct hs_cg {
-    OpDev A;
-    cudaStream_t stream;
-    int grid;
-    double* r;
-    double* p;
-    double* q;
-    double* partials;      // 2 * grid doubles
-    CgScalars* S;          // device scalars
-    CgScalars* S_host;     // pinned mirror
-    void* owned[3];        // device copies of host CSR arrays
-    double* bx_dev[2];     // device staging of host b and x (allocated on demand)
-    int64_t staged_n;
-};
-
-namespace {
+namespace hcg {
 
 int check_op(const hs_op* A)
 {
@@ -334,7 +268,7 @@ int launch_apply(const OpDev& A, const double* p, double* y, cudaStream_t s)
     return HS_OK;
 }
 
-}  // namespace
+}  // namespace hcg
 
 extern "C" {
 
@@ -360,6 +294,7 @@ int cg_destroy(hs_cg_t c)
     cudaFree(c->S);
     if (c->S_host) cudaFreeHost(c->S_host);
     for (void* o : c->owned) cudaFree(o);
+    if (c->mx) cg_mixed_release(c->mx);
     cudaFree(c->bx_dev[0]);
     cudaFree(c->bx_dev[1]);
     delete c;
@@ -436,6 +371,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
            int32_t max_iter, hs_cg_info* info)
 {
     if (!c || !b_in || !x_inout) return fail(HS_EINVAL, "cg_run: NULL argument");
+    if (c->mx) return cg_run_mixed(c, b_in, x_inout, host_buffers, rtol, max_iter, info);
     if (!(rtol >= 0.0) || !std::isfinite(rtol)) return fail(HS_EINVAL, "cg_run: rtol must be finite and >= 0");
     if (max_iter < 0) return fail(HS_EINVAL, "cg_run: max_iter < 0");
     const int64_t n = c->A.n;
@@ -512,6 +448,8 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
         info->relres_recur = f.relres;
         info->relres_true = f.zero_rhs ? 0.0 : sqrt(f.rr_true) / f.bnorm;
         info->status = converged ? HS_OK : HS_ENOCONV;
+        info->refinements = 0;
+        info->reserved = 0;
     }
     if (!converged) {
         set_error("cg_run: no convergence to rtol %g within %d iterations (relres %g)", rtol,

@@ -1,0 +1,451 @@
+// Mixed-precision CG: FP32 Krylov vectors inside FP64 iterative refinement.
+//
+//   x (FP64, the caller's)                     outer loop, until ||b - A x|| / ||b|| <= rtol:
+//     r  = b - A x              in FP64          (true residual, FP64 operator)
+//     solve A d = r approximately by CG with d, r', p, q stored in FP32 and
+//        the FP32 operator (matrix-free, or the CSR values rounded to FP32),
+//        stopping once ||r'|| <= inner_rtol ||r'_0||
+//     x += d                    in FP64
+//
+// The CG of each inner solve is the textbook one of Section 7.5.  Its dot
+// products accumulate in FP64 across the grid; each thread adds at most 8
+// FP32 products before promoting them to its FP64 sum, so the long sums --
+// the part whose stability needs FP64 -- stay FP64 while the FP64 pipe (about
+// 1/64 of FP32 issue on this GPU) sees one add per 8 elements.  alpha, beta
+// and the residual norms are FP64 device scalars.  Refinement converges while
+// kappa(A) times FP32's unit roundoff is well below one (about 6e-3 for the
+// 512^3 Laplacian).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "cg_common.cuh"
+
+namespace hcg {
+
+struct MxScalars {
+    double rho;       // r'.r' of the inner recurrence
+    double rho0;      // r'.r' at the start of the inner solve
+    double pq;
+    double alpha, beta;
+    double rr64;      // ||b - A x||^2 (FP64)
+    double bnorm;     // ||b||
+    double rtol, inner_rtol;
+    int32_t outer_done;   // 1: ||b - A x|| / ||b|| <= rtol (or b = 0)
+    int32_t inner_done;   // 1: inner solve finished; 2: breakdown
+    int32_t iters;        // inner iterations, all solves
+    uint32_t ticket;
+    int32_t zero_rhs;
+    int32_t first;        // 1 until ||b|| has been computed
+};
+
+struct OpDev32 {
+    int32_t kind;
+    int32_t nx, ny, nz;
+    int64_t n;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const float* val;
+};
+
+}  // namespace hcg
+
+struct hcg::CgMixed {
+    OpDev32 A32;
+    float* d;
+    float* r;
+    float* p;
+    float* q;
+    double* r64;         // FP64 residual (the context's r)
+    double* q64;         // A x in FP64 (the context's q)
+    float* val32;        // CSR values in FP32 (owned), else NULL
+    double* partials;    // 2 * grid
+    MxScalars* S;
+    MxScalars* S_host;   // pinned
+    double inner_rtol;
+    int32_t max_inner;
+};
+
+namespace hcg {
+
+// FP64 sum of FP32 products, promoted every 8 terms.
+struct Acc32 {
+    double hi = 0.0;
+    float lo = 0.0f;
+    int n = 0;
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        lo = __fmaf_rn(a, b, lo);
+        if (++n == 8) {
+            hi += (double)lo;
+            lo = 0.0f;
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return hi + (double)lo; }
+};
+
+__device__ __forceinline__ float apply32_stencil(const OpDev32& A, const float* __restrict__ p,
+                                                 int64_t row)
+{
+    const int nx = A.nx, ny = A.ny;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int i = (int)(row % nx);
+    const int64_t jk = row / nx;
+    const int j = (int)(jk % ny);
+    const int k = (int)(jk / ny);
+    const float zm = k > 0 ? __ldg(p + row - sxy) : 0.0f;
+    const float ym = j > 0 ? __ldg(p + row - nx) : 0.0f;
+    const float xm = i > 0 ? __ldg(p + row - 1) : 0.0f;
+    const float xp = i < nx - 1 ? __ldg(p + row + 1) : 0.0f;
+    const float yp = j < ny - 1 ? __ldg(p + row + nx) : 0.0f;
+    const float zp = k < A.nz - 1 ? __ldg(p + row + sxy) : 0.0f;
+    const float s = ((zm + ym) + (xm + xp)) + (yp + zp);
+    return __fmaf_rn(6.0f, __ldg(p + row), -s);
+}
+
+__device__ __forceinline__ float apply32_csr(const OpDev32& A, const float* __restrict__ p, int64_t row)
+{
+    float s = 0.0f;
+    const int e = __ldg(A.rowptr + row + 1);
+    for (int t = __ldg(A.rowptr + row); t < e; ++t)
+        s = __fmaf_rn(__ldg(A.val + t), __ldg(p + __ldg(A.col + t)), s);
+    return s;
+}
+
+template <int KIND>
+__device__ __forceinline__ float apply32(const OpDev32& A, const float* __restrict__ p, int64_t row)
+{
+    if (KIND == HS_OP_STENCIL7) return apply32_stencil(A, p, row);
+    return apply32_csr(A, p, row);
+}
+
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst)
+{
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock)
+        dst[t] = __double2float_rn(src[t]);
+}
+
+// r64 = b - q64 (q64 = A x); ||r64||^2 (and ||b||^2 the first time) in FP64;
+// the inner start r' = p = float(r64), d = 0, rho0 = r'.r'.  Decides the outer stop.
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ q64,
+                  double* __restrict__ r64, float* __restrict__ r, float* __restrict__ p,
+                  float* __restrict__ d, double* partials, MxScalars* S)
+{
+    __shared__ double sh[kCgBlock / 32];
+    const bool first = S->first != 0;
+    double rr = 0.0, bb = 0.0;
+    Acc32 rho;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock) {
+        const double bt = b[t];
+        const double rt = bt - q64[t];
+        r64[t] = rt;
+        const float rf = __double2float_rn(rt);
+        r[t] = rf;
+        p[t] = rf;
+        d[t] = 0.0f;
+        rr = __fma_rn(rt, rt, rr);
+        if (first) bb = __fma_rn(bt, bt, bb);
+        rho.add(rf, rf);
+    }
+    const double rr_blk = block_sum<kCgBlock>(rr, sh);
+    const double bb_blk = block_sum<kCgBlock>(bb, sh);
+    const double rho_blk = block_sum<kCgBlock>(rho.total(), sh);
+    if (threadIdx.x == 0) {
+        partials[gridDim.x + blockIdx.x] = bb_blk;
+        partials[2 * gridDim.x + blockIdx.x] = rho_blk;
+    }
+    if (!arrive_last(rr_blk, partials, &S->ticket)) return;
+    const double rr_tot = sum_partials(partials, gridDim.x, sh);
+    const double bb_tot = first ? sum_partials(partials + gridDim.x, gridDim.x, sh) : 0.0;
+    const double rho_tot = sum_partials(partials + 2 * gridDim.x, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        if (first) {
+            S->bnorm = sqrt(bb_tot);
+            S->zero_rhs = (bb_tot == 0.0);
+            S->first = 0;
+        }
+        S->rr64 = rr_tot;
+        S->rho = rho_tot;
+        S->rho0 = rho_tot;
+        S->inner_done = 0;
+        S->outer_done = (S->zero_rhs || sqrt(rr_tot) / S->bnorm <= S->rtol) ? 1 : 0;
+        if (S->outer_done || rho_tot == 0.0) S->inner_done = 1;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_spmv_dot(OpDev32 A, const float* __restrict__ p, float* __restrict__ q, double* partials,
+                  MxScalars* S)
+{
+    if (*(volatile int32_t*)&S->inner_done) return;
+    __shared__ double sh[kCgBlock / 32];
+    Acc32 pq;
+    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
+         row += (int64_t)gridDim.x * kCgBlock) {
+        const float qv = apply32<KIND>(A, p, row);
+        q[row] = qv;
+        pq.add(__ldg(p + row), qv);
+    }
+    const double blk = block_sum<kCgBlock>(pq.total(), sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double tot = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->pq = tot;
+        if (!(tot > 0.0))
+            S->inner_done = 2;
+        else
+            S->alpha = S->rho / tot;
+    }
+}
+
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_update(int64_t n, float* __restrict__ d, float* __restrict__ r, const float* __restrict__ p,
+                const float* __restrict__ q, double* partials, MxScalars* S)
+{
+    if (*(volatile int32_t*)&S->inner_done) return;
+    __shared__ double sh[kCgBlock / 32];
+    const float alpha = (float)S->alpha;
+    Acc32 rr;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock) {
+        d[t] = __fmaf_rn(alpha, p[t], d[t]);
+        const float rt = __fmaf_rn(-alpha, q[t], r[t]);
+        r[t] = rt;
+        rr.add(rt, rt);
+    }
+    const double blk = block_sum<kCgBlock>(rr.total(), sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double rho_new = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->iters += 1;
+        if (rho_new <= S->inner_rtol * S->inner_rtol * S->rho0) {
+            S->inner_done = 1;
+        } else {
+            S->beta = rho_new / S->rho;
+        }
+        S->rho = rho_new;
+    }
+}
+
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_pupdate(int64_t n, const float* __restrict__ r, float* __restrict__ p, MxScalars* S)
+{
+    if (*(volatile int32_t*)&S->inner_done) return;
+    const float beta = (float)S->beta;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock)
+        p[t] = __fmaf_rn(beta, p[t], r[t]);
+}
+
+// x += d in FP64.
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_correct(int64_t n, double* __restrict__ x, const float* __restrict__ d)
+{
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock)
+        x[t] += (double)d[t];
+}
+
+void cg_mixed_release(CgMixed* m)
+{
+    if (!m) return;
+    cudaFree(m->d);
+    cudaFree(m->r);
+    cudaFree(m->p);
+    cudaFree(m->q);
+    cudaFree(m->val32);
+    cudaFree(m->partials);
+    cudaFree(m->S);
+    if (m->S_host) cudaFreeHost(m->S_host);
+    delete m;
+}
+
+// Outer/inner loop on the host: one synchronisation per outer step and one
+// per chunk of inner iterations (kernels return at once after the inner stop).
+int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, double rtol,
+                 int32_t max_iter, hs_cg_info* info)
+{
+    CgMixed* m = c->mx;
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) return fail(HS_EINVAL, "cg_run: rtol must be finite and >= 0");
+    if (max_iter < 0) return fail(HS_EINVAL, "cg_run: max_iter < 0");
+    const int64_t n = c->A.n;
+    const size_t vbytes = sizeof(double) * (size_t)n;
+    const double* b = (const double*)b_in;
+    double* x = (double*)x_inout;
+    if (host_buffers) {
+        for (int t = 0; t < 2; ++t)
+            if (!c->bx_dev[t]) HS_TRY_CUDA(cudaMalloc((void**)&c->bx_dev[t], vbytes), "cg_run: staging buffer");
+        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[0], b_in, vbytes, cudaMemcpyHostToDevice, c->stream),
+                    "cg_run: copy of b");
+        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[1], x_inout, vbytes, cudaMemcpyHostToDevice, c->stream),
+                    "cg_run: copy of x0");
+        b = c->bx_dev[0];
+        x = c->bx_dev[1];
+    }
+    MxScalars init;
+    memset(&init, 0, sizeof(init));
+    init.rtol = rtol;
+    init.inner_rtol = m->inner_rtol;
+    init.first = 1;
+    *m->S_host = init;
+    HS_TRY_CUDA(cudaMemcpyAsync(m->S, m->S_host, sizeof(MxScalars), cudaMemcpyHostToDevice, c->stream),
+                "cg_run: scalar init");
+    const int G = c->grid;
+    int32_t outer = 0;
+    bool converged = false, breakdown = false;
+    for (;;) {
+        int rc = launch_apply(c->A, x, m->q64, c->stream);   // A x in FP64
+        if (rc != HS_OK) return rc;
+        k_mx_residual<<<G, kCgBlock, 0, c->stream>>>(n, b, m->q64, m->r64, m->r, m->p, m->d,
+                                                    m->partials, m->S);
+        HS_CHECK_LAUNCH("cg mixed: residual kernel");
+        HS_TRY_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(MxScalars), cudaMemcpyDeviceToHost, c->stream),
+                    "cg_run: scalar readback");
+        HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
+        if (m->S_host->outer_done) {
+            converged = true;
+            break;
+        }
+        if (m->S_host->iters >= max_iter) break;
+        // inner FP32 solve
+        int32_t inner = 0;
+        int chunk = 4;
+        for (;;) {
+            const int32_t budget_total = max_iter - m->S_host->iters - inner;
+            const int32_t budget_inner = m->max_inner - inner;
+            int32_t todo = chunk;
+            if (todo > budget_total) todo = budget_total;
+            if (todo > budget_inner) todo = budget_inner;
+            if (todo <= 0) break;
+            for (int32_t t = 0; t < todo; ++t) {
+                if (c->A.kind == HS_OP_STENCIL7)
+                    k_mx_spmv_dot<HS_OP_STENCIL7><<<G, kCgBlock, 0, c->stream>>>(m->A32, m->p, m->q,
+                                                                                 m->partials, m->S);
+                else
+                    k_mx_spmv_dot<HS_OP_CSR><<<G, kCgBlock, 0, c->stream>>>(m->A32, m->p, m->q,
+                                                                            m->partials, m->S);
+                HS_CHECK_LAUNCH("cg mixed: spmv+dot kernel");
+                k_mx_update<<<G, kCgBlock, 0, c->stream>>>(n, m->d, m->r, m->p, m->q, m->partials, m->S);
+                HS_CHECK_LAUNCH("cg mixed: update kernel");
+                k_mx_pupdate<<<G, kCgBlock, 0, c->stream>>>(n, m->r, m->p, m->S);
+                HS_CHECK_LAUNCH("cg mixed: p update kernel");
+            }
+            inner += todo;
+            HS_TRY_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(MxScalars), cudaMemcpyDeviceToHost,
+                                        c->stream),
+                        "cg_run: scalar readback");
+            HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
+            if (m->S_host->inner_done) break;
+            if (chunk < 32) chunk *= 2;
+        }
+        if (m->S_host->inner_done == 2) {
+            breakdown = true;
+            break;
+        }
+        k_mx_correct<<<G, kCgBlock, 0, c->stream>>>(n, x, m->d);   // x += d (FP64)
+        HS_CHECK_LAUNCH("cg mixed: correction kernel");
+        ++outer;
+    }
+    if (m->S_host->zero_rhs) HS_TRY_CUDA(cudaMemsetAsync(x, 0, vbytes, c->stream), "cg_run: zero solution");
+    if (host_buffers)
+        HS_TRY_CUDA(cudaMemcpyAsync(x_inout, x, vbytes, cudaMemcpyDeviceToHost, c->stream),
+                    "cg_run: copy of x");
+    HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
+    if (breakdown) return fail(HS_ECUDA, "cg_run: breakdown in the FP32 inner solve");
+    const MxScalars f = *m->S_host;   // from the last residual evaluation
+    const double relres = f.zero_rhs ? 0.0 : sqrt(f.rr64) / f.bnorm;
+    if (info) {
+        info->iters = f.iters;
+        info->relres_recur = relres;
+        info->relres_true = relres;   // the outer residual is recomputed in FP64
+        info->status = converged ? HS_OK : HS_ENOCONV;
+        info->refinements = outer;
+        info->reserved = 0;
+    }
+    if (!converged) {
+        set_error("cg_run: mixed precision stopped at %d inner iterations (relres %g > rtol %g)",
+                  f.iters, relres, rtol);
+        return HS_ENOCONV;
+    }
+    return HS_OK;
+}
+
+}  // namespace hcg
+
+using namespace hcg;
+
+extern "C" {
+
+int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, void* stream)
+{
+    if (!out) return fail(HS_EINVAL, "cg_create_mixed: out is NULL");
+    *out = nullptr;
+    double inner_rtol = 1e-4;
+    int32_t max_inner = 1 << 20;
+    if (opts) {
+        if (opts->inner_rtol != 0.0) inner_rtol = opts->inner_rtol;
+        if (opts->max_inner != 0) max_inner = opts->max_inner;
+    }
+    if (!(inner_rtol > 0.0 && inner_rtol < 1.0))
+        return fail(HS_EINVAL, "cg_create_mixed: inner_rtol %g not in (0, 1)", inner_rtol);
+    if (max_inner < 1) return fail(HS_EINVAL, "cg_create_mixed: max_inner < 1");
+    hs_cg_t c = nullptr;
+    int rc = cg_create(&c, A, stream);
+    if (rc != HS_OK) return rc;
+    CgMixed* m = new (std::nothrow) CgMixed();
+    if (!m) {
+        cg_destroy(c);
+        return fail(HS_ENOMEM, "cg_create_mixed: host allocation failed");
+    }
+    c->mx = m;
+    m->inner_rtol = inner_rtol;
+    m->max_inner = max_inner;
+    const int64_t n = c->A.n;
+    const int G = c->grid;
+    cudaError_t e = cudaSuccess;
+    for (float** v : {&m->d, &m->r, &m->p, &m->q})
+        if (e == cudaSuccess) e = cudaMalloc((void**)v, sizeof(float) * (size_t)n);
+    // the FP64 residual and A x live in the context's FP64 r and q; its p is not needed
+    m->r64 = c->r;
+    m->q64 = c->q;
+    cudaFree(c->p);
+    c->p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->partials, sizeof(double) * 3 * (size_t)G);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->S, sizeof(MxScalars));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&m->S_host, sizeof(MxScalars));
+    if (e == cudaSuccess && c->A.kind == HS_OP_CSR) {
+        const int64_t nnz = c->A.rowptr ? A->nnz : 0;
+        e = cudaMalloc((void**)&m->val32, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess && nnz > 0) {
+            k_mx_to_f32<<<grid_for(nnz), kCgBlock, 0, c->stream>>>(nnz, c->A.val, m->val32);
+            e = cudaPeekAtLastError();
+            count_launch();
+        }
+    }
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "cg_create_mixed: allocation");
+        cg_destroy(c);
+        return rc;
+    }
+    m->A32.kind = c->A.kind;
+    m->A32.nx = c->A.nx;
+    m->A32.ny = c->A.ny;
+    m->A32.nz = c->A.nz;
+    m->A32.n = n;
+    m->A32.rowptr = c->A.rowptr;
+    m->A32.col = c->A.col;
+    m->A32.val = m->val32;
+    *out = c;
+    return HS_OK;
+}
+
+}  // extern "C"

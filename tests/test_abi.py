@@ -28,7 +28,8 @@ def test_binding_struct_sizes_match_header_layout():
     # hs_heat_desc: 3*int32 + pad, double, uint32, int32, int32 + pad, void*
     assert ctypes.sizeof(nat.hs_heat_desc) == 48
     assert ctypes.sizeof(nat.hs_op) == 64
-    assert ctypes.sizeof(nat.hs_cg_info) == 24
+    assert ctypes.sizeof(nat.hs_cg_info) == 32
+    assert ctypes.sizeof(nat.hs_cg_mixed_opts) == 16
 
 
 def test_version_and_error_string_without_gpu():
