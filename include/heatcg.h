@@ -151,6 +151,40 @@ int heat_get_tdepth(hs_heat_t h, int32_t* tdepth);
 /* Release the handle and its device buffers (synchronises its stream). */
 int heat_destroy(hs_heat_t h);
 
+/* ---- batched heat stepping ---------------------------------------------- */
+/* Many independent grids -- their own sizes, r and step counts, FP64 or FP32
+ * -- advanced together in ONE persistent kernel launch (optionally replayed
+ * from a captured CUDA graph).  Each grid is a heat handle (plain HS_F64 or
+ * HS_F32, not HS_FIXED64) whose field has been uploaded; a run advances
+ * grid i by steps[i] steps of the update of Section 4, Eq. 4 -- the work of
+ * the Interior and Boundary kernels of each step -- with the same per-point
+ * arithmetic as heat_step, so the results match running each grid alone bit
+ * for bit.  Work items are (step, grid, column tile) taken from a device work
+ * counter; a grid's step starts once its previous step is complete, a wait
+ * that is bounded (about a second), after which heat_batch_wait reports
+ * HS_ETIMEOUT. */
+typedef struct hs_batch* hs_batch_t;
+
+/* Build the batch and its step-major work schedule.  grids[0..n) must be
+ * distinct and outlive the batch; steps[i] >= 0.  The batch runs on `stream`
+ * (each grid's own stream is synchronised before a run). */
+int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps, int32_t n,
+                      void* stream);
+
+/* Enqueue one run: every grid advances by its steps (asynchronous; the
+ * handles' step counters and current buffers are updated at once).  With
+ * use_graph != 0 the first run captures [clear counters, persistent launch]
+ * into a CUDA graph that later runs replay. */
+int heat_batch_run(hs_batch_t b, int use_graph);
+
+/* Synchronise the batch stream; HS_ETIMEOUT if a bounded wait ran out. */
+int heat_batch_wait(hs_batch_t b);
+
+/* Lattice-point updates per run, and blocks of the persistent launch. */
+int heat_batch_info(hs_batch_t b, int64_t* lups, int32_t* blocks);
+
+int heat_batch_destroy(hs_batch_t b);
+
 /* ---- conjugate gradients (Section 7.5) --------------------------------- */
 #define HS_OP_STENCIL7 0   /* matrix-free 7-point Dirichlet Laplacian on nx*ny*nz */
 #define HS_OP_CSR      1   /* CSR matrix (rowptr, col, val), int32 indices        */
@@ -213,8 +247,9 @@ int cg_run(hs_cg_t c, const void* b, void* x, int host_buffers, double rtol, int
 
 /* Create a mixed-precision CG context: cg_run on it solves A x = b to rtol by
  * FP64 iterative refinement around FP32 CG -- r = b - A x in FP64, an inner CG
- * with its Krylov vectors (d, r', p, q) and operator in FP32 solves A d = r to
- * inner_rtol, x += d in FP64, repeat.  Dot products accumulate in FP64 (each
+ * with its Krylov vectors (d, r', p, q) and operator in FP32 solves A d = r,
+ * reducing its residual by inner_rtol or by just what reaching rtol needs
+ * (with a factor-2 margin), whichever is less, x += d in FP64, repeat.  Dot products accumulate in FP64 (each
  * thread promotes after at most 8 FP32 products); alpha, beta and the residual
  * norms are FP64.  The stop test and info->relres_true use the FP64 residual,
  * so the returned x meets rtol in FP64 terms; info->iters counts inner

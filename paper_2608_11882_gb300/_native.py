@@ -69,6 +69,11 @@ def _load():
         "heat_get_tdepth": [vp, ctypes.POINTER(i32)],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
+        "heat_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64), i32, vp],
+        "heat_batch_run": [vp, ctypes.c_int],
+        "heat_batch_wait": [vp],
+        "heat_batch_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)],
+        "heat_batch_destroy": [vp],
         "cg_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), vp],
         "cg_create_mixed": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), ctypes.POINTER(hs_cg_mixed_opts), vp],
         "cg_run": [vp, vp, vp, ctypes.c_int, dbl, i32, ctypes.POINTER(hs_cg_info)],
@@ -156,6 +161,33 @@ def heat_get_tdepth(h: int) -> int:
 
 def heat_destroy(h: int) -> None:
     check(lib.heat_destroy(h), "heat_destroy")
+
+
+def heat_batch_create(handles, steps, stream: int = 0) -> int:
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*handles)
+    st = (ctypes.c_int64 * n)(*[int(s) for s in steps])
+    b = ctypes.c_void_p()
+    check(lib.heat_batch_create(ctypes.byref(b), arr, st, n, stream), "heat_batch_create")
+    return b.value
+
+
+def heat_batch_run(b: int, use_graph: bool = True) -> None:
+    check(lib.heat_batch_run(b, int(bool(use_graph))), "heat_batch_run")
+
+
+def heat_batch_wait(b: int) -> None:
+    check(lib.heat_batch_wait(b), "heat_batch_wait")
+
+
+def heat_batch_info(b: int):
+    lups, blocks = ctypes.c_int64(), ctypes.c_int32()
+    check(lib.heat_batch_info(b, ctypes.byref(lups), ctypes.byref(blocks)), "heat_batch_info")
+    return lups.value, blocks.value
+
+
+def heat_batch_destroy(b: int) -> None:
+    check(lib.heat_batch_destroy(b), "heat_batch_destroy")
 
 
 def op_apply(op: hs_op, p_ptr: int, y_ptr: int, stream: int = 0) -> None:

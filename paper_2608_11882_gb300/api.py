@@ -113,6 +113,49 @@ class Heat:
             pass
 
 
+class HeatBatch:
+    """Several Heat handles advanced together by one persistent launch
+    (heat_batch_create / heat_batch_run / heat_batch_wait)."""
+
+    def __init__(self, heats, steps, stream=None):
+        self.heats = list(heats)
+        self.steps = [int(s) for s in steps]
+        self.stream = _stream_handle(stream)
+        self.handle = native.heat_batch_create([h.handle for h in self.heats], self.steps, self.stream)
+
+    def run(self, use_graph: bool = True) -> "HeatBatch":
+        native.heat_batch_run(self.handle, use_graph)
+        return self
+
+    def wait(self) -> None:
+        native.heat_batch_wait(self.handle)
+
+    @property
+    def lups(self) -> int:
+        return native.heat_batch_info(self.handle)[0]
+
+    @property
+    def blocks(self) -> int:
+        return native.heat_batch_info(self.handle)[1]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.heat_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Operator:
     """The CG operator: matrix-free 7-point stencil or CSR arrays (torch CUDA
     tensors, or numpy arrays that cg_create copies to the device)."""

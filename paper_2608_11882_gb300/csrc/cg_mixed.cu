@@ -4,7 +4,7 @@
 //     r  = b - A x              in FP64          (true residual, FP64 operator)
 //     solve A d = r approximately by CG with d, r', p, q stored in FP32 and
 //        the FP32 operator (matrix-free, or the CSR values rounded to FP32),
-//        stopping once ||r'|| <= inner_rtol ||r'_0||
+//        stopping once ||r'|| <= max(inner_rtol, rtol ||b|| / (2 ||r||)) ||r'_0||
 //     x += d                    in FP64
 //
 // The CG of each inner solve is the textbook one of Section 7.5.  Its dot
@@ -31,6 +31,7 @@ struct MxScalars {
     double rr64;      // ||b - A x||^2 (FP64)
     double bnorm;     // ||b||
     double rtol, inner_rtol;
+    double inner_stop;    // the inner solve ends once r'.r' <= inner_stop
     int32_t outer_done;   // 1: ||b - A x|| / ||b|| <= rtol (or b = 0)
     int32_t inner_done;   // 1: inner solve finished; 2: breakdown
     int32_t iters;        // inner iterations, all solves
@@ -173,6 +174,12 @@ __global__ void __launch_bounds__(kCgBlock)
         S->rr64 = rr_tot;
         S->rho = rho_tot;
         S->rho0 = rho_tot;
+        // reduce the residual by inner_rtol, or just by what reaching rtol (with a
+        // factor-2 margin) needs, whichever is the smaller reduction
+        double f2 = S->inner_rtol * S->inner_rtol;
+        const double need = 0.5 * S->rtol * S->bnorm;
+        if (rr_tot > 0.0 && need * need / rr_tot > f2) f2 = need * need / rr_tot;
+        S->inner_stop = f2 * rho_tot;
         S->inner_done = 0;
         S->outer_done = (S->zero_rhs || sqrt(rr_tot) / S->bnorm <= S->rtol) ? 1 : 0;
         if (S->outer_done || rho_tot == 0.0) S->inner_done = 1;
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kCgBlock)
     if (threadIdx.x == 0) {
         S->ticket = 0;
         S->iters += 1;
-        if (rho_new <= S->inner_rtol * S->inner_rtol * S->rho0) {
+        if (rho_new <= S->inner_stop) {
             S->inner_done = 1;
         } else {
             S->beta = rho_new / S->rho;

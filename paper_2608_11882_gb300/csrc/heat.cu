@@ -491,6 +491,32 @@ unsigned conv_blocks(const HeatGeom& g)
 
 }  // namespace
 
+namespace hcg {
+
+int heat_batch_view(hs_heat_t h, HeatBatchView* v)
+{
+    if (!h || !v) return fail(HS_EINVAL, "heat batch: NULL handle");
+    v->g = h->g;
+    v->buf[0] = h->buf[0];
+    v->buf[1] = h->buf[1];
+    v->r = h->r;
+    v->arith = h->arith;
+    v->cur = h->cur;
+    v->stream = h->stream;
+    return HS_OK;
+}
+
+int heat_batch_advance(hs_heat_t h, int64_t steps)
+{
+    if (!h) return fail(HS_EINVAL, "heat batch: NULL handle");
+    h->cur = (int)((h->cur + steps) & 1);
+    h->steps += steps;
+    h->fxseq += steps;
+    return HS_OK;
+}
+
+}  // namespace hcg
+
 extern "C" {
 
 int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)

@@ -1,0 +1,386 @@
+// Batched heat stepping: many independent grids (their own sizes, r, step
+// counts, FP32 or FP64), every step of every grid, in ONE persistent kernel
+// launch, optionally replayed from a captured CUDA graph.
+//
+// Work items are (step m, grid g, column tile t) in step-major order; a
+// persistent grid of co-resident blocks takes them from an atomic counter.
+// An item of step m of grid g may start once all tiles of step m-1 of grid g
+// have finished (a per-grid completion counter, published with a fence), so
+// each step of a grid reads a complete previous time level -- the Interior
+// and Boundary work of one step of Section 4's update, over the whole grid.
+// Items of step m-1 always come earlier in the order, so they have been taken
+// by running blocks and the wait ends; it is still bounded (about a second of
+// SM clock), after which the kernel records HS_ETIMEOUT and stops.
+//
+// Loads use ld.global.cg (L2 only): a block must never see another SM's
+// freshly written plane through its own stale L1 lines.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "heat_common.cuh"
+
+namespace hcg {
+
+constexpr int kBatchBX = 32, kBatchBY = 8;
+constexpr long long kBatchWaitCycles = 2000000000ll;
+
+struct BatchGrid {
+    HeatGeom g;
+    void* buf[2];
+    double r;
+    int32_t dtype;      // HS_F64 or HS_F32
+    int32_t cur;        // buffer holding the field when the batch starts
+    int32_t tiles_x;
+    int32_t tiles;      // tiles per step
+    int64_t steps;
+};
+
+struct BatchDev {
+    const BatchGrid* grids;
+    const int64_t* step_item0;    // first item of step m (size max_steps + 1)
+    const int32_t* step_list0;    // first entry of step m in the active lists (size max_steps + 1)
+    const int32_t* list_grid;     // active grid of each entry
+    const int64_t* list_item0;    // first item (within its step) of each entry
+    unsigned long long* next;     // work counter
+    unsigned long long* done;     // per grid: tiles completed, all steps
+    int* err;
+    int64_t items;
+    int32_t max_steps;
+};
+
+template <typename T>
+__device__ __forceinline__ void batch_tile(const BatchGrid& G, int m, int t)
+{
+    const HeatGeom& g = G.g;
+    const int tx = t % G.tiles_x, ty = t / G.tiles_x;
+    const int i = tx * kBatchBX + threadIdx.x;
+    const int j = ty * kBatchBY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int src_b = (G.cur + m) & 1;
+    const T* __restrict__ src = (const T*)G.buf[src_b];
+    T* __restrict__ dst = (T*)G.buf[src_b ^ 1];
+    const T r = (T)G.r;
+    const int64_t P = g.plane, Y = g.pitch;
+    int64_t c = g.at(i, j, 0);
+    T below = __ldcg(src + c - P);
+    T cur = __ldcg(src + c);
+    for (int k = 0; k < g.nz; ++k) {
+        const T above = __ldcg(src + c + P);
+        const T xm = __ldcg(src + c - 1), xp = __ldcg(src + c + 1);
+        const T ym = __ldcg(src + c - Y), yp = __ldcg(src + c + Y);
+        dst[c] = Point<T, false>::update(cur, xm, xp, ym, yp, below, above, r, 0);
+        below = cur;
+        cur = above;
+        c += P;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
+{
+    __shared__ long long s_item;
+    __shared__ int s_abort;
+    const int tid = threadIdx.y * kBatchBX + threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            s_abort = *(volatile int*)B.err;
+            s_item = s_abort ? B.items : (long long)atomicAdd(B.next, 1ull);
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= B.items) break;
+        // step m: the last m with step_item0[m] <= item
+        int lo = 0, hi = B.max_steps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.step_item0[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const int m = lo;
+        const long long in_step = item - B.step_item0[m];
+        int a = B.step_list0[m], z = B.step_list0[m + 1] - 1;
+        while (a < z) {
+            const int mid = (a + z + 1) >> 1;
+            if (B.list_item0[mid] <= in_step) a = mid; else z = mid - 1;
+        }
+        const int gi = B.list_grid[a];
+        const BatchGrid& G = B.grids[gi];
+        const int t = (int)(in_step - B.list_item0[a]);
+        if (tid == 0 && m > 0) {
+            // wait until step m-1 of this grid is complete
+            const unsigned long long need = (unsigned long long)m * (unsigned long long)G.tiles;
+            const long long t0 = clock64();
+            while (*(volatile unsigned long long*)&B.done[gi] < need) {
+                if (clock64() - t0 > kBatchWaitCycles) {
+                    atomicExch(B.err, 1);
+                    s_abort = 1;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (G.dtype == HS_F64)
+            batch_tile<double>(G, m, t);
+        else
+            batch_tile<float>(G, m, t);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(&B.done[gi], 1ull);
+    }
+}
+
+}  // namespace hcg
+
+using namespace hcg;
+
+struct hs_batch {
+    cudaStream_t stream;
+    std::vector<hs_heat_t> handles;
+    std::vector<int64_t> steps;
+    BatchDev dev;
+    void* arena;          // device: grids, schedule, counters
+    size_t counter_bytes;
+    void* counters;       // next + done[] + err (cleared before each run)
+    int blocks;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t capture;   // private stream the graph is captured on
+    int64_t lups;
+};
+
+extern "C" {
+
+int heat_batch_destroy(hs_batch_t b)
+{
+    if (!b) return HS_OK;
+    int rc = HS_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "heat_batch_destroy: synchronize");
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    cudaFree(b->arena);
+    delete b;
+    return rc;
+}
+
+int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps, int32_t n,
+                      void* stream)
+{
+    if (!out) return fail(HS_EINVAL, "heat_batch_create: out is NULL");
+    *out = nullptr;
+    if (!grids || !steps || n < 1) return fail(HS_EINVAL, "heat_batch_create: no grids");
+    std::vector<BatchGrid> hg((size_t)n);
+    int64_t max_steps = 0;
+    int64_t lups = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const hs_heat_t h = grids[i];
+        if (!h) return fail(HS_EINVAL, "heat_batch_create: grid %d is NULL", i);
+        if (steps[i] < 0) return fail(HS_EINVAL, "heat_batch_create: steps[%d] < 0", i);
+        HeatBatchView v;
+        int rc = heat_batch_view(h, &v);
+        if (rc != HS_OK) return rc;
+        if (v.arith != A_F64 && v.arith != A_F32)
+            return fail(HS_EINVAL, "heat_batch_create: grid %d must be plain FP64 or FP32", i);
+        for (int32_t k = 0; k < i; ++k)
+            if (grids[k] == h) return fail(HS_EINVAL, "heat_batch_create: grid %d appears twice", i);
+        BatchGrid& G = hg[(size_t)i];
+        G.g = v.g;
+        G.buf[0] = v.buf[0];
+        G.buf[1] = v.buf[1];
+        G.r = v.r;
+        G.dtype = v.arith == A_F64 ? HS_F64 : HS_F32;
+        G.cur = 0;   // set at each run
+        G.tiles_x = (v.g.nx + kBatchBX - 1) / kBatchBX;
+        G.tiles = G.tiles_x * ((v.g.ny + kBatchBY - 1) / kBatchBY);
+        G.steps = steps[i];
+        if (steps[i] > max_steps) max_steps = steps[i];
+        lups += (int64_t)v.g.nx * v.g.ny * v.g.nz * steps[i];
+    }
+    if (max_steps > (1 << 30)) return fail(HS_EINVAL, "heat_batch_create: too many steps");
+    // step-major schedule
+    std::vector<int64_t> step_item0((size_t)max_steps + 1, 0);
+    std::vector<int32_t> step_list0((size_t)max_steps + 1, 0);
+    std::vector<int32_t> list_grid;
+    std::vector<int64_t> list_item0;
+    int64_t items = 0;
+    for (int64_t m = 0; m < max_steps; ++m) {
+        step_item0[(size_t)m] = items;
+        step_list0[(size_t)m] = (int32_t)list_grid.size();
+        int64_t in_step = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            if (hg[(size_t)i].steps <= m) continue;
+            list_grid.push_back(i);
+            list_item0.push_back(in_step);
+            in_step += hg[(size_t)i].tiles;
+        }
+        items += in_step;
+    }
+    step_item0[(size_t)max_steps] = items;
+    step_list0[(size_t)max_steps] = (int32_t)list_grid.size();
+    if (list_grid.size() > (size_t)INT32_MAX) return fail(HS_EINVAL, "heat_batch_create: schedule too large");
+
+    hs_batch* b = new (std::nothrow) hs_batch();
+    if (!b) return fail(HS_ENOMEM, "heat_batch_create: host allocation failed");
+    b->stream = (cudaStream_t)stream;
+    b->handles.assign(grids, grids + n);
+    b->steps.assign(steps, steps + n);
+    b->lups = lups;
+    // one arena: grids | step_item0 | list_item0 | step_list0 | list_grid | counters
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t s_grids = align(sizeof(BatchGrid) * hg.size());
+    const size_t s_si = align(sizeof(int64_t) * step_item0.size());
+    const size_t s_li = align(sizeof(int64_t) * (list_item0.size() ? list_item0.size() : 1));
+    const size_t s_sl = align(sizeof(int32_t) * step_list0.size());
+    const size_t s_lg = align(sizeof(int32_t) * (list_grid.size() ? list_grid.size() : 1));
+    b->counter_bytes = align(sizeof(unsigned long long) * (1 + (size_t)n) + sizeof(int));
+    const size_t total = s_grids + s_si + s_li + s_sl + s_lg + b->counter_bytes;
+    cudaError_t e = cudaMalloc(&b->arena, total);
+    if (e != cudaSuccess) {
+        b->arena = nullptr;
+        const int rc = cuda_fail(e, "heat_batch_create: cudaMalloc");
+        heat_batch_destroy(b);
+        return rc;
+    }
+    char* base = (char*)b->arena;
+    BatchGrid* d_grids = (BatchGrid*)base;
+    int64_t* d_si = (int64_t*)(base + s_grids);
+    int64_t* d_li = (int64_t*)(base + s_grids + s_si);
+    int32_t* d_sl = (int32_t*)(base + s_grids + s_si + s_li);
+    int32_t* d_lg = (int32_t*)(base + s_grids + s_si + s_li + s_sl);
+    b->counters = base + s_grids + s_si + s_li + s_sl + s_lg;
+    // grids are re-uploaded at each run (cur changes); the schedule once
+    e = cudaMemcpy(d_si, step_item0.data(), sizeof(int64_t) * step_item0.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !list_item0.empty())
+        e = cudaMemcpy(d_li, list_item0.data(), sizeof(int64_t) * list_item0.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_sl, step_list0.data(), sizeof(int32_t) * step_list0.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !list_grid.empty())
+        e = cudaMemcpy(d_lg, list_grid.data(), sizeof(int32_t) * list_grid.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_grids, hg.data(), sizeof(BatchGrid) * hg.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(e, "heat_batch_create: schedule upload");
+        heat_batch_destroy(b);
+        return rc;
+    }
+    unsigned long long* ctr = (unsigned long long*)b->counters;
+    b->dev.grids = d_grids;
+    b->dev.step_item0 = d_si;
+    b->dev.step_list0 = d_sl;
+    b->dev.list_grid = d_lg;
+    b->dev.list_item0 = d_li;
+    b->dev.next = ctr;
+    b->dev.done = ctr + 1;
+    b->dev.err = (int*)(ctr + 1 + n);
+    b->dev.items = items;
+    b->dev.max_steps = (int32_t)(max_steps > 0 ? max_steps : 1);
+    // persistent grid: every block resident at once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heat_batch, kBatchBX * kBatchBY, 0);
+    int sms = kNumSMs;
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || per_sm < 1) {
+        const int rc = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration,
+                                 "heat_batch_create: occupancy");
+        heat_batch_destroy(b);
+        return rc;
+    }
+    b->blocks = per_sm * sms;
+    *out = b;
+    return HS_OK;
+}
+
+// Enqueue: refresh each grid's current buffer, clear the counters, launch.
+static int batch_enqueue(hs_batch* b)
+{
+    const int n = (int)b->handles.size();
+    std::vector<BatchGrid> hg((size_t)n);
+    HS_TRY_CUDA(cudaMemcpy(hg.data(), b->dev.grids, sizeof(BatchGrid) * n, cudaMemcpyDeviceToHost),
+                "heat_batch_run: grid table");
+    bool changed = false;
+    for (int i = 0; i < n; ++i) {
+        HeatBatchView v;
+        int rc = heat_batch_view(b->handles[(size_t)i], &v);
+        if (rc != HS_OK) return rc;
+        // the grid's own stream may still be uploading into it
+        if (v.stream != b->stream)
+            HS_TRY_CUDA(cudaStreamSynchronize(v.stream), "heat_batch_run: grid stream");
+        if (hg[(size_t)i].cur != v.cur) {
+            hg[(size_t)i].cur = v.cur;
+            changed = true;
+        }
+    }
+    if (changed)
+        HS_TRY_CUDA(cudaMemcpyAsync((void*)b->dev.grids, hg.data(), sizeof(BatchGrid) * n,
+                                    cudaMemcpyHostToDevice, b->stream),
+                    "heat_batch_run: grid table");
+    HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_run: synchronize");
+    return changed ? 1 : 0;
+}
+
+int heat_batch_run(hs_batch_t b, int use_graph)
+{
+    if (!b) return fail(HS_EINVAL, "heat_batch_run: NULL batch");
+    int rc = batch_enqueue(b);
+    if (rc < 0) return rc;
+    if (use_graph) {
+        if (!b->exec) {
+            // capture on a private stream (the caller's may be the legacy
+            // default stream, which cannot be captured); launch on the caller's
+            if (!b->capture)
+                HS_TRY_CUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking),
+                            "heat_batch_run: capture stream");
+            HS_TRY_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal),
+                        "heat_batch_run: begin capture");
+            cudaError_t e1 = cudaMemsetAsync(b->counters, 0, b->counter_bytes, b->capture);
+            k_heat_batch<<<b->blocks, dim3(kBatchBX, kBatchBY), 0, b->capture>>>(b->dev);
+            cudaError_t e2 = cudaPeekAtLastError();
+            cudaGraph_t graph = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(b->capture, &graph);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+                (void)cudaGetLastError();
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3,
+                                 "heat_batch_run: capture");
+            }
+            b->graph = graph;
+            HS_TRY_CUDA(cudaGraphInstantiate(&b->exec, graph, 0), "heat_batch_run: instantiate");
+        }
+        HS_TRY_CUDA(cudaGraphLaunch(b->exec, b->stream), "heat_batch_run: graph launch");
+        count_launch();
+    } else {
+        HS_TRY_CUDA(cudaMemsetAsync(b->counters, 0, b->counter_bytes, b->stream), "heat_batch_run: memset");
+        k_heat_batch<<<b->blocks, dim3(kBatchBX, kBatchBY), 0, b->stream>>>(b->dev);
+        HS_CHECK_LAUNCH("heat batch kernel");
+    }
+    // every grid advanced by its steps: update the handles' bookkeeping
+    for (size_t i = 0; i < b->handles.size(); ++i) {
+        rc = heat_batch_advance(b->handles[i], b->steps[i]);
+        if (rc != HS_OK) return rc;
+    }
+    return HS_OK;
+}
+
+int heat_batch_wait(hs_batch_t b)
+{
+    if (!b) return fail(HS_EINVAL, "heat_batch_wait: NULL batch");
+    HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_wait: synchronize");
+    int err = 0;
+    HS_TRY_CUDA(cudaMemcpy(&err, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost), "heat_batch_wait: status");
+    if (err) return fail(HS_ETIMEOUT, "heat_batch_wait: a bounded wait in the batch kernel ran out");
+    return HS_OK;
+}
+
+int heat_batch_info(hs_batch_t b, int64_t* lups, int32_t* blocks)
+{
+    if (!b) return fail(HS_EINVAL, "heat_batch_info: NULL batch");
+    if (lups) *lups = b->lups;
+    if (blocks) *blocks = b->blocks;
+    return HS_OK;
+}
+
+}  // extern "C"

@@ -270,6 +270,19 @@ int stream_box(int arith, uint32_t* box_x, uint32_t* box_y);
 // Rows of the streaming kernel's tile (its tile is 32 x kStreamRows columns).
 constexpr int kStreamRowsHost = 16;
 
+// What the batched kernel needs to know about a heat handle (heat.cu).
+struct HeatBatchView {
+    HeatGeom g;
+    void* buf[2];
+    double r;
+    int arith;
+    int cur;
+    cudaStream_t stream;
+};
+int heat_batch_view(hs_heat_t h, HeatBatchView* v);
+// Records that a batch advanced the handle by `steps` steps.
+int heat_batch_advance(hs_heat_t h, int64_t steps);
+
 // Rows of the temporally blocked kernel's thread block (its tile is
 // (32 - 2L) x (kTbRows - 2L) columns).
 constexpr int kTbRows = 32;

@@ -1,0 +1,111 @@
+"""Batched heat stepping (one persistent launch for many uneven grids,
+FP32 and FP64, optionally a CUDA graph): every grid must equal the same grid
+stepped alone through heat_step, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_util import F64_REL, lib, rel_max_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    oracle.build()
+    return lib()
+
+
+def draw_batch(n, seed, edge=(16, 128), steps=(50, 500)):
+    """Edges log-uniform in [16, 128] (non-cubic), r ~ U[0.05, 0.16],
+    steps ~ U{lo..hi}, dtype alternating FP32 / FP64."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for g in range(n):
+        nz, ny, nx = np.round(np.exp(rng.uniform(np.log(edge[0]), np.log(edge[1]), 3))).astype(int)
+        out.append(dict(shape=(int(nz), int(ny), int(nx)), r=float(rng.uniform(0.05, 0.16)),
+                        steps=int(rng.integers(steps[0], steps[1] + 1)),
+                        dtype="f32" if g % 2 else "f64",
+                        u0=rng.uniform(-1, 1, size=(int(nz), int(ny), int(nx)))))
+    return out
+
+
+def alone(pkg, spec, steps):
+    nz, ny, nx = spec["shape"]
+    with pkg.Heat(nx, ny, nz, spec["r"], dtype=spec["dtype"], tdepth=1) as h:
+        h.upload(spec["u0"].astype(h.np_dtype))
+        h.step(steps)
+        return h.read()
+
+
+def make_heats(pkg, specs):
+    hs = []
+    for s in specs:
+        nz, ny, nx = s["shape"]
+        h = pkg.Heat(nx, ny, nz, s["r"], dtype=s["dtype"], tdepth=1)
+        h.upload(s["u0"].astype(h.np_dtype))
+        hs.append(h)
+    return hs
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_alone_bitwise(pkg, use_graph):
+    specs = draw_batch(14, seed=5, edge=(4, 70), steps=(0, 60))
+    specs[3]["steps"] = 0
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b:
+        b.run(use_graph=use_graph)
+        b.wait()
+        assert b.lups == sum(np.prod(s["shape"]) * s["steps"] for s in specs)
+    for s, h in zip(specs, heats):
+        assert h.steps_done == s["steps"]
+        assert np.array_equal(h.read(), alone(pkg, s, s["steps"]))
+        h.close()
+
+
+def test_graph_replay_keeps_stepping(pkg):
+    specs = draw_batch(6, seed=6, edge=(5, 40), steps=(3, 17))
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b:
+        for _ in range(3):
+            b.run(use_graph=True)
+        b.wait()
+    for s, h in zip(specs, heats):
+        assert np.array_equal(h.read(), alone(pkg, s, 3 * s["steps"]))
+        h.close()
+
+
+def test_batch_against_oracle(pkg):
+    specs = draw_batch(4, seed=7, edge=(8, 48), steps=(10, 40))
+    for s in specs:
+        s["dtype"] = "f64"
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b:
+        b.run().wait()
+    for s, h in zip(specs, heats):
+        assert rel_max_err(h.read(), oracle.heat_run(s["u0"], s["r"], s["steps"])) <= F64_REL
+        h.close()
+
+
+def test_batch_rejects_bad_input(pkg):
+    a = pkg.Heat(8, 8, 8, 0.1)
+    fx = pkg.Heat(8, 8, 8, 0.1, flags=pkg.HS_FIXED64)
+    for handles, steps in (([a, a], [1, 1]), ([fx], [1]), ([a], [-1])):
+        with pytest.raises(pkg.HeatCGError):
+            pkg.HeatBatch(handles, steps)
+    a.close()
+    fx.close()
+
+
+def test_batch_workload_256_grids_subset(pkg):
+    """The batching workload's recipe (256 grids, edges log-uniform in [16, 128],
+    r ~ U[0.05, 0.16], steps ~ U[50, 500], FP32 and FP64); every 16th grid is
+    checked against a run alone."""
+    specs = draw_batch(256, seed=20261202)
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b:
+        b.run(use_graph=True).wait()
+    for i in range(0, 256, 16):
+        assert np.array_equal(heats[i].read(), alone(pkg, specs[i], specs[i]["steps"]))
+    for h in heats:
+        h.close()
