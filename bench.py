@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--heat-mode", choices=sorted(HEAT_MODES), default="f64",
                     help="arithmetic of the timed heat segment")
+    ap.add_argument("--workload", choices=["default", "precision"], default="default",
+                    help="default: the timed heat + CG step; precision: the 1024^3 FP32 heat "
+                         "and 512^3 mixed-precision CG comparison (one run, no timing contract)")
     ap.add_argument("--tdepth", type=int, default=0,
                     help="steps per pass of the timed heat handle (0: library choice)")
     ap.add_argument("--no-side", action="store_true",
@@ -134,6 +137,75 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.rows)}
+
+
+def batching_side(pkg, stream):
+    """The batching workload: 256 heat grids (edges log-uniform in [16, 128],
+    FP64/FP32, r ~ U[0.05, 0.16], steps ~ U{50..500}) in one persistent launch
+    replayed from a CUDA graph, against the same grids stepped one handle at a
+    time; and 64 CG solves (edges in [32, 128], rtol 1e-8) batched against one
+    at a time."""
+    import torch
+
+    from workloads import cg_batch_specs, heat_batch_specs
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    specs = heat_batch_specs(256)
+    heats = []
+    for s in specs:
+        nz, ny, nx = s["shape"]
+        h = pkg.Heat(nx, ny, nz, s["r"], dtype=s["dtype"], stream=stream, tdepth=1)
+        h.upload(s["u0"].astype(h.np_dtype))
+        heats.append(h)
+    out = {}
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs], stream=stream) as b:
+        b.run(use_graph=True).wait()                      # warm-up (captures the graph)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        b.run(use_graph=True)
+        e1.record(stream)
+        b.wait()
+        ms = e0.elapsed_time(e1)
+        out["heat_256"] = {"lups": b.lups, "ms": ms, "glups": b.lups / (ms * 1e-3) / 1e9,
+                           "blocks": b.blocks, "launches_per_run": 1}
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for s, h in zip(specs, heats):
+        h.step(s["steps"])
+    e1.record(stream)
+    e1.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    out["heat_256"]["alone_ms"] = ms1
+    out["heat_256"]["speedup_vs_alone"] = ms1 / out["heat_256"]["ms"]
+    for h in heats:
+        h.close()
+    cg_specs = cg_batch_specs(64)
+    ops = [pkg.Operator.stencil(nx, ny, nz) for (nz, ny, nx), _ in cg_specs]
+    bs = [torch.from_numpy(b).cuda() for _, b in cg_specs]
+    with pkg.CGBatch(ops, stream=stream) as cb:
+        cb.run(bs, rtol=1e-8, max_iter=20000)             # warm-up
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        _, infos = cb.run(bs, rtol=1e-8, max_iter=20000)
+        e1.record(stream)
+        e1.synchronize()
+        msb = e0.elapsed_time(e1)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    iters = 0
+    for op, b in zip(ops, bs):
+        with pkg.CG(op, stream=stream) as cg:
+            _, inf = cg.run(b, rtol=1e-8, max_iter=20000)
+            iters += inf["iters"]
+    e1.record(stream)
+    e1.synchronize()
+    msa = e0.elapsed_time(e1)
+    out["cg_64"] = {"ms": msb, "alone_ms": msa, "speedup_vs_alone": msa / msb,
+                    "total_iters": sum(i["iters"] for i in infos),
+                    "all_converged": all(i["converged"] for i in infos)}
+    return out
 
 
 def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind, tdepth=1):
@@ -478,6 +550,29 @@ def run_ours(args):
             entry["max_rel_diff_vs_f64_gpu"] = err / refmax
         line["heat_modes"] = side
 
+    # ---- batching: 256 uneven heat grids in one persistent launch, 64 CG solves -
+    if not args.no_side:
+        line["batching"] = batching_side(pkg, stream)
+
+    # ---- mixed-precision CG beside the FP64 solves (untimed region) ------------
+    if not args.no_side:
+        mixed = {}
+        for kind, op in (("matrix_free", pkg.Operator.stencil(m, m, m)), ("csr", pkg.Operator.csr(*csr_dev))):
+            with pkg.CG(op, stream=stream, mixed=True) as cgm:
+                xm = torch.zeros_like(x_mf)
+                cgm.run(b_dev, xm, rtol=args.rtol, max_iter=200000)   # warm-up
+                xm.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, im = cgm.run(b_dev, xm, rtol=args.rtol, max_iter=200000)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                mixed[kind] = {"ms_per_solve": ms, "inner_iters": im["iters"],
+                               "refinements": im["refinements"], "relres_true": im["relres_true"],
+                               "speedup_vs_f64": line["cg"][kind]["ms_per_solve"] / ms}
+        line["cg"]["mixed_f32_krylov"] = mixed
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, host_cores())
 
@@ -491,10 +586,71 @@ def run_ours(args):
     return 0
 
 
+def run_precision(args):
+    """The precision workload: heat 1024^3 FP32 (storage and arithmetic),
+    r = 0.1, 2000 steps, max error against the FIXED64 path (FP64 interface,
+    parity-tested against the FP64 oracle); CG on 512^3 to rtol 1e-10 with
+    FP32 Krylov vectors and FP64 refinement, beside FP64 CG."""
+    import numpy as np
+    import torch
+
+    from paper_2608_11882_gb300.build import build
+    build()
+    import paper_2608_11882_gb300 as pkg
+    from workloads import cg_rhs, heat_u0_modes
+
+    stream = torch.cuda.current_stream()
+    n, steps, r = 1024, 2000, 0.1
+    u0, _, _ = heat_u0_modes(n, n, n, seed=SEED)
+    res = {}
+    fields = {}
+    for mode, dtype, flags in (("f32", "f32", 0), ("fixed64", "f64", pkg.HS_FIXED64)):
+        src = torch.from_numpy(u0).cuda()
+        if dtype == "f32":
+            src = src.float()
+        with pkg.Heat(n, n, n, r, dtype=dtype, flags=flags, stream=stream) as h:
+            h.upload(src)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(steps)
+            e1.record(stream)
+            out = torch.empty_like(src)
+            h.read(out)
+            ms = e0.elapsed_time(e1)
+        res[mode] = {"glups": float(n) ** 3 * steps / (ms * 1e-3) / 1e9, "ms": ms}
+        fields[mode] = out.double()
+        del src
+    ref = fields["fixed64"]
+    err = float((fields["f32"] - ref).abs().max())
+    res["f32"]["max_abs_err_vs_fixed64"] = err
+    res["f32"]["max_rel_err_vs_fixed64"] = err / float(ref.abs().max())
+    del fields, ref
+    m = 512
+    b = torch.from_numpy(cg_rhs(m ** 3, seed=SEED)).cuda()
+    cgres = {}
+    for name, kw in (("f64", {}), ("mixed_f32_krylov", {"mixed": True})):
+        with pkg.CG(pkg.Operator.stencil(m, m, m), stream=stream, **kw) as cg:
+            x = torch.zeros_like(b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = cg.run(b, x, rtol=1e-10, max_iter=400000)
+            e1.record(stream)
+            e1.synchronize()
+            cgres[name] = {"ms": e0.elapsed_time(e1), "iters": info["iters"],
+                           "refinements": info["refinements"], "relres_true": info["relres_true"],
+                           "converged": info["converged"]}
+    line = {"workload": "precision: heat 1024^3 FP32 r=0.1 2000 steps; CG 512^3 matrix-free rtol 1e-10",
+            "heat": res, "cg": cgres}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

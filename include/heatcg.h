@@ -263,6 +263,20 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
 /* Release a CG context (synchronises its stream). */
 int cg_destroy(hs_cg_t c);
 
+/* Batched CG: n independent systems (each its own operator, device b and x)
+ * solved together -- three kernel launches per iteration for the whole batch.
+ * Each system uses the row partition and reduction order its own cg_run
+ * would use, so its results equal solving it alone bit for bit; a system
+ * stops when it reaches rtol or max_iter while the others go on.  infos (may
+ * be NULL) receives one hs_cg_info per system.  Returns HS_OK when every
+ * system converged, HS_ENOCONV if any did not (x and infos filled anyway).
+ * Operators must be device memory and outlive the batch. */
+typedef struct hs_cg_batch* hs_cg_batch_t;
+int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* stream);
+int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double rtol,
+                 int32_t max_iter, hs_cg_info* infos);
+int cg_batch_destroy(hs_cg_batch_t b);
+
 /* One-shot form: cg_create + cg_run (device b and x) + cg_destroy. */
 int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
              hs_cg_info* info, void* stream);

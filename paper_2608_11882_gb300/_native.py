@@ -78,6 +78,9 @@ def _load():
         "cg_create_mixed": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), ctypes.POINTER(hs_cg_mixed_opts), vp],
         "cg_run": [vp, vp, vp, ctypes.c_int, dbl, i32, ctypes.POINTER(hs_cg_info)],
         "cg_destroy": [vp],
+        "cg_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), i32, vp],
+        "cg_batch_run": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, ctypes.POINTER(hs_cg_info)],
+        "cg_batch_destroy": [vp],
         "cg_solve": [ctypes.POINTER(hs_op), vp, vp, dbl, i32, ctypes.POINTER(hs_cg_info), vp],
     }
     for name, args in sig.items():
@@ -214,6 +217,28 @@ def cg_run(c: int, b_ptr: int, x_ptr: int, host_buffers: bool, rtol: float, max_
                     ctypes.byref(info))
     check(rc, "cg_run", ok=(HS_OK, HS_ENOCONV))
     return rc, info
+
+
+def cg_batch_create(ops, stream: int = 0) -> int:
+    n = len(ops)
+    arr = (hs_op * n)(*ops)
+    b = ctypes.c_void_p()
+    check(lib.cg_batch_create(ctypes.byref(b), arr, n, stream), "cg_batch_create")
+    return b.value
+
+
+def cg_batch_run(b: int, b_ptrs, x_ptrs, rtol: float, max_iter: int):
+    n = len(b_ptrs)
+    bs = (ctypes.c_void_p * n)(*b_ptrs)
+    xs = (ctypes.c_void_p * n)(*x_ptrs)
+    infos = (hs_cg_info * n)()
+    rc = lib.cg_batch_run(b, bs, xs, float(rtol), int(max_iter), infos)
+    check(rc, "cg_batch_run", ok=(HS_OK, HS_ENOCONV))
+    return rc, list(infos)
+
+
+def cg_batch_destroy(b: int) -> None:
+    check(lib.cg_batch_destroy(b), "cg_batch_destroy")
 
 
 def cg_destroy(c: int) -> None:

@@ -249,3 +249,44 @@ class CG:
             self.close()
         except Exception:
             pass
+
+
+class CGBatch:
+    """Several CG systems solved together (cg_batch_create / cg_batch_run)."""
+
+    def __init__(self, ops, stream=None):
+        self.ops = list(ops)
+        self.stream = _stream_handle(stream)
+        self.handle = native.cg_batch_create([o.op for o in self.ops], self.stream)
+
+    def run(self, bs, xs=None, rtol: float = 1e-8, max_iter: int = 10000):
+        """bs, xs: lists of torch CUDA float64 tensors (xs are start vectors and
+        receive the solutions; zeros when omitted).  Returns (xs, infos)."""
+        torch = _torch()
+        if xs is None:
+            xs = [torch.zeros_like(b) for b in bs]
+        for o, b, x in zip(self.ops, bs, xs):
+            if b.numel() != o.n or x.numel() != o.n or not (b.is_cuda and x.is_cuda):
+                raise ValueError("each b and x must be a CUDA tensor of its system's size")
+        rc, infos = native.cg_batch_run(self.handle, [b.data_ptr() for b in bs],
+                                        [x.data_ptr() for x in xs], rtol, max_iter)
+        return xs, [{"iters": i.iters, "status": i.status, "relres_recur": i.relres_recur,
+                     "relres_true": i.relres_true, "converged": i.status == native.HS_OK}
+                    for i in infos]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.cg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -60,6 +60,46 @@ __device__ __forceinline__ double sum_partials(const double* partials, int m, do
     return block_sum<kCgBlock>(v, sh);
 }
 
+// (A p)[row] for the matrix-free 7-point operator: 6 p - sum of the interior
+// face neighbours; missing neighbours (outside the box) are Dirichlet zeros.
+__device__ __forceinline__ double apply_stencil_row(const OpDev& A, const double* __restrict__ p,
+                                                    int64_t row)
+{
+    const int nx = A.nx, ny = A.ny;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int i = (int)(row % nx);
+    const int64_t jk = row / nx;
+    const int j = (int)(jk % ny);
+    const int k = (int)(jk / ny);
+    const double zm = k > 0 ? __ldg(p + row - sxy) : 0.0;
+    const double ym = j > 0 ? __ldg(p + row - nx) : 0.0;
+    const double xm = i > 0 ? __ldg(p + row - 1) : 0.0;
+    const double xp = i < nx - 1 ? __ldg(p + row + 1) : 0.0;
+    const double yp = j < ny - 1 ? __ldg(p + row + nx) : 0.0;
+    const double zp = k < A.nz - 1 ? __ldg(p + row + sxy) : 0.0;
+    const double s = ((zm + ym) + (xm + xp)) + (yp + zp);
+    return __fma_rn(6.0, __ldg(p + row), -s);
+}
+
+// (A p)[row] for CSR: the row loop of Algorithm "spmv" (b), accumulated with FMA.
+__device__ __forceinline__ double apply_csr_row(const OpDev& A, const double* __restrict__ p,
+                                                int64_t row)
+{
+    double s = 0.0;
+    const int e = __ldg(A.rowptr + row + 1);
+    for (int t = __ldg(A.rowptr + row); t < e; ++t)
+        s = __fma_rn(__ldg(A.val + t), __ldg(p + __ldg(A.col + t)), s);
+    return s;
+}
+
+template <int KIND>
+__device__ __forceinline__ double apply_row(const OpDev& A, const double* __restrict__ p,
+                                            int64_t row)
+{
+    if (KIND == HS_OP_STENCIL7) return apply_stencil_row(A, p, row);
+    return apply_csr_row(A, p, row);
+}
+
 struct CgMixed;   // mixed-precision state (cg_mixed.cu)
 
 int check_op(const hs_op* A);

@@ -102,3 +102,29 @@ def lap7_csr(nx: int, ny: int, nz: int):
     col = cols.reshape(-1)[mask]
     val = vals.reshape(-1)[mask]
     return rowptr.astype(np.int32), np.ascontiguousarray(col), np.ascontiguousarray(val)
+
+
+def heat_batch_specs(n: int = 256, seed: int = DEFAULT_SEED, edge=(16, 128), steps=(50, 500)):
+    """The batching workload's heat grids: edges log-uniform in [16, 128]
+    (independently per axis, so non-cubic), r ~ U[0.05, 0.16], steps ~ U{50..500},
+    FP64 and FP32 alternating; u0 ~ U[-1, 1].  Returns a list of dicts."""
+    rng = np.random.default_rng([seed, 3])
+    out = []
+    for g in range(n):
+        nz, ny, nx = (int(v) for v in np.round(np.exp(rng.uniform(np.log(edge[0]), np.log(edge[1]), 3))))
+        out.append(dict(shape=(nz, ny, nx), r=float(rng.uniform(0.05, 0.16)),
+                        steps=int(rng.integers(steps[0], steps[1] + 1)),
+                        dtype="f32" if g % 2 else "f64",
+                        u0=rng.uniform(-1.0, 1.0, size=(nz, ny, nx))))
+    return out
+
+
+def cg_batch_specs(n: int = 64, seed: int = DEFAULT_SEED, edge=(32, 128)):
+    """The batching workload's CG systems: 7-point Laplacians with edges
+    log-uniform in [32, 128] per axis, b ~ N(0, 1).  Returns (shape, b) pairs."""
+    rng = np.random.default_rng([seed, 4])
+    out = []
+    for i in range(n):
+        nz, ny, nx = (int(v) for v in np.round(np.exp(rng.uniform(np.log(edge[0]), np.log(edge[1]), 3))))
+        out.append(((nz, ny, nx), rng.standard_normal(nx * ny * nz)))
+    return out
