@@ -61,9 +61,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--heat-mode", choices=sorted(HEAT_MODES), default="f64",
                     help="arithmetic of the timed heat segment")
-    ap.add_argument("--workload", choices=["default", "precision"], default="default",
+    ap.add_argument("--workload", choices=["default", "precision", "serving"], default="default",
                     help="default: the timed heat + CG step; precision: the 1024^3 FP32 heat "
-                         "and 512^3 mixed-precision CG comparison (one run, no timing contract)")
+                         "and 512^3 mixed-precision CG comparison; serving: the continuous-"
+                         "batching request stream (these two: one run, no timing contract)")
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests in the trace")
     ap.add_argument("--tdepth", type=int, default=0,
                     help="steps per pass of the timed heat handle (0: library choice)")
     ap.add_argument("--no-side", action="store_true",
@@ -645,12 +647,54 @@ def run_precision(args):
     return 0
 
 
+def run_serving(args):
+    """The serving workload: a seeded Poisson stream of heat (75%) and CG (25%)
+    requests, edges log-uniform in [32, 384] per axis, steps log-uniform in
+    [10, 2000], FP32/FP64 half each, admitted by free HBM with fields resident.
+    Capacity is measured closed-loop (every request arriving at once); the
+    same trace is then replayed at 0.5, 0.7 and 0.9 of that request rate."""
+    import torch
+
+    from paper_2608_11882_gb300.build import build
+    build()
+    from paper_2608_11882_gb300.serve import GpuBackend, Server, poisson_trace, summarize
+
+    base = poisson_trace(args.requests, rate=1.0, seed=SEED)   # arrivals for rate 1, rescaled below
+    unit = [q.arrival for q in base]
+
+    def serve(scale):
+        for q, a in zip(base, unit):
+            q.arrival = a * scale
+        be = GpuBackend(workers=4)
+        srv = Server(be, quantum=64, max_slots=32)
+        res = srv.run(base)
+        be.close()
+        out = summarize(res, base, srv.makespan)
+        out.update({"peak_slots": srv.peak_slots, "peak_gb": srv.peak_bytes / 1e9,
+                    "rejected": len(srv.rejected)})
+        return out
+
+    closed = serve(0.0)
+    capacity = args.requests / closed["makespan_s"]
+    line = {"workload": f"serving: {args.requests} Poisson-arrival requests (heat 75% / CG 25%), "
+                        "edges log-uniform [32, 384], steps log-uniform [10, 2000], FP32/FP64 50/50, "
+                        "CG rtol 1e-8", "seed": SEED,
+            "closed_loop": closed, "capacity_req_per_s": capacity, "loads": {}}
+    for load in (0.5, 0.7, 0.9):
+        line["loads"][str(load)] = serve(1.0 / (load * capacity))
+    torch.cuda.synchronize()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

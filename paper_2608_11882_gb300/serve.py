@@ -1,0 +1,258 @@
+"""Continuous-batching solve server for heat and CG requests.
+
+Requests (heat: a field, r and a step count; CG: a right-hand side and a
+tolerance) arrive over time.  The scheduler admits a request as soon as it has
+arrived, a slot is free and its device memory fits the free-HBM budget; the
+admitted request's field stays resident on the device until it completes.
+Every tick all admitted heat requests advance together by up to `quantum`
+steps in ONE batched persistent launch (heat_batch_*), so requests that arrive
+while others are running join the next tick's batch.  CG requests are solved
+on worker threads, each with its own CUDA stream, so they overlap on the
+device with the heat batches and with each other.  The per-point and
+per-iteration arithmetic is the library's, and a request's result does not
+depend on what it ran beside: heat equals heat_step alone and CG equals
+cg_run alone, bit for bit.
+
+The GPU work goes through a backend object so the scheduling logic can be
+exercised without a GPU (``FakeBackend`` in the tests).  Latency is
+completion minus arrival; throughput is heat lattice-point updates per
+second of makespan.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str                    # "heat" or "cg"
+    shape: tuple                 # (nz, ny, nx)
+    dtype: str = "f64"           # heat: "f64" or "f32"; CG is FP64
+    r: float = 0.1               # heat
+    steps: int = 0               # heat
+    rtol: float = 1e-8           # CG
+    max_iter: int = 100000       # CG
+    arrival: float = 0.0         # seconds after the start of the run
+    payload: object = None       # heat: u0 (nz, ny, nx); CG: b (n,)
+
+    @property
+    def points(self) -> int:
+        return int(np.prod(self.shape))
+
+    @property
+    def lups(self) -> int:
+        return self.points * self.steps if self.kind == "heat" else 0
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    arrival: float
+    admitted: float
+    completed: float
+    output: object = None
+    info: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float:
+        return self.completed - self.arrival
+
+
+def device_bytes(req: Request) -> int:
+    """Device memory a request holds while admitted (both padded field buffers
+    for heat; r, p, q, b and x for CG), with row padding to 128 bytes."""
+    nz, ny, nx = req.shape
+    if req.kind == "heat":
+        elem = 8 if req.dtype == "f64" else 4
+        pitch = -(-(32 // elem + nx + 1) * elem // 128) * 128
+        return 2 * pitch * (ny + 2) * (nz + 2)
+    return 5 * 8 * req.points
+
+
+def percentile(values, q: float) -> float:
+    """Nearest-rank percentile (q in [0, 100])."""
+    if not values:
+        return float("nan")
+    v = sorted(values)
+    k = max(0, min(len(v) - 1, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return float(v[k])
+
+
+class GpuBackend:
+    """The library on the current CUDA device: heat handles advanced by
+    heat_batch, CG contexts on per-worker streams."""
+
+    def __init__(self, workers: int = 4):
+        import torch
+
+        import paper_2608_11882_gb300 as pkg
+        self.torch = torch
+        self.pkg = pkg
+        self.stream = torch.cuda.Stream()
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self._local = threading.local()
+
+    def free_bytes(self) -> int:
+        return int(self.torch.cuda.mem_get_info()[0])
+
+    def heat_open(self, req: Request):
+        nz, ny, nx = req.shape
+        h = self.pkg.Heat(nx, ny, nz, req.r, dtype=req.dtype, stream=self.stream, tdepth=1)
+        h.upload(np.ascontiguousarray(req.payload, dtype=h.np_dtype))
+        return h
+
+    def heat_advance(self, handles, steps) -> None:
+        with self.pkg.HeatBatch(handles, steps, stream=self.stream) as b:
+            b.run(use_graph=False)
+            b.wait()
+
+    def heat_close(self, h):
+        out = h.read()
+        h.close()
+        return out
+
+    def _cg_job(self, req: Request):
+        torch = self.torch
+        s = getattr(self._local, "stream", None)
+        if s is None:
+            s = self._local.stream = torch.cuda.Stream()
+        nz, ny, nx = req.shape
+        with torch.cuda.stream(s):
+            b = torch.from_numpy(np.ascontiguousarray(req.payload, dtype=np.float64)).cuda(non_blocking=False)
+            with self.pkg.CG(self.pkg.Operator.stencil(nx, ny, nz), stream=s) as cg:
+                x, info = cg.run(b, rtol=req.rtol, max_iter=req.max_iter)
+            out = x.cpu().numpy()
+        return out, info
+
+    def cg_submit(self, req: Request):
+        return self.pool.submit(self._cg_job, req)
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
+class Server:
+    """Continuous-batching scheduler (see the module docstring).
+
+    hbm_budget: bytes the admitted requests may hold at once (default: the
+    backend's free device memory minus `reserve` at start).  max_slots:
+    requests admitted at once.  quantum: heat steps per tick.
+    """
+
+    def __init__(self, backend, hbm_budget: int | None = None, reserve: int = 2 << 30,
+                 max_slots: int = 32, quantum: int = 64, clock=time.perf_counter,
+                 sleep=time.sleep):
+        self.backend = backend
+        self.budget = hbm_budget if hbm_budget is not None else max(0, backend.free_bytes() - reserve)
+        self.max_slots = max_slots
+        self.quantum = quantum
+        self.clock = clock
+        self.sleep = sleep
+        self.peak_bytes = 0
+        self.peak_slots = 0
+        self.rejected = []
+
+    def run(self, requests):
+        """Serve requests (their arrival offsets relative to the start) and
+        return the results in request-id order."""
+        pending = sorted(requests, key=lambda q: (q.arrival, q.rid))
+        for q in pending:
+            if device_bytes(q) > self.budget:
+                self.rejected.append(q.rid)
+        pending = [q for q in pending if q.rid not in set(self.rejected)]
+        t0 = self.clock()
+        used = 0
+        heat = {}          # rid -> [req, handle, remaining, admitted]
+        cg = {}            # rid -> [req, future, admitted]
+        results = {}
+        i = 0
+        while i < len(pending) or heat or cg:
+            now = self.clock() - t0
+            # admit everything that has arrived and fits
+            while i < len(pending) and pending[i].arrival <= now:
+                q = pending[i]
+                need = device_bytes(q)
+                if len(heat) + len(cg) >= self.max_slots or used + need > self.budget:
+                    break
+                used += need
+                if q.kind == "heat":
+                    heat[q.rid] = [q, self.backend.heat_open(q), q.steps, now]
+                else:
+                    cg[q.rid] = [q, self.backend.cg_submit(q), now]
+                i += 1
+            self.peak_bytes = max(self.peak_bytes, used)
+            self.peak_slots = max(self.peak_slots, len(heat) + len(cg))
+            worked = False
+            if heat:
+                live = [v for v in heat.values() if v[2] > 0]
+                if live:
+                    steps = [min(self.quantum, v[2]) for v in live]
+                    self.backend.heat_advance([v[1] for v in live], steps)
+                    for v, s in zip(live, steps):
+                        v[2] -= s
+                    worked = True
+                now = self.clock() - t0
+                for rid in [r for r, v in heat.items() if v[2] == 0]:
+                    q, h, _, adm = heat.pop(rid)
+                    out = self.backend.heat_close(h)
+                    results[rid] = Result(rid, "heat", q.arrival, adm, self.clock() - t0, out)
+                    used -= device_bytes(q)
+            for rid in [r for r, v in cg.items() if v[1].done()]:
+                q, fut, adm = cg.pop(rid)
+                out, info = fut.result()
+                results[rid] = Result(rid, "cg", q.arrival, adm, self.clock() - t0, out, info)
+                used -= device_bytes(q)
+                worked = True
+            if not worked:
+                # idle: wait a little for the next arrival or a CG completion
+                wait = 0.0005
+                if i < len(pending) and not cg:
+                    wait = min(max(pending[i].arrival - (self.clock() - t0), 0.0), 0.001)
+                self.sleep(wait)
+        self.makespan = self.clock() - t0
+        return [results[r] for r in sorted(results)]
+
+
+def summarize(results, requests, makespan: float) -> dict:
+    """p50/p99 latency per kind and overall, heat GLUP/s over the makespan."""
+    by = {"heat": [], "cg": []}
+    for r in results:
+        by[r.kind].append(r.latency)
+    lups = sum(q.lups for q in requests if q.rid in {r.rid for r in results})
+    out = {"requests": len(results), "makespan_s": makespan,
+           "glups": lups / makespan / 1e9 if makespan > 0 else float("nan"),
+           "latency_s": {"p50": percentile([r.latency for r in results], 50),
+                         "p99": percentile([r.latency for r in results], 99)}}
+    for k, v in by.items():
+        out[f"latency_{k}_s"] = {"p50": percentile(v, 50), "p99": percentile(v, 99), "n": len(v)}
+    return out
+
+
+def poisson_trace(n: int, rate: float, seed: int, edge=(32, 384), steps=(10, 2000),
+                  heat_frac: float = 0.75, f32_frac: float = 0.5, rtol: float = 1e-8):
+    """Seeded requests: exponential inter-arrival times of mean 1/rate; heat
+    with probability heat_frac; edges log-uniform per axis in `edge`; steps
+    log-uniform in `steps`; FP32/FP64 by f32_frac; u0 ~ U[-1, 1]; b ~ N(0, 1)."""
+    rng = np.random.default_rng([seed, 5])
+    t = 0.0
+    reqs = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate)
+        shape = tuple(int(v) for v in np.round(np.exp(rng.uniform(np.log(edge[0]), np.log(edge[1]), 3))))
+        if rng.uniform() < heat_frac:
+            st = int(round(math.exp(rng.uniform(math.log(steps[0]), math.log(steps[1])))))
+            dt = "f32" if rng.uniform() < f32_frac else "f64"
+            reqs.append(Request(rid, "heat", shape, dt, float(rng.uniform(0.05, 0.16)), st,
+                                arrival=t, payload=rng.uniform(-1.0, 1.0, size=shape)))
+        else:
+            reqs.append(Request(rid, "cg", shape, "f64", rtol=rtol, arrival=t,
+                                payload=rng.standard_normal(int(np.prod(shape)))))
+    return reqs

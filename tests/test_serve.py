@@ -1,0 +1,109 @@
+"""The serving scheduler's logic on the CPU, with a fake backend: admission by
+an injected free-HBM budget and by slots, quanta of heat steps, continuous
+joining of late arrivals, percentiles."""
+from concurrent.futures import Future
+
+import numpy as np
+
+from paper_2608_11882_gb300.serve import (Request, Server, device_bytes, percentile, poisson_trace,
+                                          summarize)
+
+
+class FakeBackend:
+    def __init__(self, free=1 << 40):
+        self.free = free
+        self.advances = []      # (rids, steps) per heat batch
+        self.open = set()
+
+    def free_bytes(self):
+        return self.free
+
+    def heat_open(self, req):
+        self.open.add(req.rid)
+        return {"rid": req.rid, "done": 0}
+
+    def heat_advance(self, handles, steps):
+        for h, s in zip(handles, steps):
+            h["done"] += s
+        self.advances.append(([h["rid"] for h in handles], list(steps)))
+
+    def heat_close(self, h):
+        self.open.discard(h["rid"])
+        return h["done"]
+
+    def cg_submit(self, req):
+        f = Future()
+        f.set_result((np.zeros(req.points), {"iters": 1}))
+        return f
+
+
+def heat(rid, shape=(8, 8, 8), steps=100, arrival=0.0):
+    return Request(rid, "heat", shape, "f64", 0.1, steps, arrival=arrival)
+
+
+def test_every_request_gets_exactly_its_steps():
+    be = FakeBackend()
+    reqs = [heat(i, steps=s) for i, s in enumerate([1, 64, 65, 200, 0, 7])]
+    res = Server(be, quantum=64).run(reqs)
+    assert [r.output for r in res] == [1, 64, 65, 200, 0, 7]
+    assert all(max(st) <= 64 for _, st in be.advances)
+    assert not be.open
+
+
+def test_admission_respects_budget_and_slots():
+    be = FakeBackend()
+    reqs = [heat(i, shape=(16, 16, 16), steps=50) for i in range(10)]
+    one = device_bytes(reqs[0])
+    srv = Server(be, hbm_budget=3 * one, max_slots=8, quantum=10)
+    res = srv.run(reqs)
+    assert len(res) == 10 and srv.peak_bytes <= 3 * one and srv.peak_slots <= 3
+    srv = Server(FakeBackend(), hbm_budget=100 * one, max_slots=2, quantum=10)
+    srv.run(reqs)
+    assert srv.peak_slots <= 2
+
+
+def test_requests_that_can_never_fit_are_rejected():
+    be = FakeBackend()
+    small, big = heat(0, (8, 8, 8)), heat(1, (64, 64, 64))
+    srv = Server(be, hbm_budget=device_bytes(small) * 2, quantum=64)
+    res = srv.run([small, big])
+    assert [r.rid for r in res] == [0] and srv.rejected == [1]
+
+
+def test_default_budget_comes_from_free_memory():
+    srv = Server(FakeBackend(free=10 << 30), reserve=2 << 30)
+    assert srv.budget == 8 << 30
+
+
+def test_late_arrivals_join_running_batches():
+    be = FakeBackend()
+    reqs = [heat(0, steps=2000, arrival=0.0), heat(1, steps=100, arrival=0.01)]
+    t = {"now": 0.0}
+
+    def clock():
+        return t["now"]
+
+    def sleep(dt):
+        t["now"] += max(dt, 1e-4)
+
+    class Stepping(FakeBackend):
+        def heat_advance(self, handles, steps):
+            super().heat_advance(handles, steps)
+            t["now"] += 0.005          # each batch takes 5 ms of "device time"
+
+    be = Stepping()
+    res = Server(be, quantum=64, clock=clock, sleep=sleep).run(reqs)
+    assert [r.output for r in res] == [2000, 100]
+    joint = [rids for rids, _ in be.advances if rids == [0, 1]]
+    assert joint, "request 1 should have joined request 0's batches"
+    assert res[1].completed < res[0].completed
+
+
+def test_percentiles_and_summary():
+    assert percentile([3, 1, 2, 4], 50) == 2
+    assert percentile(list(range(1, 101)), 99) == 99
+    reqs = poisson_trace(20, rate=100.0, seed=1, edge=(8, 16), steps=(5, 20))
+    assert len(reqs) == 20 and all(b.arrival >= a.arrival for a, b in zip(reqs, reqs[1:]))
+    res = Server(FakeBackend(), quantum=8).run(reqs)
+    s = summarize(res, reqs, 1.0)
+    assert s["requests"] == 20 and s["latency_s"]["p99"] >= s["latency_s"]["p50"]
