@@ -75,6 +75,10 @@ def _load():
         lib.oracle_heat_run_timed.argtypes = lib.oracle_heat_run.argtypes + [dp]
         lib.oracle_heat_run_timed.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_heat_vk_run.argtypes = [ctypes.c_int32] * 3 + [ctypes.c_double, ctypes.c_int64,
+                                                                   dp, dp, ctypes.c_int32,
+                                                                   ctypes.c_double, ctypes.c_int32]
+        lib.oracle_heat_vk_run.restype = ctypes.c_int
         lib.oracle_lap7_apply.argtypes = [ctypes.c_int32] * 3 + [dp, dp, ctypes.c_int32]
         lib.oracle_csr_spmv.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int32]
         lib.oracle_dot.argtypes = [ctypes.c_int64, dp, dp]
@@ -115,6 +119,23 @@ def heat_run(u0: np.ndarray, r: float, n_steps: int, threads: int = 1,
     if rc != 0:
         raise ValueError(f"oracle_heat_run failed with {rc}")
     return (out, secs.value) if return_seconds else out
+
+
+def heat_vk_run(u0: np.ndarray, r: float, n_steps: int, threads: int = 1,
+                kappa_const: float = 0.0, with_source: bool = True) -> np.ndarray:
+    """The paper's variable-coefficient update (Section 4, Eqs. 1-4):
+    kappa = 0.5 + 0.45 sin sin sin, f = 1 + cos cos cos, dt = r h_min^2,
+    u' = u + dt f + sum_d dt/(2 h_d^2) D_d with face-averaged D_d
+    (D_x = (k[i+1]+k[i])(u[i+1]-u[i]) - (k[i]+k[i-1])(u[i]-u[i-1])).
+    kappa_const > 0 makes kappa that constant; with_source=False drops f."""
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    nz, ny, nx = u0.shape
+    out = np.empty_like(u0)
+    rc = _load().oracle_heat_vk_run(nx, ny, nz, float(r), int(n_steps), _ptr(u0), _ptr(out),
+                                    int(threads), float(kappa_const), int(bool(with_source)))
+    if rc != 0:
+        raise ValueError(f"oracle_heat_vk_run failed with {rc}")
+    return out
 
 
 def lap7_apply(p: np.ndarray, threads: int = 1) -> np.ndarray:

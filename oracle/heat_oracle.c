@@ -33,6 +33,7 @@
  * Each output point depends only on the previous time level, so the OpenMP
  * loop gives results identical to one thread.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -136,4 +137,81 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/*
+ * The paper's variable-coefficient problem (Section 4, Eqs. 1-4):
+ *     du/dt = div(kappa grad u) + f,
+ *     kappa = 0.5 + 0.45 sin(pi x) sin(pi y) sin(pi z)      (Eq. 2)
+ *     f     = 1 + cos(pi x) cos(pi y) cos(pi z)               (Eq. 3)
+ *     u^{m+1} = u^m + dt f + dt/(2h^2) (Dx + Dy + Dz)          (Eq. 4)
+ * with the face-averaged differences (the paper does not print D; this is
+ * the reading consistent with beta = dt/(2h^2)):
+ *     Dx = (k[i+1] + k[i]) (u[i+1] - u[i]) - (k[i] + k[i-1]) (u[i] - u[i-1])
+ * On a grid of nx x ny x nz interior nodes, node i of the padded axis sits at
+ * x = i h_x, h_x = 1/(nx+1) (the boundary nodes at x = 0 and 1 carry kappa
+ * too).  dt = r h^2 with h = the smallest h_d (the paper's cubic grid has one
+ * h and dt = h^2/(12 kappa_max), i.e. r = 1/(12 * 0.95)); each axis gets its
+ * own beta_d = dt/(2 h_d^2).  Evaluation order (no FMA):
+ *     s  = (bx Dx + by Dy) + bz Dz,   u' = (u + dt f) + s.
+ * kappa_const > 0 replaces kappa by that constant, and with_source == 0 drops f
+ * (both used to pin this routine).
+ */
+int oracle_heat_vk_run(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_steps,
+                       const double* u0, double* u_out, int32_t nthreads, double kappa_const,
+                       int32_t with_source)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || n_steps < 0 || !u0 || !u_out) return -1;
+    if (nthreads < 1) nthreads = 1;
+    const double pi = 3.14159265358979323846;
+    const double hx = 1.0 / (nx + 1), hy = 1.0 / (ny + 1), hz = 1.0 / (nz + 1);
+    double h = hx;
+    if (hy < h) h = hy;
+    if (hz < h) h = hz;
+    const double dt = r * h * h;
+    const double bx = dt / (2.0 * hx * hx), by = dt / (2.0 * hy * hy), bz = dt / (2.0 * hz * hz);
+    const size_t total = (size_t)(nx + 2) * (size_t)(ny + 2) * (size_t)(nz + 2);
+    double* a = (double*)calloc(total, sizeof(double));
+    double* b = (double*)calloc(total, sizeof(double));
+    double* kap = (double*)calloc(total, sizeof(double));
+    double* fdt = (double*)calloc(total, sizeof(double));
+    if (!a || !b || !kap || !fdt) { free(a); free(b); free(kap); free(fdt); return -2; }
+    for (int64_t k = 0; k <= nz + 1; ++k)
+        for (int64_t j = 0; j <= ny + 1; ++j)
+            for (int64_t i = 0; i <= nx + 1; ++i) {
+                const size_t c = pad_index(i, j, k, nx, ny);
+                const double x = i * hx, y = j * hy, z = k * hz;
+                kap[c] = kappa_const > 0.0 ? kappa_const
+                                           : 0.5 + 0.45 * sin(pi * x) * sin(pi * y) * sin(pi * z);
+                fdt[c] = with_source ? dt * (1.0 + cos(pi * x) * cos(pi * y) * cos(pi * z)) : 0.0;
+            }
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j) {
+            const double* row = u0 + ((size_t)k * ny + j) * nx;
+            memcpy(a + pad_index(1, j + 1, k + 1, nx, ny), row, sizeof(double) * nx);
+        }
+    const int64_t sy = nx + 2, sz = (int64_t)(nx + 2) * (ny + 2);
+    for (int64_t m = 0; m < n_steps; ++m) {
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads)
+#endif
+        for (int64_t k = 1; k <= nz; ++k)
+            for (int64_t j = 1; j <= ny; ++j)
+                for (int64_t i = 1; i <= nx; ++i) {
+                    const size_t c = pad_index(i, j, k, nx, ny);
+                    const double u = a[c], kc = kap[c];
+                    const double dx = (kap[c + 1] + kc) * (a[c + 1] - u) - (kc + kap[c - 1]) * (u - a[c - 1]);
+                    const double dy = (kap[c + sy] + kc) * (a[c + sy] - u) - (kc + kap[c - sy]) * (u - a[c - sy]);
+                    const double dz = (kap[c + sz] + kc) * (a[c + sz] - u) - (kc + kap[c - sz]) * (u - a[c - sz]);
+                    const double s = (bx * dx + by * dy) + bz * dz;
+                    b[c] = (u + fdt[c]) + s;
+                }
+        double* t = a; a = b; b = t;
+    }
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            memcpy(u_out + ((size_t)k * ny + j) * nx, a + pad_index(1, j + 1, k + 1, nx, ny),
+                   sizeof(double) * nx);
+    free(a); free(b); free(kap); free(fdt);
+    return 0;
 }
