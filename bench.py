@@ -141,6 +141,37 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def paper_problem_side(pkg, stream):
+    """The paper's variable-coefficient problem at its N = 512 (510^3 interior
+    nodes, dt = h^2/(12 kappa_max)), 500 steps, FP64 and FP32.  The paper's
+    measured k = 6.4042e-11 s per point-step for OpenMP offload on one H100
+    (Table of used measurements) is 15.6 GLUP/s -- another GPU's number, for
+    context."""
+    import torch
+
+    from workloads import heat_u0_single_mode
+    n, steps = 510, 500
+    u0 = heat_u0_single_mode(n, n, n)
+    out = {"grid": "510^3 interior (paper N = 512)", "steps": steps, "r": 1.0 / (12 * 0.95),
+           "paper_h100_openmp_glups": 1.0 / 6.4042e-11 / 1e9}
+    for dtype in ("f64", "f32"):
+        src = torch.from_numpy(u0).cuda()
+        if dtype == "f32":
+            src = src.float()
+        with pkg.Heat(n, n, n, 1.0 / (12 * 0.95), dtype=dtype, flags=pkg.HS_VARKAPPA, stream=stream) as h:
+            h.upload(src).step(20)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h.upload(src)
+            e0.record(stream)
+            h.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        out[dtype] = {"glups": float(n) ** 3 * steps / (ms * 1e-3) / 1e9, "ms": ms}
+        del src
+    return out
+
+
 def batching_side(pkg, stream):
     """The batching workload: 256 heat grids (edges log-uniform in [16, 128],
     FP64/FP32, r ~ U[0.05, 0.16], steps ~ U{50..500}) in one persistent launch
@@ -555,6 +586,10 @@ def run_ours(args):
     # ---- batching: 256 uneven heat grids in one persistent launch, 64 CG solves -
     if not args.no_side:
         line["batching"] = batching_side(pkg, stream)
+
+    # ---- the paper's own problem: variable kappa, N = 512, 500 steps ---------------
+    if not args.no_side:
+        line["paper_problem"] = paper_problem_side(pkg, stream)
 
     # ---- mixed-precision CG beside the FP64 solves (untimed region) ------------
     if not args.no_side:

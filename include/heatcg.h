@@ -78,6 +78,19 @@ extern "C" {
  * Per step this costs integer instructions instead of FP64 ones, so on GPUs
  * whose FP64 pipe is narrow it runs at memory speed. */
 #define HS_FIXED64          0x8u
+/* The paper's variable-coefficient problem instead of the constant one
+ * (Section 4, Eqs. 1-4): du/dt = div(kappa grad u) + f with
+ * kappa = 0.5 + 0.45 sin(pi x) sin(pi y) sin(pi z), f = 1 + cos(pi x) cos(pi y)
+ * cos(pi z), and u' = u + dt f + sum_d dt/(2 h_d^2) D_d with face-averaged
+ * differences D_x = (k[i+1] + k[i])(u[i+1] - u[i]) - (k[i] + k[i-1])(u[i] - u[i-1])
+ * (the paper does not print D; this is the reading consistent with its
+ * beta = dt/(2h^2)).  Here r means dt / h_min^2 (the paper's choice is
+ * dt = h^2/(12 kappa_max), r = 1/(12 * 0.95)); the stability bound is
+ * r <= 1/(6 kappa_max).  kappa (on every node, boundary included) and dt f
+ * live on the device beside u, as in the paper's 1-GPU Baseline.  HS_F64 or
+ * HS_F32; excludes HS_FIXED64, HS_EXACT_ROUNDING, HS_SCHED_FULL and tdepth > 1;
+ * cannot join a heat batch. */
+#define HS_VARKAPPA         0x10u
 
 typedef struct hs_heat* hs_heat_t;
 

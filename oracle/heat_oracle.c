@@ -176,6 +176,9 @@ int oracle_heat_vk_run(int32_t nx, int32_t ny, int32_t nz, double r, int64_t n_s
     double* kap = (double*)calloc(total, sizeof(double));
     double* fdt = (double*)calloc(total, sizeof(double));
     if (!a || !b || !kap || !fdt) { free(a); free(b); free(kap); free(fdt); return -2; }
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads)
+#endif
     for (int64_t k = 0; k <= nz + 1; ++k)
         for (int64_t j = 0; j <= ny + 1; ++j)
             for (int64_t i = 0; i <= nx + 1; ++i) {

@@ -7,7 +7,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import _native as native
-from ._native import (HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_F32, HS_F64, HS_FIXED64, HS_OP_CSR,
+from ._native import (HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_F32, HS_F64, HS_FIXED64, HS_VARKAPPA,
+                      HS_OP_CSR,
                       HS_OP_STENCIL7, HS_SCHED_FULL, HeatCGError)
 
 __all__ = ["Heat", "Operator", "CG", "native", "HeatCGError", "HS_F64", "HS_F32",

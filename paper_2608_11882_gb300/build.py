@@ -17,7 +17,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libheatcg.so"
-SOURCES = ["api.cu", "heat.cu", "heat_tb.cu", "heat_stream.cu", "heat_batch.cu", "cg.cu",
+SOURCES = ["api.cu", "heat.cu", "heat_tb.cu", "heat_stream.cu", "heat_batch.cu", "heat_vk.cu", "cg.cu",
            "cg_mixed.cu", "cg_batch.cu"]
 HEADERS = [ROOT / "include" / "heatcg.h", CSRC / "common.cuh", CSRC / "heat_common.cuh", CSRC / "tma.cuh",
            CSRC / "cg_common.cuh"]

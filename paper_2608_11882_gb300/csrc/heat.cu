@@ -253,11 +253,16 @@ struct hs_heat {
     uint32_t tbox[2];      // box of maps[]
     uint32_t sbox[2];      // box of smaps[]
     int kc_stream;         // k-planes per block of the streaming Interior kernel
+    void* kap;             // HS_VARKAPPA: kappa on every padded node
+    void* fdt;             // HS_VARKAPPA: dt f on the interior
+    double vbx, vby, vbz;  // HS_VARKAPPA: dt / (2 h_d^2)
 };
 
 namespace {
 
-constexpr uint32_t kKnownFlags = HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64;
+constexpr uint32_t kKnownFlags =
+    HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64 | HS_VARKAPPA;
+constexpr double kKappaMax = 0.95;   // max of 0.5 + 0.45 sin sin sin (Section 4, Eq. 2)
 
 int check_desc(const hs_heat_desc* d)
 {
@@ -285,6 +290,17 @@ int check_desc(const hs_heat_desc* d)
         return fail(HS_EINVAL, "heat: tdepth %d not in {0, 1, 2, 3, 4}", d->tdepth);
     if ((d->flags & HS_SCHED_FULL) && d->tdepth > 1)
         return fail(HS_EINVAL, "heat: HS_SCHED_FULL runs one step per pass (tdepth 0 or 1)");
+    if (d->flags & HS_VARKAPPA) {
+        if (d->flags & (HS_FIXED64 | HS_EXACT_ROUNDING | HS_SCHED_FULL))
+            return fail(HS_EINVAL, "heat: HS_VARKAPPA runs plain FP64 or FP32, Interior + Boundary");
+        if (d->tdepth > 1) return fail(HS_EINVAL, "heat: HS_VARKAPPA runs one step per pass");
+        // the update stays a convex combination (without the source) while
+        // dt (kappa_max) sum_d 2/h_d^2 <= 1, which r = dt/h_min^2 <= 1/(6 kappa_max) ensures
+        if (d->r > 1.0 / (6.0 * kKappaMax) && !(d->flags & HS_ALLOW_UNSTABLE))
+            return fail(HS_EUNSTABLE, "heat: r = %.17g exceeds 1/(6 kappa_max) = %.6g", d->r,
+                        1.0 / (6.0 * kKappaMax));
+        return HS_OK;
+    }
     // Three-dimensional stability of the explicit update: r <= 1/6.
     if (d->r > 1.0 / 6.0 && !(d->flags & HS_ALLOW_UNSTABLE))
         return fail(HS_EUNSTABLE, "heat: r = %.17g exceeds the stability bound 1/6", d->r);
@@ -384,8 +400,27 @@ int launch_part(hs_heat* h, Part p, T param)
     return launch_full_t<T, EXACT>(h, param);
 }
 
+int vk_part(hs_heat* h, Part p)
+{
+    VkCall c;
+    c.part = (p == P_INTERIOR) ? 0 : 1;
+    c.f64 = h->dtype == HS_F64;
+    c.src = h->buf[h->cur];
+    c.dst = h->buf[1 - h->cur];
+    c.kap = h->kap;
+    c.fdt = h->fdt;
+    c.g = &h->g;
+    c.bx = h->vbx;
+    c.by = h->vby;
+    c.bz = h->vbz;
+    c.kchunk = h->kchunk;
+    c.stream = h->stream;
+    return vk_launch(c);
+}
+
 int do_part(hs_heat* h, Part p)
 {
+    if (h->flags & HS_VARKAPPA) return vk_part(h, p);
     switch (h->arith) {
     case A_F64: return launch_part<double, false>(h, p, h->r);
     case A_F64_EXACT: return launch_part<double, true>(h, p, h->r);
@@ -502,6 +537,7 @@ int heat_batch_view(hs_heat_t h, HeatBatchView* v)
     v->r = h->r;
     v->arith = h->arith;
     v->cur = h->cur;
+    v->vk = (h->flags & HS_VARKAPPA) ? 1 : 0;
     v->stream = h->stream;
     return HS_OK;
 }
@@ -527,6 +563,7 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
     const HeatGeom g = make_geom(desc->nx, desc->ny, desc->nz, elem_size(desc->dtype));
     *bytes = 2 * (size_t)g.total * elem_size(desc->dtype);
     if (desc->flags & HS_FIXED64) *bytes += sizeof(FxState);
+    if (desc->flags & HS_VARKAPPA) *bytes += 2 * (size_t)g.total * elem_size(desc->dtype);
     return HS_OK;
 }
 
@@ -625,6 +662,35 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
         if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "heat_create: fixed-point state");
+            heat_destroy(h);
+            return rc;
+        }
+    }
+    if (h->flags & HS_VARKAPPA) {
+        const size_t bytes = (size_t)h->g.total * h->elem;
+        cudaError_t e = cudaMalloc(&h->kap, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&h->fdt, bytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->kap, 0, bytes, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->fdt, 0, bytes, h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "heat_create: kappa/source arrays");
+            heat_destroy(h);
+            return rc;
+        }
+        const double hx = 1.0 / (h->g.nx + 1), hy = 1.0 / (h->g.ny + 1), hz = 1.0 / (h->g.nz + 1);
+        const double hmin = std::fmin(hx, std::fmin(hy, hz));
+        const double dt = desc->r * hmin * hmin;
+        h->vbx = dt / (2.0 * hx * hx);
+        h->vby = dt / (2.0 * hy * hy);
+        h->vbz = dt / (2.0 * hz * hz);
+        VkCall c = {};
+        c.f64 = h->dtype == HS_F64;
+        c.kap = h->kap;
+        c.fdt = h->fdt;
+        c.g = &h->g;
+        c.stream = h->stream;
+        rc = vk_init(c, dt);
+        if (rc != HS_OK) {
             heat_destroy(h);
             return rc;
         }
@@ -777,6 +843,8 @@ int heat_destroy(hs_heat_t h)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->fx) cudaFree(h->fx);
     if (h->err) cudaFree(h->err);
+    if (h->kap) cudaFree(h->kap);
+    if (h->fdt) cudaFree(h->fdt);
     delete h;
     return rc;
 }

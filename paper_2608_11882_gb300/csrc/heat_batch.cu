@@ -182,7 +182,7 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
         HeatBatchView v;
         int rc = heat_batch_view(h, &v);
         if (rc != HS_OK) return rc;
-        if (v.arith != A_F64 && v.arith != A_F32)
+        if ((v.arith != A_F64 && v.arith != A_F32) || v.vk)
             return fail(HS_EINVAL, "heat_batch_create: grid %d must be plain FP64 or FP32", i);
         for (int32_t k = 0; k < i; ++k)
             if (grids[k] == h) return fail(HS_EINVAL, "heat_batch_create: grid %d appears twice", i);

@@ -270,6 +270,22 @@ int stream_box(int arith, uint32_t* box_x, uint32_t* box_y);
 // Rows of the streaming kernel's tile (its tile is 32 x kStreamRows columns).
 constexpr int kStreamRowsHost = 16;
 
+// One launch of a variable-coefficient kernel (heat_vk.cu).
+struct VkCall {
+    int part;                // 0: Interior (planes 1..nz-2), 1: Boundary (planes 0, nz-1)
+    int f64;                 // 1: FP64, 0: FP32
+    const void* src;
+    void* dst;
+    void* kap;               // kappa on every padded node
+    void* fdt;               // dt f on the interior
+    const HeatGeom* g;
+    double bx, by, bz;       // dt / (2 h_d^2)
+    int kchunk;
+    cudaStream_t stream;
+};
+int vk_init(const VkCall& c, double dt);
+int vk_launch(const VkCall& c);
+
 // What the batched kernel needs to know about a heat handle (heat.cu).
 struct HeatBatchView {
     HeatGeom g;
@@ -277,6 +293,7 @@ struct HeatBatchView {
     double r;
     int arith;
     int cur;
+    int vk;                  // 1 for the variable-coefficient problem
     cudaStream_t stream;
 };
 int heat_batch_view(hs_heat_t h, HeatBatchView* v);

@@ -1,0 +1,135 @@
+// The paper's variable-coefficient heat problem (Section 4, Eqs. 1-4):
+//     du/dt = div(kappa grad u) + f,  kappa = 0.5 + 0.45 sin(pi x) sin(pi y) sin(pi z),
+//     f = 1 + cos(pi x) cos(pi y) cos(pi z),
+//     u' = u + dt f + sum_d dt/(2 h_d^2) D_d(u),
+//     D_x = (k[i+1] + k[i]) (u[i+1] - u[i]) - (k[i] + k[i-1]) (u[i] - u[i-1])
+// (face-averaged kappa: the reading of the unprinted D that matches
+// beta = dt/(2h^2)).  As in the paper's Algorithm "1-GPU Baseline", kappa and
+// dt f are arrays resident beside u: kappa on every node of the padded box
+// (the boundary nodes carry kappa too), dt f on the interior.  Interior and
+// Boundary kernels as for the constant-coefficient update; per point 11 loads
+// (u and kappa at the centre's six neighbours, u, kappa and dt f at the
+// centre, mostly from L1), 22 floating-point instructions.
+#include <cmath>
+
+#include "heat_common.cuh"
+
+namespace hcg {
+
+constexpr int kVkBX = 32, kVkBY = 8;
+
+// kappa on every padded node, dt f on interior nodes (zero on the boundary).
+template <typename T>
+__global__ void __launch_bounds__(256) k_vk_init(T* __restrict__ kap, T* __restrict__ fdt, HeatGeom g,
+                                                 double dt)
+{
+    const double hx = 1.0 / (g.nx + 1), hy = 1.0 / (g.ny + 1), hz = 1.0 / (g.nz + 1);
+    const int64_t n = (int64_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t % (g.nx + 2));
+        const int64_t jk = t / (g.nx + 2);
+        const int J = (int)(jk % (g.ny + 2));
+        const int K = (int)(jk / (g.ny + 2));
+        const int64_t c = (int64_t)K * g.plane + (int64_t)J * g.pitch + g.lead - 1 + I;
+        const double x = I * hx, y = J * hy, z = K * hz;
+        kap[c] = (T)(0.5 + 0.45 * sinpi(x) * sinpi(y) * sinpi(z));
+        const bool interior = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
+        fdt[c] = interior ? (T)(dt * (1.0 + cospi(x) * cospi(y) * cospi(z))) : (T)0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T vk_point(T uc, T uxm, T uxp, T uym, T uyp, T uzm, T uzp, T kc, T kxm, T kxp,
+                                      T kym, T kyp, T kzm, T kzp, T f, T bx, T by, T bz)
+{
+    const T dx = (kxp + kc) * (uxp - uc) - (kc + kxm) * (uc - uxm);
+    const T dy = (kyp + kc) * (uyp - uc) - (kc + kym) * (uc - uym);
+    const T dz = (kzp + kc) * (uzp - uc) - (kc + kzm) * (uc - uzm);
+    return (uc + f) + ((bx * dx + by * dy) + bz * dz);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_interior(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ kap,
+                  const T* __restrict__ fdt, HeatGeom g, T bx, T by, T bz, int kbeg, int kend, int kchunk)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = kbeg + (int)blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, kend);
+    if (k0 >= k1) return;
+    const int64_t P = g.plane, Y = g.pitch;
+    int64_t c = g.at(i, j, k0);
+    T ub = __ldg(src + c - P), uc = __ldg(src + c);
+    T kb = __ldg(kap + c - P), kc = __ldg(kap + c);
+    for (int k = k0; k < k1; ++k) {
+        const T ua = __ldg(src + c + P), ka = __ldg(kap + c + P);
+        dst[c] = vk_point<T>(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y),
+                             __ldg(src + c + Y), ub, ua, kc, __ldg(kap + c - 1), __ldg(kap + c + 1),
+                             __ldg(kap + c - Y), __ldg(kap + c + Y), kb, ka, __ldg(fdt + c), bx, by, bz);
+        ub = uc;
+        uc = ua;
+        kb = kc;
+        kc = ka;
+        c += P;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_boundary(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ kap,
+                  const T* __restrict__ fdt, HeatGeom g, T bx, T by, T bz)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
+    const int64_t P = g.plane, Y = g.pitch;
+    const int64_t c = g.at(i, j, k);
+    dst[c] = vk_point<T>(__ldg(src + c), __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y),
+                         __ldg(src + c + Y), __ldg(src + c - P), __ldg(src + c + P), __ldg(kap + c),
+                         __ldg(kap + c - 1), __ldg(kap + c + 1), __ldg(kap + c - Y), __ldg(kap + c + Y),
+                         __ldg(kap + c - P), __ldg(kap + c + P), __ldg(fdt + c), bx, by, bz);
+}
+
+int vk_init(const VkCall& c, double dt)
+{
+    const int64_t n = (int64_t)(c.g->nx + 2) * (c.g->ny + 2) * (c.g->nz + 2);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
+    if (c.f64)
+        k_vk_init<double><<<(unsigned)blocks, 256, 0, c.stream>>>((double*)c.kap, (double*)c.fdt, *c.g, dt);
+    else
+        k_vk_init<float><<<(unsigned)blocks, 256, 0, c.stream>>>((float*)c.kap, (float*)c.fdt, *c.g, dt);
+    HS_CHECK_LAUNCH("heat: kappa/source init kernel");
+    return HS_OK;
+}
+
+template <typename T>
+int vk_launch_t(const VkCall& c)
+{
+    const HeatGeom& g = *c.g;
+    dim3 block(kVkBX, kVkBY, 1);
+    const T bx = (T)c.bx, by = (T)c.by, bz = (T)c.bz;
+    if (c.part == 0) {
+        if (g.nz < 3) return HS_OK;
+        const int kbeg = 1, kend = g.nz - 1;
+        const int nchunks = (kend - kbeg + c.kchunk - 1) / c.kchunk;
+        dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, nchunks);
+        k_vk_interior<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
+                                                       (const T*)c.fdt, g, bx, by, bz, kbeg, kend, c.kchunk);
+        HS_CHECK_LAUNCH("heat variable-kappa interior kernel");
+    } else {
+        dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, g.nz >= 2 ? 2 : 1);
+        k_vk_boundary<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
+                                                       (const T*)c.fdt, g, bx, by, bz);
+        HS_CHECK_LAUNCH("heat variable-kappa boundary kernel");
+    }
+    return HS_OK;
+}
+
+int vk_launch(const VkCall& c) { return c.f64 ? vk_launch_t<double>(c) : vk_launch_t<float>(c); }
+
+}  // namespace hcg
