@@ -250,8 +250,12 @@ def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind, tdepth=1):
     lup = float(n) * n * (max(n - 2, 0) if tdepth == 1 else n)
     hbm_rate = lup * spec["bytes"] / (int_ms * 1e-3) / 1e9
     tname = {"f64": "double", "fixed64": "long long", "f32": "float"}[mode_name]
-    name = (f"k_heat_stream<{tname}> (Interior, one step)" if tdepth == 1
-            else f"k_heat_tb<{tname}, L={tdepth}>")
+    if tdepth > 1:
+        name = f"k_heat_tb<{tname}, L={tdepth}>"
+    elif mode_name == "f64":
+        name = "k_heat_interior<double> (Interior, register z-march, one step)"
+    else:
+        name = f"k_heat_stream<{tname}> (Interior, TMA-staged, one step)"
     if spec["bound"] == "alu":
         rate = lup * tdepth * FP64_INSTR_PER_LUP / (int_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": name, "achieved": rate, "peak": FP64_INSTR_PEAK_T,

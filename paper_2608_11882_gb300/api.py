@@ -47,9 +47,16 @@ class Heat:
     """A resident heat field (heat_create / heat_upload / heat_step / heat_read)."""
 
     def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
-                 stream=None, tdepth: int = 0):
+                 stream=None, tdepth=0):
+        """tdepth: steps per pass (0 = the library's default, 1..4), or "auto" for
+        the autotuner's cached or freshly measured choice for this shape."""
         self.shape = (nz, ny, nx)
         self.dtype_code, self.np_dtype = _DTYPES[dtype]
+        if tdepth == "auto":
+            from .autotune import Tuner
+            arith = ("fixed64" if flags & HS_FIXED64 else "f64exact" if flags & HS_EXACT_ROUNDING
+                     else dtype)
+            tdepth = 1 if flags & (HS_VARKAPPA | HS_SCHED_FULL) else Tuner().best_depth(arith, self.shape)
         self.stream = _stream_handle(stream)
         desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,
                                    tdepth=tdepth, stream=self.stream)
