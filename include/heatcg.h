@@ -91,6 +91,22 @@ extern "C" {
  * HS_F32; excludes HS_FIXED64, HS_EXACT_ROUNDING, HS_SCHED_FULL and tdepth > 1;
  * cannot join a heat batch. */
 #define HS_VARKAPPA         0x10u
+/* HS_F64 only: do every operation of the update on the FP64 pipe (the six
+ * additions and two fused multiply-adds of the written order).  Without this
+ * flag a plain HS_F64 handle with tdepth <= 1 keeps its fields in FP64 but
+ * forms the numerator S - 6u exactly: each value becomes the 64-bit integer
+ * trunc(u 2^(1080 - e)), e the largest binary exponent field in the current
+ * field (tracked on the device step by step), the integer sum is exact, and
+ * u' = fma(r, (S - 6U) 2^(e - 1080), u) with the numerator rounded to the
+ * nearest double -- one FP64 instruction per point instead of seven, the
+ * conversions done with integer instructions.  Its error against exact
+ * arithmetic on the same field is below 2 r 2^-57 max|u| + 2 ulp; values
+ * more than 57 binades below the field's maximum count as 0 in the sum (not
+ * as centre values).  Fields whose largest exponent field lies outside
+ * [70, 2040] (all-zero or tiny fields, values near overflow, NaN, Inf) are
+ * stepped on the FP64 pipe instead.  Temporal blocking (tdepth >= 2) and
+ * HS_VARKAPPA always use the FP64 pipe. */
+#define HS_FP64_PIPE        0x20u
 
 typedef struct hs_heat* hs_heat_t;
 
@@ -135,8 +151,9 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device);
  * an L-wide halo stream up the k axis, the intermediate time levels living
  * in shared memory and registers), then swaps; a remainder of n_steps is done
  * in shallower passes.  The result equals stepping one step at a time up to
- * rounding (bit for bit for FP32 and FP64, whose per-point arithmetic is the
- * same; FIXED64 may rescale at different steps).  Asynchronous: launch errors
+ * rounding (bit for bit for FP32, and for FP64 against an HS_FP64_PIPE handle
+ * stepped one step at a time, whose per-point arithmetic is the same; FIXED64
+ * may rescale at different steps).  Asynchronous: launch errors
  * are returned here, errors raised while kernels run are returned by the next
  * synchronising call (a bounded device wait that ran out: HS_ETIMEOUT). */
 int heat_step(hs_heat_t h, int64_t n_steps);

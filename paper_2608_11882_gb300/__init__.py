@@ -7,7 +7,7 @@ names load the library on first use and raise ImportError if it is not built:
 there is no CPU fallback.
 """
 _API = {"Heat", "HeatBatch", "Operator", "CG", "CGBatch", "HeatCGError", "HS_F64", "HS_F32", "HS_ALLOW_UNSTABLE",
-        "HS_EXACT_ROUNDING", "HS_SCHED_FULL", "HS_FIXED64", "HS_VARKAPPA", "HS_OP_STENCIL7", "HS_OP_CSR", "native"}
+        "HS_EXACT_ROUNDING", "HS_SCHED_FULL", "HS_FIXED64", "HS_VARKAPPA", "HS_FP64_PIPE", "HS_OP_STENCIL7", "HS_OP_CSR", "native"}
 
 __all__ = sorted(_API)
 

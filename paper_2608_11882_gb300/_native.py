@@ -13,6 +13,7 @@ HS_OK, HS_EINVAL, HS_ENOMEM, HS_ECUDA = 0, -1, -2, -3
 HS_EUNSTABLE, HS_ENOCONV, HS_ETIMEOUT, HS_EBUSY, HS_ERANGE = -4, -5, -6, -7, -8
 HS_F64, HS_F32 = 0, 1
 HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_SCHED_FULL, HS_FIXED64, HS_VARKAPPA = 0x1, 0x2, 0x4, 0x8, 0x10
+HS_FP64_PIPE = 0x20
 HS_OP_STENCIL7, HS_OP_CSR = 0, 1
 
 _CODE_NAMES = {HS_EINVAL: "HS_EINVAL", HS_ENOMEM: "HS_ENOMEM", HS_ECUDA: "HS_ECUDA",

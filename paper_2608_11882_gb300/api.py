@@ -7,12 +7,12 @@ from __future__ import annotations
 import numpy as np
 
 from . import _native as native
-from ._native import (HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_F32, HS_F64, HS_FIXED64, HS_VARKAPPA,
-                      HS_OP_CSR,
-                      HS_OP_STENCIL7, HS_SCHED_FULL, HeatCGError)
+from ._native import (HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_F32, HS_F64, HS_FIXED64, HS_FP64_PIPE,
+                      HS_OP_CSR, HS_OP_STENCIL7, HS_SCHED_FULL, HS_VARKAPPA, HeatCGError)
 
-__all__ = ["Heat", "Operator", "CG", "native", "HeatCGError", "HS_F64", "HS_F32",
-           "HS_ALLOW_UNSTABLE", "HS_EXACT_ROUNDING", "HS_SCHED_FULL", "HS_OP_STENCIL7", "HS_OP_CSR"]
+__all__ = ["Heat", "HeatBatch", "Operator", "CG", "CGBatch", "native", "HeatCGError", "HS_F64", "HS_F32",
+           "HS_ALLOW_UNSTABLE", "HS_EXACT_ROUNDING", "HS_SCHED_FULL", "HS_FIXED64", "HS_VARKAPPA",
+           "HS_FP64_PIPE", "HS_OP_STENCIL7", "HS_OP_CSR"]
 
 _DTYPES = {"f64": (HS_F64, np.float64), "f32": (HS_F32, np.float32)}
 
@@ -55,7 +55,7 @@ class Heat:
         if tdepth == "auto":
             from .autotune import Tuner
             arith = ("fixed64" if flags & HS_FIXED64 else "f64exact" if flags & HS_EXACT_ROUNDING
-                     else dtype)
+                     else "f64pipe" if flags & HS_FP64_PIPE else dtype)
             tdepth = 1 if flags & (HS_VARKAPPA | HS_SCHED_FULL) else Tuner().best_depth(arith, self.shape)
         self.stream = _stream_handle(stream)
         desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,

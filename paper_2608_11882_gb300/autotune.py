@@ -4,10 +4,11 @@ For a grid shape and arithmetic it times ``heat_step`` with every built depth
 (1 = Interior + Boundary kernels every step, 2..4 = the temporally blocked
 kernel) on a short sample of steps on the actual device, keeps the fastest,
 and caches the choice in a JSON file keyed by GPU name, arithmetic and size
-class, so later handles of that kind start from the cached depth.  The kernels
-and their per-point arithmetic do not depend on the choice beyond rounding
-order (FP32/FP64 results are bitwise equal across depths; FIXED64 may rescale
-at other steps), so tuning changes speed only.
+class, so later handles of that kind start from the cached depth.  Results
+depend on the choice only through rounding: FP32 and FP64-pipe results are
+bitwise equal across depths, FIXED64 may rescale at other steps, and a plain
+FP64 handle runs the exact-sum arithmetic at depth 1 and the FP64 pipe at
+depths 2..4, both within the FP64 tolerance of the exact update.
 """
 from __future__ import annotations
 
@@ -82,7 +83,8 @@ def _gpu_timer(arith: str, shape, depth: int, steps: int = 24) -> float:
 
     import paper_2608_11882_gb300 as pkg
     nz, ny, nx = shape
-    flags = {"fixed64": pkg.HS_FIXED64, "f64exact": pkg.HS_EXACT_ROUNDING}.get(arith, 0)
+    flags = {"fixed64": pkg.HS_FIXED64, "f64exact": pkg.HS_EXACT_ROUNDING,
+             "f64pipe": pkg.HS_FP64_PIPE}.get(arith, 0)
     dtype = "f32" if arith == "f32" else "f64"
     u0 = np.random.default_rng(0).uniform(-1, 1, size=shape)
     with pkg.Heat(nx, ny, nz, 0.1, dtype=dtype, flags=flags, tdepth=depth) as h:

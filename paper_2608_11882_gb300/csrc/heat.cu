@@ -7,7 +7,11 @@
 // on interior points; the boundary layer stays zero (Dirichlet).
 //
 // Arithmetic, chosen per handle:
-//   FP64      the update in double precision with two fused multiply-adds;
+//   FP64      (default) FP64 fields, the six-neighbour sum and S - 6u exact in
+//             64-bit fixed point on the field's current scale, converted back
+//             and applied with one FP64 fused multiply-add (heat_common.cuh);
+//   FP64 pipe (HS_FP64_PIPE, and temporal blocking) the update in double
+//             precision with two fused multiply-adds;
 //   FP64 exact one rounding per operation in the written order (no FMA), the
 //             oracle's rounding sequence bit for bit;
 //   FP32      the update in single precision (storage and arithmetic);
@@ -145,6 +149,55 @@ __global__ void __launch_bounds__(256)
     if constexpr (kIsFixed<T>) fx_finish<256>(mx, fx, m3, ks, blockIdx.x == 0);
 }
 
+// ---- Boundary and full-step kernels in the FP64 exact-sum arithmetic ------------------
+// Per point the seven doubles are converted, then updated as in the streaming
+// Interior kernel (xs_point); every output joins the step's maximum.
+__global__ void __launch_bounds__(kBX* kBY)
+    k_heat_boundary_xs(const double* __restrict__ src, double* __restrict__ dst, HeatGeom g, double r,
+                       FxState* fx, int m3)
+{
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int emax = xs_emax(fx, m3);
+    unsigned mx = 0;
+    if (i < g.nx && j < g.ny) {
+        const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
+        const int64_t P = g.plane, Y = g.pitch;
+        const int64_t c = g.at(i, j, k);
+        const double v = xs_point(__ldg(src + c), __ldg(src + c - 1), __ldg(src + c + 1),
+                                  __ldg(src + c - Y), __ldg(src + c + Y), __ldg(src + c - P),
+                                  __ldg(src + c + P), r, emax);
+        dst[c] = v;
+        mx = xs_abs_hi(v);
+    }
+    fx_finish<kBX * kBY>((unsigned long long)mx << 32, fx, m3, 0,
+                         blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+}
+
+__global__ void __launch_bounds__(256)
+    k_heat_full_xs(const double* __restrict__ src, double* __restrict__ dst, HeatGeom g, double r,
+                   FxState* fx, int m3)
+{
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    const int64_t P = g.plane, Y = g.pitch;
+    const int emax = xs_emax(fx, m3);
+    unsigned mx = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const int64_t jk = t / g.nx;
+        const int j = (int)(jk % g.ny);
+        const int k = (int)(jk / g.ny);
+        const int64_t c = g.at(i, j, k);
+        const double v = xs_point(src[c], src[c - 1], src[c + 1], src[c - Y], src[c + Y], src[c - P],
+                                  src[c + P], r, emax);
+        dst[c] = v;
+        const unsigned a = xs_abs_hi(v);
+        mx = a > mx ? a : mx;
+    }
+    fx_finish<256>((unsigned long long)mx << 32, fx, m3, 0, blockIdx.x == 0);
+}
+
 // ---- FIXED64 conversions (at upload and read only) --------------------------------
 // Grid-stride over the interior points of a padded buffer.
 __global__ void __launch_bounds__(256) k_fx_maxabs(const double* __restrict__ buf, HeatGeom g,
@@ -170,6 +223,7 @@ __global__ void __launch_bounds__(256) k_fx_maxabs(const double* __restrict__ bu
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&st->maxabs_bits, m);
+        atomicMax(&st->slot[0].maxU, m);   // the exact-sum FP64 arithmetic's step-0 maximum
         if (bad) atomicOr(&st->nonfinite, 1);
     }
 }
@@ -261,7 +315,7 @@ struct hs_heat {
 namespace {
 
 constexpr uint32_t kKnownFlags =
-    HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64 | HS_VARKAPPA;
+    HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64 | HS_VARKAPPA | HS_FP64_PIPE;
 constexpr double kKappaMax = 0.95;   // max of 0.5 + 0.45 sin sin sin (Section 4, Eq. 2)
 
 int check_desc(const hs_heat_desc* d)
@@ -279,6 +333,8 @@ int check_desc(const hs_heat_desc* d)
         return fail(HS_EINVAL, "heat: dtype %d is not HS_F64 or HS_F32", d->dtype);
     if ((d->flags & HS_EXACT_ROUNDING) && d->dtype != HS_F64)
         return fail(HS_EINVAL, "heat: HS_EXACT_ROUNDING applies to HS_F64 only");
+    if ((d->flags & HS_FP64_PIPE) && (d->dtype != HS_F64 || (d->flags & HS_FIXED64)))
+        return fail(HS_EINVAL, "heat: HS_FP64_PIPE applies to plain HS_F64 only");
     if (d->flags & HS_FIXED64) {
         if (d->dtype != HS_F64) return fail(HS_EINVAL, "heat: HS_FIXED64 applies to HS_F64 only");
         if (d->flags & HS_EXACT_ROUNDING)
@@ -308,6 +364,18 @@ int check_desc(const hs_heat_desc* d)
 }
 
 size_t elem_size(int dtype) { return dtype == HS_F64 ? sizeof(double) : sizeof(float); }
+
+// Plain FP64 runs the exact-sum arithmetic, except where a kernel has only the
+// FP64-pipe form: temporal blocking and the variable-coefficient problem.
+Arith pick_arith(const hs_heat_desc* d)
+{
+    const int depth = d->tdepth ? d->tdepth : 1;
+    if (d->flags & HS_FIXED64) return A_FX64;
+    if (d->flags & HS_EXACT_ROUNDING) return A_F64_EXACT;
+    if (d->dtype == HS_F32) return A_F32;
+    if ((d->flags & (HS_FP64_PIPE | HS_VARKAPPA)) || depth > 1) return A_F64;
+    return A_F64_XS;
+}
 
 int pick_kchunk(const HeatGeom& g)
 {
@@ -388,6 +456,27 @@ int launch_stream_interior(hs_heat* h)
     return stream_launch(c);
 }
 
+int launch_part_xs(hs_heat* h, Part p)
+{
+    const HeatGeom& g = h->g;
+    const double* src = (const double*)h->buf[h->cur];
+    double* dst = (double*)h->buf[1 - h->cur];
+    const int m3 = (int)(h->fxseq % 3);
+    if (p == P_INTERIOR) return launch_stream_interior(h);
+    if (p == P_BOUNDARY) {
+        dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz >= 2 ? 2 : 1);
+        k_heat_boundary_xs<<<grid, dim3(kBX, kBY, 1), 0, h->stream>>>(src, dst, g, h->r, h->fx, m3);
+        HS_CHECK_LAUNCH("heat boundary kernel (FP64 exact sum)");
+        return HS_OK;
+    }
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)kNumSMs * 64) blocks = (int64_t)kNumSMs * 64;
+    k_heat_full_xs<<<(unsigned)blocks, 256, 0, h->stream>>>(src, dst, g, h->r, h->fx, m3);
+    HS_CHECK_LAUNCH("heat full-step kernel (FP64 exact sum)");
+    return HS_OK;
+}
+
 template <typename T, bool EXACT>
 int launch_part(hs_heat* h, Part p, T param)
 {
@@ -426,6 +515,7 @@ int do_part(hs_heat* h, Part p)
     case A_F64_EXACT: return launch_part<double, true>(h, p, h->r);
     case A_F32: return launch_part<float, false>(h, p, (float)h->r);
     case A_FX64: return launch_part<long long, false>(h, p, h->R);
+    case A_F64_XS: return launch_part_xs(h, p);
     }
     return fail(HS_EINVAL, "heat: unknown arithmetic");
 }
@@ -538,6 +628,8 @@ int heat_batch_view(hs_heat_t h, HeatBatchView* v)
     v->arith = h->arith;
     v->cur = h->cur;
     v->vk = (h->flags & HS_VARKAPPA) ? 1 : 0;
+    v->fx = h->fx;
+    v->m3 = (int)(h->fxseq % 3);
     v->stream = h->stream;
     return HS_OK;
 }
@@ -562,7 +654,8 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
     if (!bytes) return fail(HS_EINVAL, "heat_device_bytes: bytes is NULL");
     const HeatGeom g = make_geom(desc->nx, desc->ny, desc->nz, elem_size(desc->dtype));
     *bytes = 2 * (size_t)g.total * elem_size(desc->dtype);
-    if (desc->flags & HS_FIXED64) *bytes += sizeof(FxState);
+    const Arith a = pick_arith(desc);
+    if (a == A_FX64 || a == A_F64_XS) *bytes += sizeof(FxState);
     if (desc->flags & HS_VARKAPPA) *bytes += 2 * (size_t)g.total * elem_size(desc->dtype);
     return HS_OK;
 }
@@ -580,10 +673,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     h->g = make_geom(desc->nx, desc->ny, desc->nz, h->elem);
     h->r = desc->r;
     h->flags = desc->flags;
-    h->arith = (desc->flags & HS_FIXED64)          ? A_FX64
-               : (desc->flags & HS_EXACT_ROUNDING) ? A_F64_EXACT
-               : (desc->dtype == HS_F32)           ? A_F32
-                                                   : A_F64;
+    h->arith = pick_arith(desc);
     // r <= 1/6 < 1/2, so r 2^64 < 2^63.  For r >= 2^-11 it is an integer (r's
     // last bit is worth at least 2^-64), so R holds r exactly; a smaller r is
     // rounded to the nearest multiple of 2^-64.
@@ -657,7 +747,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             }
         }
     }
-    if (h->arith == A_FX64) {
+    if (h->arith == A_FX64 || h->arith == A_F64_XS) {
         cudaError_t e = cudaMalloc((void**)&h->fx, sizeof(FxState));
         if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
         if (e != cudaSuccess) {
@@ -716,6 +806,11 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
         HS_CHECK_LAUNCH("heat_upload: max|u| kernel");
         k_fx_encode<<<blocks, 256, 0, h->stream>>>((double*)h->buf[0], h->g, h->fx);
         HS_CHECK_LAUNCH("heat_upload: fixed-point encode kernel");
+    } else if (h->arith == A_F64_XS) {
+        // slot 0: the largest |u| bit pattern of the uploaded field
+        HS_TRY_CUDA(cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream), "heat_upload: memset");
+        k_fx_maxabs<<<conv_blocks(h->g), 256, 0, h->stream>>>((const double*)h->buf[0], h->g, h->fx);
+        HS_CHECK_LAUNCH("heat_upload: max|u| kernel");
     }
     h->cur = 0;
     h->steps = 0;

@@ -14,6 +14,12 @@
 //
 // Loads use ld.global.cg (L2 only): a block must never see another SM's
 // freshly written plane through its own stale L1 lines.
+//
+// Plain FP64 grids run the exact-sum arithmetic of heat_step (heat_common.cuh):
+// every tile of step m reads the field maximum of step m from the grid's slot
+// (m3 + m) % 3, which the tiles of step m-1 completed before the wait above
+// let step m start; each tile adds its outputs' maximum to slot (m3 + m + 1) % 3,
+// and tile 0 clears slot (m3 + m + 2) % 3, which no unfinished item reads.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -26,14 +32,19 @@ namespace hcg {
 constexpr int kBatchBX = 32, kBatchBY = 8;
 constexpr long long kBatchWaitCycles = 2000000000ll;
 
+enum BatchKind { K_F64_PIPE = 0, K_F32 = 1, K_F64_XS = 2 };
+
 struct BatchGrid {
     HeatGeom g;
     void* buf[2];
     double r;
-    int32_t dtype;      // HS_F64 or HS_F32
+    FxState* fx;        // K_F64_XS: the grid's per-step maxima
+    int32_t kind;       // BatchKind
     int32_t cur;        // buffer holding the field when the batch starts
+    int32_t m3;         // K_F64_XS: slot of the field when the batch starts
     int32_t tiles_x;
     int32_t tiles;      // tiles per step
+    int32_t pad;
     int64_t steps;
 };
 
@@ -50,14 +61,18 @@ struct BatchDev {
     int32_t max_steps;
 };
 
-template <typename T>
-__device__ __forceinline__ void batch_tile(const BatchGrid& G, int m, int t)
+// One column tile of step m; returns the largest |u| high word of its outputs
+// (exact-sum FP64 only).
+template <typename T, bool XS>
+__device__ __forceinline__ unsigned batch_tile(const BatchGrid& G, int m, int t)
 {
     const HeatGeom& g = G.g;
     const int tx = t % G.tiles_x, ty = t / G.tiles_x;
     const int i = tx * kBatchBX + threadIdx.x;
     const int j = ty * kBatchBY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
+    if (i >= g.nx || j >= g.ny) return 0u;
+    const int emax = XS ? xs_emax(G.fx, (G.m3 + m) % 3) : 0;
+    unsigned mx = 0;
     const int src_b = (G.cur + m) & 1;
     const T* __restrict__ src = (const T*)G.buf[src_b];
     T* __restrict__ dst = (T*)G.buf[src_b ^ 1];
@@ -70,11 +85,20 @@ __device__ __forceinline__ void batch_tile(const BatchGrid& G, int m, int t)
         const T above = __ldcg(src + c + P);
         const T xm = __ldcg(src + c - 1), xp = __ldcg(src + c + 1);
         const T ym = __ldcg(src + c - Y), yp = __ldcg(src + c + Y);
-        dst[c] = Point<T, false>::update(cur, xm, xp, ym, yp, below, above, r, 0);
+        T v;
+        if constexpr (XS) {
+            v = xs_point(cur, xm, xp, ym, yp, below, above, r, emax);
+            const unsigned a = xs_abs_hi(v);
+            mx = a > mx ? a : mx;
+        } else {
+            v = Point<T, false>::update(cur, xm, xp, ym, yp, below, above, r, 0);
+        }
+        dst[c] = v;
         below = cur;
         cur = above;
         c += P;
     }
+    return mx;
 }
 
 __global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
@@ -121,10 +145,14 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
         }
         __syncthreads();
         if (s_abort) break;
-        if (G.dtype == HS_F64)
-            batch_tile<double>(G, m, t);
-        else
-            batch_tile<float>(G, m, t);
+        if (G.kind == K_F64_XS) {
+            const unsigned mx = batch_tile<double, true>(G, m, t);
+            fx_finish<kBatchBX * kBatchBY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
+        } else if (G.kind == K_F64_PIPE) {
+            batch_tile<double, false>(G, m, t);
+        } else {
+            batch_tile<float, false>(G, m, t);
+        }
         __threadfence();
         __syncthreads();
         if (tid == 0) atomicAdd(&B.done[gi], 1ull);
@@ -182,7 +210,7 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
         HeatBatchView v;
         int rc = heat_batch_view(h, &v);
         if (rc != HS_OK) return rc;
-        if ((v.arith != A_F64 && v.arith != A_F32) || v.vk)
+        if ((v.arith != A_F64 && v.arith != A_F64_XS && v.arith != A_F32) || v.vk)
             return fail(HS_EINVAL, "heat_batch_create: grid %d must be plain FP64 or FP32", i);
         for (int32_t k = 0; k < i; ++k)
             if (grids[k] == h) return fail(HS_EINVAL, "heat_batch_create: grid %d appears twice", i);
@@ -191,8 +219,11 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
         G.buf[0] = v.buf[0];
         G.buf[1] = v.buf[1];
         G.r = v.r;
-        G.dtype = v.arith == A_F64 ? HS_F64 : HS_F32;
-        G.cur = 0;   // set at each run
+        G.kind = v.arith == A_F64 ? K_F64_PIPE : v.arith == A_F64_XS ? K_F64_XS : K_F32;
+        G.fx = v.fx;
+        G.cur = 0;   // cur and m3 are set at each run
+        G.m3 = 0;
+        G.pad = 0;
         G.tiles_x = (v.g.nx + kBatchBX - 1) / kBatchBX;
         G.tiles = G.tiles_x * ((v.g.ny + kBatchBY - 1) / kBatchBY);
         G.steps = steps[i];
@@ -309,8 +340,9 @@ static int batch_enqueue(hs_batch* b)
         // the grid's own stream may still be uploading into it
         if (v.stream != b->stream)
             HS_TRY_CUDA(cudaStreamSynchronize(v.stream), "heat_batch_run: grid stream");
-        if (hg[(size_t)i].cur != v.cur) {
+        if (hg[(size_t)i].cur != v.cur || hg[(size_t)i].m3 != v.m3) {
             hg[(size_t)i].cur = v.cur;
+            hg[(size_t)i].m3 = v.m3;
             changed = true;
         }
     }

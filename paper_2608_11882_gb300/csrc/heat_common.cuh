@@ -154,6 +154,87 @@ struct Point<long long, EXACT> {
 template <typename T>
 constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
+// ---- FP64 with an exact neighbour sum ---------------------------------------------
+// FP64 fields in HBM, updated with one FP64 instruction per point.  Each value
+// u of the current field becomes the signed integer U = trunc(u 2^(1080 - e)),
+// where e is the largest biased exponent field among the field's values (so
+// |U| < 2^58; values more than 57 binades below the maximum become 0).  The
+// numerator L = S - 6U is then exact in 64-bit integers (|L| < 12 2^58), is
+// turned back into the nearest double L 2^(e - 1080) with integer operations
+// only, and u' = fma(r, L, u) rounds once.  Against the exact update of the
+// same field the error is below r 12 2^-57 max|u| plus two FP64 roundings.
+// The conversions use integer instructions because on GB300 every FP64 <-> int64
+// conversion instruction runs at the FP64 rate.  e is tracked per step like the
+// FIXED64 scale: slot m % 3 of an FxState holds the largest |u| bit pattern of
+// the field at step m (non-negative doubles order like their bit patterns).
+// Fields whose largest exponent is outside [kXsEmaxLo, kXsEmaxHi] -- tiny or
+// all-zero fields, values near overflow, NaN or Inf -- take the FP64-pipe
+// update (Point<double, false>), which also carries NaN and Inf through.
+constexpr int kXsEmaxLo = 70, kXsEmaxHi = 2040;
+
+__device__ __forceinline__ bool xs_native(int emax) { return emax < kXsEmaxLo || emax > kXsEmaxHi; }
+
+__device__ __forceinline__ int xs_emax(const FxState* fx, int m3)
+{
+    return (int)(__ldcg(&fx->slot[m3].maxU) >> 52);
+}
+
+// The fixed-point integer of the double with bit pattern `bits` (its exponent
+// field must not exceed emax; zeros and subnormals give 0 for emax >= 64).
+__device__ __forceinline__ long long xs_fix(long long bits, int emax)
+{
+    const unsigned hi = (unsigned)((unsigned long long)bits >> 32), lo = (unsigned)bits;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    // (1.mantissa) << 5: bits 57..0, the implicit bit at 57
+    const unsigned mh = (__funnelshift_l(lo, hi, 5) & 0x01ffffffu) | 0x02000000u;
+    const unsigned long long m5 = ((unsigned long long)mh << 32) | (unsigned long long)(lo << 5);
+    const unsigned t = min((unsigned)(emax - (int)e), 63u);
+    const unsigned long long v = m5 >> t;
+    const unsigned long long s = (unsigned long long)((long long)(int)hi >> 31);   // 0 or all ones
+    return (long long)((v ^ s) - s);
+}
+
+// x 2^(emax - 1080) rounded to the nearest double, ties to even (|x| < 2^62,
+// kXsEmaxLo <= emax <= kXsEmaxHi, so the result is a normal number or zero).
+__device__ __forceinline__ double xs_unfix(long long x, int emax)
+{
+    const unsigned long long s = (unsigned long long)(x >> 63);
+    const unsigned long long a = ((unsigned long long)x ^ s) - s;
+    const int lz = __clzll((long long)a);                       // >= 2; 64 for a = 0
+    const unsigned long long n = a << ((lz - 1) & 63);          // leading one at bit 62
+    const unsigned long long q = (n + 0x1ffull + ((n >> 10) & 1ull)) >> 10;   // 2^52 <= q <= 2^53
+    // biased exponent emax + 6 - lz; q's bit 52 (or a carry to 53) adds into the exponent field
+    const unsigned hi = (unsigned)(q >> 32) + ((unsigned)(emax + 5 - lz) << 20) +
+                        ((unsigned)s & 0x80000000u);
+    const long long bits = (long long)(((unsigned long long)hi << 32) | (unsigned)q);
+    return a ? __longlong_as_double(bits) : 0.0;
+}
+
+// The update of a point from its centre's double and the seven fixed-point values.
+__device__ __forceinline__ double xs_update(double uc, long long c, long long xm, long long xp,
+                                            long long ym, long long yp, long long zm, long long zp,
+                                            double r, int emax)
+{
+    const long long L = ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;
+    return __fma_rn(r, xs_unfix(L, emax), uc);
+}
+
+// The same update from seven doubles (kernels that convert per point).
+__device__ __forceinline__ double xs_point(double c, double xm, double xp, double ym, double yp,
+                                           double zm, double zp, double r, int emax)
+{
+    if (xs_native(emax)) return Point<double, false>::update(c, xm, xp, ym, yp, zm, zp, r, 0);
+    auto f = [emax](double v) { return xs_fix(__double_as_longlong(v), emax); };
+    return xs_update(c, f(c), f(xm), f(xp), f(ym), f(yp), f(zm), f(zp), r, emax);
+}
+
+// |u| of a result as the high word of its bit pattern (the exponent field and
+// the top of the mantissa): what the per-step maximum needs.
+__device__ __forceinline__ unsigned xs_abs_hi(double v)
+{
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+}
+
 // V consecutive x points per thread, moved as one 16-byte vector.
 template <typename T>
 struct Vec;
@@ -205,7 +286,9 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[Vec<T>::V])
 }
 
 // Arithmetic of a heat handle.
-enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3 };
+// A_F64: every operation on the FP64 pipe; A_F64_XS: FP64 fields with the exact
+// integer neighbour sum and one FP64 FMA per point (above).
+enum Arith { A_F64 = 0, A_F64_EXACT = 1, A_F32 = 2, A_FX64 = 3, A_F64_XS = 4 };
 
 // One launch of the temporally blocked kernel (heat_tb.cu).
 struct TbCall {
@@ -294,6 +377,8 @@ struct HeatBatchView {
     int arith;
     int cur;
     int vk;                  // 1 for the variable-coefficient problem
+    FxState* fx;             // A_F64_XS: the per-step maxima
+    int m3;                  // A_F64_XS: slot of the current field
     cudaStream_t stream;
 };
 int heat_batch_view(hs_heat_t h, HeatBatchView* v);

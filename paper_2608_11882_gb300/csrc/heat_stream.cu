@@ -171,10 +171,240 @@ __global__ void __launch_bounds__(32 * RY)
         fx_finish<32 * RY>(mx, fx, m3, ks, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
+// ---- FP64 with the exact neighbour sum (A_F64_XS) -------------------------------------
+// The tile, ring, waits and error handling of k_heat_stream, for FP64 fields
+// in the exact-sum arithmetic (heat_common.cuh).  Once plane k+1 has landed,
+// the block converts it in place to fixed point on the field's scale: every
+// thread its own vector (keeping the raw doubles, the centre values of the next
+// iteration), warps 0 and 1 the halo rows, warp 2 the two halo columns, so each
+// staged value is converted once.  Plane k, converted one iteration earlier,
+// gives the in-plane neighbours.  A point then costs the exact integer sum, one
+// conversion back and one FP64 fused multiply-add.  Converted slots are written
+// through the generic proxy and refilled later by TMA (the async proxy), so
+// every thread fences the async proxy after its conversion stores, before the
+// block barrier that precedes a refill.  CONV = false is the FP64-pipe update
+// on the raw planes, for fields outside the conversion's exponent range.
+template <int RY, int NST, bool CONV>
+__device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* __restrict__ dst,
+                                               const HeatGeom& g, double r, int kb, int ke, int emax,
+                                               long long* stage, uint64_t* bars, int& s_abort,
+                                               unsigned& mx, int* err)
+{
+    using S = StreamShape<double>;
+    constexpr int V = S::V;
+    constexpr int BW = S::BW;
+    constexpr int ROWS = RY + 2;
+    constexpr uint32_t BOX_BYTES = ROWS * BW * (uint32_t)sizeof(double);
+    constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(double));
+    static_assert(V == 2 && 2 * RY == 32, "warp 2 converts the 2 RY halo-column values");
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * RY;
+    const int X = x0 + V * tx, Y = y0 + ty;
+    const int xs = g.lead + x0 - S::D;
+    const int own = (ty + 1) * BW + S::D + V * tx;
+    const bool row_ok = (Y < g.ny);
+    const int nvalid = row_ok ? min(V, g.nx - X) : 0;
+    const int p_first = kb - 1, p_last = ke;
+    // what this thread converts besides its own vector: a vector of halo row 0
+    // (warp 0) or RY+1 (warp 1), or one halo-column value (warp 2)
+    int extra = -1;
+    if (ty == 0) extra = S::D + V * tx;
+    else if (ty == 1) extra = (RY + 1) * BW + S::D + V * tx;
+    else if (ty == 2) extra = tx < RY ? (tx + 1) * BW + S::D - 1 : (tx - RY + 1) * BW + S::D + 32 * V;
+
+    // converts this thread's part of the staged plane at `pl`; returns its own raw vector
+    auto convert = [&](long long* pl, long long (&q)[V], double (&raw)[V]) {
+        long long b[V];
+        ld_vec(pl + own, b);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            raw[i] = __longlong_as_double(b[i]);
+            q[i] = CONV ? xs_fix(b[i], emax) : b[i];
+        }
+        if constexpr (CONV) {
+            st_vec(pl + own, q);
+            if (ty < 2) {
+                long long h[V];
+                ld_vec(pl + extra, h);
+#pragma unroll
+                for (int i = 0; i < V; ++i) h[i] = xs_fix(h[i], emax);
+                st_vec(pl + extra, h);
+            } else if (ty == 2) {
+                pl[extra] = xs_fix(pl[extra], emax);
+            }
+        }
+    };
+
+    int issued = p_first - 1;
+    int drain_from = p_first;
+    if (tid == 0) {
+        for (int s = 0; s < NST && p_first + s <= p_last; ++s) {
+            mbar_arrive_expect_tx(&bars[s], BOX_BYTES);
+            tma_load_3d(stage + s * STAGE, map, xs, y0, p_first + s + 1, &bars[s]);
+            issued = p_first + s;
+        }
+    }
+    long long below[V], cur[V], above[V];
+    double craw[V], araw[V];
+    int s_cur = 0, n_cur = 0;
+    bool ok = mbar_wait_bounded(&bars[0], 0);
+    {
+        long long b[V];
+        ld_vec(stage + own, b);
+#pragma unroll
+        for (int i = 0; i < V; ++i) below[i] = CONV ? xs_fix(b[i], emax) : b[i];
+    }
+    int s_nxt = 1 % NST, n_nxt = 1 / NST;
+    ok = ok && mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u);
+    convert(stage + s_nxt * STAGE, cur, craw);
+    s_cur = s_nxt;
+    n_cur = n_nxt;
+    if (!ok) {
+        atomicExch(err, 1);
+        s_abort = 1;
+    }
+    if constexpr (CONV) fence_proxy_async_smem();
+    __syncthreads();
+
+    double* out = dst + g.at(X < g.nx ? X : 0, row_ok ? Y : 0, kb);   // only used when nvalid > 0
+    if (!s_abort) {
+        for (int k = kb; k < ke; ++k) {
+            s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
+            n_nxt = s_nxt == 0 ? n_cur + 1 : n_cur;
+            if (!mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u)) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            convert(stage + s_nxt * STAGE, above, araw);
+            const long long* pl = stage + s_cur * STAGE + own;
+            long long ym[V], yp[V];
+            ld_vec(pl - BW, ym);
+            ld_vec(pl + BW, yp);
+            const long long left = pl[-1], right = pl[V];
+            double v[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const long long xm = i == 0 ? left : cur[i - 1];
+                const long long xp = i == V - 1 ? right : cur[i + 1];
+                if constexpr (CONV) {
+                    v[i] = xs_update(craw[i], cur[i], xm, xp, ym[i], yp[i], below[i], above[i], r, emax);
+                } else {
+                    auto d = [](long long b) { return __longlong_as_double(b); };
+                    v[i] = Point<double, false>::update(craw[i], d(xm), d(xp), d(ym[i]), d(yp[i]),
+                                                        d(below[i]), d(above[i]), r, 0);
+                }
+            }
+            if (nvalid == V) {
+                st_vec(out, v);
+            } else {
+                for (int i = 0; i < nvalid; ++i) out[i] = v[i];
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const unsigned a = i < nvalid ? xs_abs_hi(v[i]) : 0u;
+                mx = a > mx ? a : mx;
+                below[i] = cur[i];
+                cur[i] = above[i];
+                craw[i] = araw[i];
+            }
+            out += g.plane;
+            if constexpr (CONV) fence_proxy_async_smem();
+            __syncthreads();
+            if (s_abort) {
+                drain_from = k + 1;
+                break;
+            }
+            if (tid == 0 && issued < p_last) {
+                const int slot = s_cur == 0 ? NST - 1 : s_cur - 1;   // plane k-1's slot is free
+                const int pn = issued + 1;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[slot], BOX_BYTES);
+                tma_load_3d(stage + slot * STAGE, map, xs, y0, pn + 1, &bars[slot]);
+                issued = pn;
+            }
+            s_cur = s_nxt;
+            n_cur = n_nxt;
+        }
+    } else {
+        drain_from = p_first;
+    }
+    if (s_abort && tid == 0) {
+        const long long t0 = clock64();   // one time budget for the whole drain
+        for (int p = drain_from; p <= issued; ++p) {
+            const int i = p - p_first;
+            (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
+        }
+    }
+}
+
+template <int RY, int NST>
+__global__ void __launch_bounds__(32 * RY)
+    k_heat_stream_xs(const __grid_constant__ CUtensorMap map, double* __restrict__ dst, HeatGeom g,
+                     double r, int kbeg, int kend, int kc, FxState* fx, int m3, int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    using S = StreamShape<double>;
+    constexpr uint32_t BOX_BYTES = (RY + 2) * S::BW * (uint32_t)sizeof(double);
+    constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(double));
+    long long* stage = reinterpret_cast<long long*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + NST * STAGE);
+    __shared__ int s_abort;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int kb = kbeg + blockIdx.z * kc;
+    const int ke = min(kb + kc, kend);
+    if (tid == 0) {
+        // a block that starts after another one gave up does no work at all
+        s_abort = *(volatile int*)err;
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const int emax = xs_emax(fx, m3);
+    unsigned mx = 0;
+    if (xs_native(emax))
+        xs_stream_body<RY, NST, false>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
+    else
+        xs_stream_body<RY, NST, true>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
+    if (s_abort) return;   // uniform: every thread passed the barrier that saw it
+    fx_finish<32 * RY>((unsigned long long)mx << 32, fx, m3, 0,
+                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+}
+
 template <typename T>
 constexpr int stream_rows()
 {
     return 16;
+}
+
+int stream_launch_xs(const StreamCall& c)
+{
+    constexpr int RY = stream_rows<double>();
+    constexpr int NST = 6;
+    constexpr size_t box_bytes = sizeof(double) * (size_t)(RY + 2) * StreamShape<double>::BW;
+    constexpr size_t smem = NST * ((box_bytes + 127) / 128 * 128) + NST * sizeof(uint64_t);
+    if (c.box[0] != (uint32_t)StreamShape<double>::BW || c.box[1] != (uint32_t)(RY + 2))
+        return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
+                    c.box[1], StreamShape<double>::BW, RY + 2);
+    auto kern = k_heat_stream_xs<RY, NST>;
+    static bool configured = false;
+    if (!configured) {
+        HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "heat: streaming kernel smem attribute");
+        configured = true;
+    }
+    const HeatGeom& g = *c.g;
+    const int planes = c.kend - c.kbeg;
+    if (planes <= 0) return HS_OK;
+    constexpr int TXW = 32 * StreamShape<double>::V;
+    dim3 grid((g.nx + TXW - 1) / TXW, (g.ny + RY - 1) / RY, (planes + c.kc - 1) / c.kc);
+    dim3 block(32, RY, 1);
+    kern<<<grid, block, smem, c.stream>>>(*c.map, (double*)c.dst, g, c.r, c.kbeg, c.kend, c.kc, c.fx,
+                                          c.m3, c.err);
+    HS_CHECK_LAUNCH("heat streaming Interior kernel (FP64 exact sum)");
+    return HS_OK;
 }
 
 template <typename T, bool EXACT>
@@ -213,6 +443,7 @@ int stream_launch(const StreamCall& c)
     case A_F64_EXACT: return stream_launch_t<double, true>(c);
     case A_F32: return stream_launch_t<float, false>(c);
     case A_FX64: return stream_launch_t<long long, false>(c);
+    case A_F64_XS: return stream_launch_xs(c);
     }
     return fail(HS_EINVAL, "heat: unknown arithmetic");
 }

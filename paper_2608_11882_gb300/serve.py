@@ -68,12 +68,13 @@ class Result:
 
 def device_bytes(req: Request) -> int:
     """Device memory a request holds while admitted (both padded field buffers
-    for heat; r, p, q, b and x for CG), with row padding to 128 bytes."""
+    and, for FP64, the 64-byte per-step state, for heat; r, p, q, b and x for
+    CG), with row padding to 128 bytes."""
     nz, ny, nx = req.shape
     if req.kind == "heat":
         elem = 8 if req.dtype == "f64" else 4
         pitch = -(-(32 // elem + nx + 1) * elem // 128) * 128
-        return 2 * pitch * (ny + 2) * (nz + 2)
+        return 2 * pitch * (ny + 2) * (nz + 2) + (64 if req.dtype == "f64" else 0)
     return 5 * 8 * req.points
 
 

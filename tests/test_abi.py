@@ -46,5 +46,9 @@ def test_version_and_error_string_without_gpu():
     size = ctypes.c_size_t()
     desc.r = 0.1
     assert nat.lib.heat_device_bytes(ctypes.byref(desc), ctypes.byref(size)) == 0
-    # 2 buffers x 6 planes x 6 rows x 16-element (128-byte) rows of doubles
+    # two padded buffers (pitch 16, (ny+2)(nz+2) rows, 8-byte values) + the
+    # 64-byte per-step state of the default FP64 arithmetic
+    assert size.value == 2 * 6 * 6 * 16 * 8 + 64
+    desc.flags = nat.HS_FP64_PIPE   # the FP64-pipe arithmetic keeps no per-step state
+    assert nat.lib.heat_device_bytes(ctypes.byref(desc), ctypes.byref(size)) == 0
     assert size.value == 2 * 6 * 6 * 16 * 8

@@ -33,12 +33,18 @@ def run(pkg, u0, r, steps, dtype="f64", flags=0, tdepth=0):
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_blocked_equals_stepwise_bitwise(pkg, tdepth, shape, dtype):
     """Same per-point arithmetic, so the blocked pass reproduces one-step
-    stepping bit for bit; 19 steps leaves a remainder for every depth."""
+    stepping bit for bit (FP64 blocking computes on the FP64 pipe, so its
+    one-step twin is an HS_FP64_PIPE handle); 19 steps leaves a remainder for
+    every depth."""
     rng = np.random.default_rng(sum(shape) + tdepth)
     u0 = rng.uniform(-1, 1, size=shape)
-    a = run(pkg, u0, 0.16, 19, dtype=dtype, tdepth=1)
+    flags = pkg.HS_FP64_PIPE if dtype == "f64" else 0
+    a = run(pkg, u0, 0.16, 19, dtype=dtype, flags=flags, tdepth=1)
     b = run(pkg, u0, 0.16, 19, dtype=dtype, tdepth=tdepth)
     assert np.array_equal(a, b)
+    if dtype == "f64":   # and the default one-step (exact-sum) arithmetic agrees within the gate
+        c = run(pkg, u0, 0.16, 19, dtype=dtype, tdepth=1)
+        assert rel_max_err(c, b) <= F64_REL
 
 
 @pytest.mark.parametrize("tdepth", DEPTHS)
