@@ -94,18 +94,19 @@ extern "C" {
 /* HS_F64 only: do every operation of the update on the FP64 pipe (the six
  * additions and two fused multiply-adds of the written order).  Without this
  * flag a plain HS_F64 handle with tdepth <= 1 keeps its fields in FP64 but
- * forms the numerator S - 6u exactly: each value becomes the 64-bit integer
- * trunc(u 2^(1080 - e)), e the largest binary exponent field in the current
- * field (tracked on the device step by step), the integer sum is exact, and
- * u' = fma(r, (S - 6U) 2^(e - 1080), u) with the numerator rounded to the
- * nearest double -- one FP64 instruction per point instead of seven, the
- * conversions done with integer instructions.  Its error against exact
- * arithmetic on the same field is below 2 r 2^-57 max|u| + 2 ulp; values
- * more than 57 binades below the field's maximum count as 0 in the sum (not
- * as centre values).  Fields whose largest exponent field lies outside
- * [70, 2040] (all-zero or tiny fields, values near overflow, NaN, Inf) are
- * stepped on the FP64 pipe instead.  Temporal blocking (tdepth >= 2) and
- * HS_VARKAPPA always use the FP64 pipe. */
+ * forms the numerator S - 6u exactly: each value becomes a 64-bit integer
+ * within two units of u 2^(1080 - e), e the largest binary exponent field in
+ * the current field (tracked on the device step by step), the integer sum is
+ * exact, and u' = fma(r, (S - 6U) 2^(e - 1080), u) with the numerator rounded
+ * to the nearest double -- one or two FP64 instructions per point instead of
+ * seven, the rest done with integer instructions.  Its error against exact
+ * arithmetic on the same field is below 24 r 2^-57 max|u| + 2 ulp; values
+ * more than 58 binades below the field's maximum count as 0 (or one unit) in
+ * the sum, not as centre values.  Fields whose largest exponent field lies
+ * outside [max(70, 1081 - exponent field of r), 2040] (all-zero or tiny
+ * fields, values near overflow, NaN, Inf) are stepped on the FP64 pipe
+ * instead.  Temporal blocking (tdepth >= 2) and HS_VARKAPPA always use the
+ * FP64 pipe. */
 #define HS_FP64_PIPE        0x20u
 
 typedef struct hs_heat* hs_heat_t;

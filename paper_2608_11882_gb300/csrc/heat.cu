@@ -8,8 +8,9 @@
 //
 // Arithmetic, chosen per handle:
 //   FP64      (default) FP64 fields, the six-neighbour sum and S - 6u exact in
-//             64-bit fixed point on the field's current scale, converted back
-//             and applied with one FP64 fused multiply-add (heat_common.cuh);
+//             64-bit fixed point on the field's current scale, rounded back to
+//             a double and applied with one FP64 fused multiply-add
+//             (heat_common.cuh);
 //   FP64 pipe (HS_FP64_PIPE, and temporal blocking) the update in double
 //             precision with two fused multiply-adds;
 //   FP64 exact one rounding per operation in the written order (no FMA), the

@@ -155,47 +155,69 @@ template <typename T>
 constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
 // ---- FP64 with an exact neighbour sum ---------------------------------------------
-// FP64 fields in HBM, updated with one FP64 instruction per point.  Each value
-// u of the current field becomes the signed integer U = trunc(u 2^(1080 - e)),
-// where e is the largest biased exponent field among the field's values (so
-// |U| < 2^58; values more than 57 binades below the maximum become 0).  The
-// numerator L = S - 6U is then exact in 64-bit integers (|L| < 12 2^58), is
-// turned back into the nearest double L 2^(e - 1080) with integer operations
-// only, and u' = fma(r, L, u) rounds once.  Against the exact update of the
-// same field the error is below r 12 2^-57 max|u| plus two FP64 roundings.
-// The conversions use integer instructions because on GB300 every FP64 <-> int64
-// conversion instruction runs at the FP64 rate.  e is tracked per step like the
-// FIXED64 scale: slot m % 3 of an FxState holds the largest |u| bit pattern of
-// the field at step m (non-negative doubles order like their bit patterns).
-// Fields whose largest exponent is outside [kXsEmaxLo, kXsEmaxHi] -- tiny or
-// all-zero fields, values near overflow, NaN or Inf -- take the FP64-pipe
-// update (Point<double, false>), which also carries NaN and Inf through.
+// FP64 fields in HBM, updated with one or two FP64 instructions per point.
+// Each value u of the current field becomes a signed integer U within two
+// units of u 2^(1080 - e), where e is the largest biased exponent field among
+// the field's values (so |U| <= 2^58; values more than 58 binades below the
+// maximum become 0 or -1).  The numerator L = S - 6U is then exact in 64-bit
+// integers (|L| < 12 2^58 + 12), is rounded once to the nearest double
+// L 2^(e - 1080), and u' = fma(r, L, u) rounds once more.  Against the exact
+// update of the same field the error is below r 24 2^-57 max|u| plus two FP64
+// roundings.  GB300 runs FP64 <-> int64 conversion instructions at its narrow
+// FP64 rate, so U is formed with integer instructions; L becomes a double
+// either with integer instructions (xs_unfix) or with one FP64-pipe conversion
+// and the scale folded into r (r2 = r 2^(e - 1080)) -- the two give the same
+// double product, so the same result bit for bit, and a kernel may mix them to
+// balance its pipes.  e is tracked per step like the FIXED64 scale: slot
+// m % 3 of an FxState holds the largest |u| bit pattern of the field at step m
+// (non-negative doubles order like their bit patterns).  Fields whose largest
+// exponent lies outside [xs_emax_lo(r), kXsEmaxHi] -- tiny or all-zero fields
+// (and fields for which r 2^(e - 1080) would be subnormal), values near
+// overflow, NaN or Inf -- take the FP64-pipe update (Point<double, false>),
+// which also carries NaN and Inf through.
 constexpr int kXsEmaxLo = 70, kXsEmaxHi = 2040;
 
-__device__ __forceinline__ bool xs_native(int emax) { return emax < kXsEmaxLo || emax > kXsEmaxHi; }
+// Smallest e for which L 2^(e - 1080) (|L| >= 1) and r 2^(e - 1080) are normal.
+__device__ __forceinline__ int xs_emax_lo(double r)
+{
+    const int er = (int)((unsigned long long)__double_as_longlong(r) >> 52) & 0x7ff;
+    return er == 0 ? kXsEmaxLo : max(kXsEmaxLo, 1081 - er);
+}
+
+__device__ __forceinline__ bool xs_native(int emax, double r)
+{
+    return emax < xs_emax_lo(r) || emax > kXsEmaxHi;
+}
 
 __device__ __forceinline__ int xs_emax(const FxState* fx, int m3)
 {
     return (int)(__ldcg(&fx->slot[m3].maxU) >> 52);
 }
 
+// r 2^(e - 1080), exact when e >= xs_emax_lo(r).
+__device__ __forceinline__ double xs_r2(double r, int emax)
+{
+    return r * __longlong_as_double((long long)(emax - 57) << 52);
+}
+
 // The fixed-point integer of the double with bit pattern `bits` (its exponent
-// field must not exceed emax; zeros and subnormals give 0 for emax >= 64).
+// field must not exceed emax): the mantissa with its implicit bit, times 2^5,
+// in ones' complement for negative values, shifted right arithmetically by
+// emax - e (at most 63) -- floor((u 2^(1080 - emax)) - [u < 0] 2^-t), within two
+// units of u 2^(1080 - emax).  Zeros and subnormals give 0 or -1 for emax >= 64.
 __device__ __forceinline__ long long xs_fix(long long bits, int emax)
 {
     const unsigned hi = (unsigned)((unsigned long long)bits >> 32), lo = (unsigned)bits;
+    const unsigned s = (unsigned)((int)hi >> 31);   // 0 or all ones
     const unsigned e = (hi >> 20) & 0x7ffu;
-    // (1.mantissa) << 5: bits 57..0, the implicit bit at 57
-    const unsigned mh = (__funnelshift_l(lo, hi, 5) & 0x01ffffffu) | 0x02000000u;
-    const unsigned long long m5 = ((unsigned long long)mh << 32) | (unsigned long long)(lo << 5);
     const unsigned t = min((unsigned)(emax - (int)e), 63u);
-    const unsigned long long v = m5 >> t;
-    const unsigned long long s = (unsigned long long)((long long)(int)hi >> 31);   // 0 or all ones
-    return (long long)((v ^ s) - s);
+    const unsigned mh = ((__funnelshift_l(lo, hi, 5) & 0x01ffffffu) | 0x02000000u) ^ s;
+    const unsigned ml = (lo << 5) ^ s;
+    return (long long)(((unsigned long long)mh << 32) | ml) >> t;
 }
 
 // x 2^(emax - 1080) rounded to the nearest double, ties to even (|x| < 2^62,
-// kXsEmaxLo <= emax <= kXsEmaxHi, so the result is a normal number or zero).
+// xs_emax_lo <= emax <= kXsEmaxHi, so the result is a normal number or zero).
 __device__ __forceinline__ double xs_unfix(long long x, int emax)
 {
     const unsigned long long s = (unsigned long long)(x >> 63);
@@ -210,22 +232,30 @@ __device__ __forceinline__ double xs_unfix(long long x, int emax)
     return a ? __longlong_as_double(bits) : 0.0;
 }
 
-// The update of a point from its centre's double and the seven fixed-point values.
-__device__ __forceinline__ double xs_update(double uc, long long c, long long xm, long long xp,
-                                            long long ym, long long yp, long long zm, long long zp,
-                                            double r, int emax)
+// L = S - 6U of a point from its seven fixed-point values.
+__device__ __forceinline__ long long xs_numerator(long long c, long long xm, long long xp, long long ym,
+                                                  long long yp, long long zm, long long zp)
 {
-    const long long L = ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;
+    return ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;
+}
+
+// u' = fma(r, L 2^(emax - 1080), uc): DPCONV converts L on the FP64 pipe and
+// scales r instead (r2 = xs_r2(r, emax)); both round the same exact product.
+template <bool DPCONV>
+__device__ __forceinline__ double xs_apply(double uc, long long L, double r, double r2, int emax)
+{
+    if constexpr (DPCONV) return __fma_rn(r2, __ll2double_rn(L), uc);
     return __fma_rn(r, xs_unfix(L, emax), uc);
 }
 
-// The same update from seven doubles (kernels that convert per point).
+// The whole update from seven doubles (kernels that convert per point).
 __device__ __forceinline__ double xs_point(double c, double xm, double xp, double ym, double yp,
                                            double zm, double zp, double r, int emax)
 {
-    if (xs_native(emax)) return Point<double, false>::update(c, xm, xp, ym, yp, zm, zp, r, 0);
+    if (xs_native(emax, r)) return Point<double, false>::update(c, xm, xp, ym, yp, zm, zp, r, 0);
     auto f = [emax](double v) { return xs_fix(__double_as_longlong(v), emax); };
-    return xs_update(c, f(c), f(xm), f(xp), f(ym), f(yp), f(zm), f(zp), r, emax);
+    const long long L = xs_numerator(f(c), f(xm), f(xp), f(ym), f(yp), f(zm), f(zp));
+    return xs_apply<false>(c, L, r, 0.0, emax);
 }
 
 // |u| of a result as the high word of its bit pattern (the exponent field and

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(32 * RY)
 // iteration), warps 0 and 1 the halo rows, warp 2 the two halo columns, so each
 // staged value is converted once.  Plane k, converted one iteration earlier,
 // gives the in-plane neighbours.  A point then costs the exact integer sum, one
-// conversion back and one FP64 fused multiply-add.  Converted slots are written
+// conversion back (on the FP64 pipe for a thread's first point, with integer
+// instructions for its second) and one FP64 fused multiply-add.  Converted slots are written
 // through the generic proxy and refilled later by TMA (the async proxy), so
 // every thread fences the async proxy after its conversion stores, before the
 // block barrier that precedes a refill.  CONV = false is the FP64-pipe update
@@ -207,6 +208,7 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     const bool row_ok = (Y < g.ny);
     const int nvalid = row_ok ? min(V, g.nx - X) : 0;
     const int p_first = kb - 1, p_last = ke;
+    const double r2 = CONV ? xs_r2(r, emax) : 0.0;
     // what this thread converts besides its own vector: a vector of halo row 0
     // (warp 0) or RY+1 (warp 1), or one halo-column value (warp 2)
     int extra = -1;
@@ -289,7 +291,11 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
                 const long long xm = i == 0 ? left : cur[i - 1];
                 const long long xp = i == V - 1 ? right : cur[i + 1];
                 if constexpr (CONV) {
-                    v[i] = xs_update(craw[i], cur[i], xm, xp, ym[i], yp[i], below[i], above[i], r, emax);
+                    // the first point converts L on the FP64 pipe, the second with
+                    // integer instructions: the same result, the two pipes shared
+                    const long long L = xs_numerator(cur[i], xm, xp, ym[i], yp[i], below[i], above[i]);
+                    v[i] = i == 0 ? xs_apply<true>(craw[i], L, r, r2, emax)
+                                  : xs_apply<false>(craw[i], L, r, r2, emax);
                 } else {
                     auto d = [](long long b) { return __longlong_as_double(b); };
                     v[i] = Point<double, false>::update(craw[i], d(xm), d(xp), d(ym[i]), d(yp[i]),
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(32 * RY)
     if (s_abort) return;
     const int emax = xs_emax(fx, m3);
     unsigned mx = 0;
-    if (xs_native(emax))
+    if (xs_native(emax, r))
         xs_stream_body<RY, NST, false>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
     else
         xs_stream_body<RY, NST, true>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);

@@ -48,8 +48,8 @@ def test_wide_dynamic_range(pkg):
     ref = oracle.heat_run(u0, 0.1, 40)
     got = run(pkg, u0, 0.1, 40)
     assert rel_max_err(got, ref) <= F64_REL
-    # per step at most r * 12 * 2^-57 max|u| from the sum plus two roundings of each result
-    bound = 40 * (0.1 * 12 * 2.0**-57 + 4 * 2.0**-53) * float(np.max(np.abs(u0)))
+    # per step at most r * 24 * 2^-57 max|u| from the sum plus two roundings of each result
+    bound = 40 * (0.1 * 24 * 2.0**-57 + 4 * 2.0**-53) * float(np.max(np.abs(u0)))
     assert float(np.max(np.abs(got - ref))) <= bound
 
 
