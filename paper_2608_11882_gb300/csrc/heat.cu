@@ -542,11 +542,13 @@ int pick_kc_tb(const HeatGeom& g, int L)
     return (int)kc;
 }
 
-int pick_kc_stream(const HeatGeom& g)
+int pick_kc_stream(const HeatGeom& g, int arith)
 {
     const int tw = 512 / (int)g.elem;                  // tile width: 32 threads x one 16-byte vector
-    const int64_t tiles = (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + kStreamRowsHost - 1) / kStreamRowsHost);
-    const int64_t target = (int64_t)kNumSMs * 3 * 4;   // about four waves of three blocks per SM
+    const int ry = stream_rows_for(arith);
+    const int64_t tiles = (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + ry - 1) / ry);
+    // about four waves of 3 blocks of 16 rows per SM (the exact-sum kernel: 4 of 8 rows)
+    const int64_t target = (int64_t)kNumSMs * (arith == A_F64_XS ? 4 : 3) * 4;
     const int64_t planes = g.nz > 2 ? g.nz - 2 : 1;
     int64_t chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
@@ -727,7 +729,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
                 return rc;
             }
         }
-        h->kc_stream = pick_kc_stream(h->g);
+        h->kc_stream = pick_kc_stream(h->g, h->arith);
     }
     if (h->tdepth > 1) {
         const CUtensorMapDataType dt = h->arith == A_FX64   ? CU_TENSOR_MAP_DATA_TYPE_INT64

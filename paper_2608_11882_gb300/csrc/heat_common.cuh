@@ -380,8 +380,11 @@ inline T stream_param(const StreamCall& c)
 int stream_launch(const StreamCall& c);
 // TMA box (elements x rows) the streaming kernel loads for an arithmetic.
 int stream_box(int arith, uint32_t* box_x, uint32_t* box_y);
-// Rows of the streaming kernel's tile (its tile is 32 x kStreamRows columns).
+// Rows of the streaming kernels' tiles (a tile is 32 threads x rows): 16 for
+// k_heat_stream, kXsRows for the exact-sum FP64 kernel.
 constexpr int kStreamRowsHost = 16;
+constexpr int kXsRows = 8;
+inline int stream_rows_for(int arith) { return arith == A_F64_XS ? kXsRows : kStreamRowsHost; }
 
 // One launch of a variable-coefficient kernel (heat_vk.cu).
 struct VkCall {

@@ -197,7 +197,7 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     constexpr int ROWS = RY + 2;
     constexpr uint32_t BOX_BYTES = ROWS * BW * (uint32_t)sizeof(double);
     constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(double));
-    static_assert(V == 2 && 2 * RY == 32, "warp 2 converts the 2 RY halo-column values");
+    static_assert(V == 2 && 2 * RY <= 32 && RY >= 3, "warp 2 converts the 2 RY halo-column values");
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
@@ -214,7 +214,8 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     int extra = -1;
     if (ty == 0) extra = S::D + V * tx;
     else if (ty == 1) extra = (RY + 1) * BW + S::D + V * tx;
-    else if (ty == 2) extra = tx < RY ? (tx + 1) * BW + S::D - 1 : (tx - RY + 1) * BW + S::D + 32 * V;
+    else if (ty == 2 && tx < 2 * RY)
+        extra = tx < RY ? (tx + 1) * BW + S::D - 1 : (tx - RY + 1) * BW + S::D + 32 * V;
 
     // converts this thread's part of the staged plane at `pl`; returns its own raw vector
     auto convert = [&](long long* pl, long long (&q)[V], double (&raw)[V]) {
@@ -233,7 +234,7 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
 #pragma unroll
                 for (int i = 0; i < V; ++i) h[i] = xs_fix(h[i], emax);
                 st_vec(pl + extra, h);
-            } else if (ty == 2) {
+            } else if (extra >= 0) {
                 pl[extra] = xs_fix(pl[extra], emax);
             }
         }
@@ -387,7 +388,7 @@ constexpr int stream_rows()
 
 int stream_launch_xs(const StreamCall& c)
 {
-    constexpr int RY = stream_rows<double>();
+    constexpr int RY = kXsRows;
     constexpr int NST = 6;
     constexpr size_t box_bytes = sizeof(double) * (size_t)(RY + 2) * StreamShape<double>::BW;
     constexpr size_t smem = NST * ((box_bytes + 127) / 128 * 128) + NST * sizeof(uint64_t);
@@ -457,6 +458,10 @@ int stream_launch(const StreamCall& c)
 int stream_box(int arith, uint32_t* box_x, uint32_t* box_y)
 {
     switch (arith) {
+    case A_F64_XS:
+        *box_x = StreamShape<double>::BW;
+        *box_y = kXsRows + 2;
+        return 0;
     case A_F32:
         *box_x = StreamShape<float>::BW;
         *box_y = stream_rows<float>() + 2;
