@@ -270,6 +270,12 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
  * last iterate on exit.  b and x are host arrays if host_buffers != 0 (copied
  * in and out on the context's stream), device arrays otherwise.  Dot products
  * accumulate in FP64 in a fixed order, so repeated runs agree bit for bit.
+ * For the matrix-free operator the SpMV forms 6p - (sum of the neighbours)
+ * exactly in 64-bit fixed point on p's current scale (its largest exponent,
+ * tracked on the device) and rounds it once to FP64 -- error below
+ * 24 2^-57 max|p| plus one rounding, where FP64 arithmetic rounds about seven
+ * times; a p whose exponents fall outside the convertible range (see
+ * HS_FP64_PIPE) takes FP64 arithmetic.  op_apply always computes in FP64.
  * Synchronises the stream.  Returns HS_OK when converged, HS_ENOCONV when
  * max_iter iterations ran without reaching rtol (x and info are still
  * filled), or an error code.  info may be NULL. */

@@ -3,7 +3,9 @@
 // p update, deterministic grid reductions, and the cg_* / op_apply entry
 // points of the C ABI.
 //
-// CG in the textbook form (unpreconditioned, FP64):
+// CG in the textbook form (unpreconditioned, FP64; the matrix-free SpMV forms
+// 6p - (neighbour sum) exactly in 64-bit fixed point on p's scale and rounds it
+// once -- xsum.cuh -- while p's exponents allow, the FP64 pipe otherwise):
 //     r0 = b - A x0, p0 = r0, rho0 = r0.r0
 //     q = A p;  alpha = rho / p.q;  x += alpha p;  r -= alpha q;  rho' = r.r
 //     stop when sqrt(rho') / ||b|| <= rtol, else p = r + (rho'/rho) p.
@@ -37,10 +39,12 @@ __global__ void __launch_bounds__(kCgBlock)
 // r = b - q, p = r; rho = r.r, ||b||; decides whether x0 already meets rtol.
 __global__ void __launch_bounds__(kCgBlock)
     k_cg_start(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
-               double* __restrict__ r, double* __restrict__ p, double* partials, CgScalars* S)
+               double* __restrict__ r, double* __restrict__ p, double* partials, CgScalars* S,
+               int track_pmax)
 {
     __shared__ double sh[kCgBlock / 32];
     double rr = 0.0, bb = 0.0;
+    unsigned pm = 0;
     for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * kCgBlock) {
         const double bt = b[t];
@@ -49,9 +53,11 @@ __global__ void __launch_bounds__(kCgBlock)
         p[t] = rt;
         rr = __fma_rn(rt, rt, rr);
         bb = __fma_rn(bt, bt, bb);
+        pm = max(pm, xs_abs_hi(rt));
     }
     const double rr_blk = block_sum<kCgBlock>(rr, sh);
     const double bb_blk = block_sum<kCgBlock>(bb, sh);
+    if (track_pmax) cg_fold_pmax(pm, S, 0, blockIdx.x == 0);   // p0 = r0: iteration 0's direction
     // two partial arrays: [0, G) for r.r and [G, 2G) for b.b
     if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = bb_blk;
     if (!arrive_last(rr_blk, partials, &S->ticket)) return;
@@ -82,11 +88,16 @@ __global__ void __launch_bounds__(kCgBlock)
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
-    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
-         row += (int64_t)gridDim.x * kCgBlock) {
-        const double qv = apply_row<KIND>(A, p, row);
-        q[row] = qv;
-        pq = __fma_rn(__ldg(p + row), qv, pq);
+    const int64_t row0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * kCgBlock;
+    if (KIND == HS_OP_STENCIL7) {
+        pq = spmv_stencil_blocks(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
+    } else {
+        for (int64_t row = row0; row < A.n; row += stride) {
+            const double qv = apply_row<KIND>(A, p, row);
+            q[row] = qv;
+            pq = __fma_rn(__ldg(p + row), qv, pq);
+        }
     }
     const double blk = block_sum<kCgBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
@@ -138,13 +149,26 @@ __global__ void __launch_bounds__(kCgBlock)
 
 // p = r + beta p.
 __global__ void __launch_bounds__(kCgBlock)
-    k_cg_pupdate(int64_t n, const double* __restrict__ r, double* __restrict__ p, CgScalars* S)
+    k_cg_pupdate(int64_t n, const double* __restrict__ r, double* __restrict__ p, CgScalars* S,
+                 int track_pmax)
 {
     if (*(volatile int32_t*)&S->done) return;
     const double beta = S->beta;
+    if (!track_pmax) {
+        for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+             t += (int64_t)gridDim.x * kCgBlock)
+            p[t] = __fma_rn(beta, p[t], r[t]);
+        return;
+    }
+    unsigned pm = 0;
     for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * kCgBlock)
-        p[t] = __fma_rn(beta, p[t], r[t]);
+         t += (int64_t)gridDim.x * kCgBlock) {
+        const double v = __fma_rn(beta, p[t], r[t]);
+        p[t] = v;
+        pm = max(pm, xs_abs_hi(v));
+    }
+    // the update kernel has counted this iteration: p is the next one's direction
+    cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
 }
 
 // ||b - q||^2 into S->rr_true (q = A x).
@@ -357,7 +381,8 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
                 "cg_run: scalar init");
     int rc = launch_apply(c->A, x, c->q, c->stream);   // q = A x0
     if (rc != HS_OK) return rc;
-    k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S);
+    const int track = c->A.kind == HS_OP_STENCIL7;
+    k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S, track);
     HS_CHECK_LAUNCH("cg: start kernel");
 
     // Iterate in chunks, reading the stop flag and count between chunks.
@@ -381,7 +406,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
             HS_CHECK_LAUNCH("cg: spmv+dot kernel");
             k_cg_update<<<c->grid, kCgBlock, 0, c->stream>>>(nn, x, c->r, c->p, c->q, c->partials, c->S);
             HS_CHECK_LAUNCH("cg: update kernel");
-            k_cg_pupdate<<<c->grid, kCgBlock, 0, c->stream>>>(nn, c->r, c->p, c->S);
+            k_cg_pupdate<<<c->grid, kCgBlock, 0, c->stream>>>(nn, c->r, c->p, c->S, track);
             HS_CHECK_LAUNCH("cg: p update kernel");
         }
         enqueued += todo;

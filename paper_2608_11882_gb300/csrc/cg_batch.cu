@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
     __shared__ double sh[kCgBlock / 32];
     double rr = 0.0, bb = 0.0;
+    unsigned pm = 0;
     for (int64_t t = (int64_t)local * kCgBlock + threadIdx.x; t < s.A.n;
          t += (int64_t)s.nblocks * kCgBlock) {
         const double bt = s.b[t];
@@ -97,9 +98,11 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
         s.p[t] = rt;
         rr = __fma_rn(rt, rt, rr);
         bb = __fma_rn(bt, bt, bb);
+        pm = max(pm, xs_abs_hi(rt));
     }
     const double rr_blk = block_sum<kCgBlock>(rr, sh);
     const double bb_blk = block_sum<kCgBlock>(bb, sh);
+    if (s.A.kind == HS_OP_STENCIL7) cg_fold_pmax(pm, s.S, 0, local == 0);
     if (threadIdx.x == 0) s.partials[s.nblocks + local] = bb_blk;
     if (!arrive_last_sys(rr_blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho = sum_partials_n(s.partials, s.nblocks, sh);
@@ -128,8 +131,12 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, in
     if (*(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
-    for (int64_t row = (int64_t)local * kCgBlock + threadIdx.x; row < s.A.n;
-         row += (int64_t)s.nblocks * kCgBlock) {
+    // as k_cg_spmv_dot: the same rows per thread and per-row arithmetic, so the same results
+    const int64_t row0 = (int64_t)local * kCgBlock + threadIdx.x;
+    const int64_t stride = (int64_t)s.nblocks * kCgBlock;
+    if (s.A.kind == HS_OP_STENCIL7) {
+        pq = spmv_stencil_blocks(s.A, s.p, s.q, cg_pemax(s.S), local, s.nblocks);
+    } else for (int64_t row = row0; row < s.A.n; row += stride) {
         const double qv = apply_sys(s.A, s.p, row);
         s.q[row] = qv;
         pq = __fma_rn(__ldg(s.p + row), qv, pq);
@@ -186,9 +193,14 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int
     // the update kernel of this iteration has already counted it
     if (*(volatile int32_t*)&s.S->done) return;
     const double beta = s.S->beta;
+    unsigned pm = 0;
     for (int64_t t = (int64_t)local * kCgBlock + threadIdx.x; t < s.A.n;
-         t += (int64_t)s.nblocks * kCgBlock)
-        s.p[t] = __fma_rn(beta, s.p[t], s.r[t]);
+         t += (int64_t)s.nblocks * kCgBlock) {
+        const double v = __fma_rn(beta, s.p[t], s.r[t]);
+        s.p[t] = v;
+        pm = max(pm, xs_abs_hi(v));
+    }
+    if (s.A.kind == HS_OP_STENCIL7) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
 }
 
 // ||b - A x||^2 into rr_true (q = A x from k_cgb_apply_x).
@@ -269,7 +281,7 @@ int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* strea
         s.block0 = (int32_t)blocks;
         blocks += s.nblocks;
         b->rows[(size_t)i] = s.A.n;
-        vec_total += s.A.n;
+        vec_total += (s.A.n + 1) & ~(int64_t)1;   // every vector starts 16-byte aligned
         part_total += 2 * (int64_t)s.nblocks;
     }
     if (blocks > INT32_MAX) {
@@ -297,7 +309,7 @@ int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* strea
         s.q = base + 2 * vec_total + off;
         s.partials = part + poff;
         s.S = b->d_S + i;
-        off += s.A.n;
+        off += (s.A.n + 1) & ~(int64_t)1;
         poff += 2 * (int64_t)s.nblocks;
     }
     *out = b;

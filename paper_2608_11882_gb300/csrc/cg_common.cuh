@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "xsum.cuh"
 
 namespace hcg {
 
@@ -22,6 +23,10 @@ struct CgScalars {
     int32_t iters;
     uint32_t ticket;   // blocks finished in the running reduction
     int32_t zero_rhs;  // ||b|| == 0
+    // Largest |p| bit pattern of the direction p_i in slot i % 3 (matrix-free
+    // operator): the kernel that forms p_i folds its values in and clears slot
+    // (i+1) % 3; the SpMV of iteration i reads slot i % 3.
+    unsigned long long pmax[3];
 };
 
 constexpr int kCgBlock = 256;
@@ -98,6 +103,231 @@ __device__ __forceinline__ double apply_row(const OpDev& A, const double* __rest
 {
     if (KIND == HS_OP_STENCIL7) return apply_stencil_row(A, p, row);
     return apply_csr_row(A, p, row);
+}
+
+// Largest exponent field of the direction p of the current iteration, and
+// whether the matrix-free SpMV may use the exact-sum form for it.
+__device__ __forceinline__ int cg_pemax(const CgScalars* S)
+{
+    return (int)(__ldcg(&S->pmax[S->iters % 3]) >> 52);
+}
+
+__device__ __forceinline__ bool cg_xs_ok(int emax) { return emax >= kXsEmaxLo && emax <= kXsEmaxHi; }
+
+// ---- matrix-free SpMV staged through shared memory ---------------------------------
+// A block of kCgBlock = 256 threads (8 warps) owns a tile of 64 x 8 points of
+// the grid and a chunk of z-planes, and marches up the chunk: every thread two
+// consecutive x points of one row.  Each z-plane of the tile, with a one-point
+// halo, is loaded once with coalesced loads (a plane ahead of its use),
+// converted once to fixed point (exact-sum form) and written to one of two
+// shared plane buffers; a thread keeps its own values at k-1, k and k+1 in
+// registers, reads the in-plane neighbours from the buffer of plane k, and
+// one block barrier per plane orders the buffers.  Points outside the grid
+// are staged as zeros (the Dirichlet boundary).  Work items (tile, chunk) are
+// taken by the system's `nblocks` blocks in a fixed order, so a block's partial
+// p.q -- and the whole reduction -- repeats bit for bit wherever the same
+// operator runs with the same block count (a batch uses its systems' own).
+constexpr int kSpTW = 64, kSpTY = 8, kSpBW = 68, kSpD = 2;   // tile width/rows, buffer row, x offset
+constexpr int kSpPlane = (kSpTY + 2) * kSpBW;                // buffer elements per plane
+static_assert(kSpTY * 32 == kCgBlock, "one warp per tile row");
+
+struct SpmvPlan {
+    int64_t tiles, items;
+    int tiles_x, kc;       // tiles per row of tiles, planes per chunk
+};
+
+// About two work items per block, at least 4 planes per chunk.
+__host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A, int nblocks)
+{
+    SpmvPlan P;
+    P.tiles_x = (A.nx + kSpTW - 1) / kSpTW;
+    P.tiles = (int64_t)P.tiles_x * ((A.ny + kSpTY - 1) / kSpTY);
+    int64_t chunks = (2 * (int64_t)nblocks + P.tiles - 1) / P.tiles;
+    const int64_t maxc = A.nz / 4 > 1 ? A.nz / 4 : 1;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    P.kc = (int)((A.nz + chunks - 1) / chunks);
+    chunks = (A.nz + P.kc - 1) / P.kc;
+    P.items = P.tiles * chunks;
+    return P;
+}
+
+// One work item: q = A p on the tile's planes [kb, ke), returning this
+// thread's share of p.q.  CONV: the exact-sum form (emax = p's largest
+// exponent field; odd warps convert the row sums on the FP64 pipe, even warps
+// with integers); otherwise the FP64-pipe row of apply_stencil_row.
+template <bool CONV>
+__device__ __forceinline__ double spmv_item(const OpDev& A, const double* __restrict__ p,
+                                            double* __restrict__ q, int emax, const SpmvPlan& P,
+                                            int64_t tile, int kb, int ke, long long* buf)
+{
+    constexpr int V = 2, BW = kSpBW;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int x0 = (int)(tile % P.tiles_x) * kSpTW, y0 = (int)(tile / P.tiles_x) * kSpTY;
+    const int X = x0 + V * tx, Y = y0 + ty;
+    const int own = (ty + 1) * BW + kSpD + V * tx;
+    const bool ok0 = Y < ny && X < nx, ok1 = Y < ny && X + 1 < nx;
+    // a 16-byte pair: X is even, so the pair is aligned when nx is even and
+    // both vectors start 16-byte aligned
+    const bool vec = ok1 && (nx & 1) == 0 &&
+                     (((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0);
+    const int64_t rowoff = (int64_t)Y * nx + X;
+    // one halo value per thread for the first 2*64 + 2*8 threads
+    int hidx = -1, hx = -1, hy = -1;
+    if (tid < 2 * kSpTW) {
+        const int r = tid < kSpTW ? 0 : kSpTY + 1;
+        const int c = tid % kSpTW;
+        hidx = r * BW + kSpD + c;
+        hx = x0 + c;
+        hy = r == 0 ? y0 - 1 : y0 + kSpTY;
+    } else if (tid < 2 * kSpTW + 2 * kSpTY) {
+        const int t = tid - 2 * kSpTW;
+        const int r = 1 + t % kSpTY;
+        const bool right = t >= kSpTY;
+        hidx = r * BW + (right ? kSpD + kSpTW : kSpD - 1);
+        hx = right ? x0 + kSpTW : x0 - 1;
+        hy = y0 + r - 1;
+    }
+    const bool hok = hidx >= 0 && hx >= 0 && hx < nx && hy >= 0 && hy < ny;
+    const int64_t hoff = (int64_t)hy * nx + hx;
+    const long long* pb = reinterpret_cast<const long long*>(p);
+    auto ld_own = [&](int k, long long (&o)[V]) {
+        o[0] = 0;
+        o[1] = 0;
+        if (k < 0 || k >= nz) return;
+        const long long* src = pb + (int64_t)k * sxy + rowoff;
+        if (vec) {
+            const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(src));
+            o[0] = v.x;
+            o[1] = v.y;
+        } else {
+            if (ok0) o[0] = __ldg(src);
+            if (ok1) o[1] = __ldg(src + 1);
+        }
+    };
+    auto ld_halo = [&](int k) -> long long {
+        return (hok && k >= 0 && k < nz) ? __ldg(pb + (int64_t)k * sxy + hoff) : 0;
+    };
+    auto fix = [&](long long b) -> long long { return CONV ? xs_fix(b, emax) : b; };
+    const bool dp = (ty & 1) != 0;
+
+    long long below[V], cur[V], above[V], nown[V], t[V];
+    double craw[V], araw[V];
+    ld_own(kb - 1, t);
+    below[0] = fix(t[0]);
+    below[1] = fix(t[1]);
+    ld_own(kb, t);
+    craw[0] = __longlong_as_double(t[0]);
+    craw[1] = __longlong_as_double(t[1]);
+    cur[0] = fix(t[0]);
+    cur[1] = fix(t[1]);
+    {
+        long long* b0 = buf + (kb & 1) * kSpPlane;
+        b0[own] = cur[0];
+        b0[own + 1] = cur[1];
+        if (hidx >= 0) b0[hidx] = fix(ld_halo(kb));
+    }
+    ld_own(kb + 1, t);
+    araw[0] = __longlong_as_double(t[0]);
+    araw[1] = __longlong_as_double(t[1]);
+    above[0] = fix(t[0]);
+    above[1] = fix(t[1]);
+    long long h1 = ld_halo(kb + 1), nh = 0;
+    nown[0] = 0;
+    nown[1] = 0;
+    if (kb + 2 <= ke) {
+        ld_own(kb + 2, nown);
+        nh = ld_halo(kb + 2);
+    }
+    __syncthreads();
+
+    double pq = 0.0;
+    for (int k = kb; k < ke; ++k) {
+        long long* bn = buf + ((k + 1) & 1) * kSpPlane;   // plane k+1: published for the next iteration
+        bn[own] = above[0];
+        bn[own + 1] = above[1];
+        if (hidx >= 0) bn[hidx] = fix(h1);
+        const long long* pc = buf + (k & 1) * kSpPlane + own;
+        const long long ym0 = pc[-BW], ym1 = pc[1 - BW], yp0 = pc[BW], yp1 = pc[1 + BW];
+        const long long left = pc[-1], right = pc[V];
+        double qv[V];
+        if constexpr (CONV) {
+            const long long L0 = 6 * cur[0] - (((below[0] + ym0) + (left + cur[1])) + (yp0 + above[0]));
+            const long long L1 = 6 * cur[1] - (((below[1] + ym1) + (cur[0] + right)) + (yp1 + above[1]));
+            qv[0] = dp ? xs_unfix_dp(L0, emax) : xs_unfix(L0, emax);
+            qv[1] = dp ? xs_unfix_dp(L1, emax) : xs_unfix(L1, emax);
+        } else {
+            auto d = [](long long b) { return __longlong_as_double(b); };
+            const double s0 = ((d(below[0]) + d(ym0)) + (d(left) + d(cur[1]))) + (d(yp0) + d(above[0]));
+            const double s1 = ((d(below[1]) + d(ym1)) + (d(cur[0]) + d(right))) + (d(yp1) + d(above[1]));
+            qv[0] = __fma_rn(6.0, d(cur[0]), -s0);
+            qv[1] = __fma_rn(6.0, d(cur[1]), -s1);
+        }
+        double* dst = q + (int64_t)k * sxy + rowoff;
+        if (vec) {
+            *reinterpret_cast<double2*>(dst) = make_double2(qv[0], qv[1]);
+        } else {
+            if (ok0) dst[0] = qv[0];
+            if (ok1) dst[1] = qv[1];
+        }
+        if (ok0) pq = __fma_rn(craw[0], qv[0], pq);
+        if (ok1) pq = __fma_rn(craw[1], qv[1], pq);
+        below[0] = cur[0];
+        below[1] = cur[1];
+        cur[0] = above[0];
+        cur[1] = above[1];
+        craw[0] = araw[0];
+        craw[1] = araw[1];
+        araw[0] = __longlong_as_double(nown[0]);
+        araw[1] = __longlong_as_double(nown[1]);
+        above[0] = fix(nown[0]);
+        above[1] = fix(nown[1]);
+        h1 = nh;
+        if (k + 3 <= ke) {
+            ld_own(k + 3, nown);
+            nh = ld_halo(k + 3);
+        }
+        __syncthreads();
+    }
+    return pq;
+}
+
+// The matrix-free SpMV of a block over its work items; returns the thread's p.q.
+__device__ __forceinline__ double spmv_stencil_blocks(const OpDev& A, const double* __restrict__ p,
+                                                      double* __restrict__ q, int emax, int local,
+                                                      int nblocks)
+{
+    __shared__ __align__(16) long long buf[2 * kSpPlane];
+    const SpmvPlan P = spmv_plan(A, nblocks);
+    double pq = 0.0;
+    const bool conv = cg_xs_ok(emax);
+    for (int64_t item = local; item < P.items; item += nblocks) {
+        const int64_t tile = item % P.tiles;
+        const int kb = (int)(item / P.tiles) * P.kc;
+        const int ke = min(kb + P.kc, A.nz);
+        pq += conv ? spmv_item<true>(A, p, q, emax, P, tile, kb, ke, buf)
+                   : spmv_item<false>(A, p, q, emax, P, tile, kb, ke, buf);
+    }
+    return pq;
+}
+
+// Folds a block's largest |p| high word (m, per thread) into S->pmax[slot] and,
+// from the system's first block, clears the slot after it.  All threads call it.
+__device__ __forceinline__ void cg_fold_pmax(unsigned m, CgScalars* S, int slot, bool first_block)
+{
+    __shared__ unsigned wmax[kCgBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned b = 0;
+        for (int w = 0; w < kCgBlock / 32; ++w) b = max(b, wmax[w]);
+        atomicMax(&S->pmax[slot], (unsigned long long)b << 32);
+        if (first_block) S->pmax[(slot + 1) % 3] = 0;
+    }
 }
 
 struct CgMixed;   // mixed-precision state (cg_mixed.cu)

@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "xsum.cuh"
 
 namespace hcg {
 
@@ -154,98 +155,17 @@ struct Point<long long, EXACT> {
 template <typename T>
 constexpr bool kIsFixed = std::is_same<T, long long>::value;
 
-// ---- FP64 with an exact neighbour sum ---------------------------------------------
-// FP64 fields in HBM, updated with one or two FP64 instructions per point.
-// Each value u of the current field becomes a signed integer U within two
-// units of u 2^(1080 - e), where e is the largest biased exponent field among
-// the field's values (so |U| <= 2^58; values more than 58 binades below the
-// maximum become 0 or -1).  The numerator L = S - 6U is then exact in 64-bit
-// integers (|L| < 12 2^58 + 12), is rounded once to the nearest double
-// L 2^(e - 1080), and u' = fma(r, L, u) rounds once more.  Against the exact
-// update of the same field the error is below r 24 2^-57 max|u| plus two FP64
-// roundings.  GB300 runs FP64 <-> int64 conversion instructions at its narrow
-// FP64 rate, so U is formed with integer instructions; L becomes a double
-// either with integer instructions (xs_unfix) or with one FP64-pipe conversion
-// and the scale folded into r (r2 = r 2^(e - 1080)) -- the two give the same
-// double product, so the same result bit for bit, and a kernel may mix them to
-// balance its pipes.  e is tracked per step like the FIXED64 scale: slot
-// m % 3 of an FxState holds the largest |u| bit pattern of the field at step m
-// (non-negative doubles order like their bit patterns).  Fields whose largest
-// exponent lies outside [xs_emax_lo(r), kXsEmaxHi] -- tiny or all-zero fields
-// (and fields for which r 2^(e - 1080) would be subnormal), values near
-// overflow, NaN or Inf -- take the FP64-pipe update (Point<double, false>),
-// which also carries NaN and Inf through.
-constexpr int kXsEmaxLo = 70, kXsEmaxHi = 2040;
-
-// Smallest e for which L 2^(e - 1080) (|L| >= 1) and r 2^(e - 1080) are normal.
-__device__ __forceinline__ int xs_emax_lo(double r)
-{
-    const int er = (int)((unsigned long long)__double_as_longlong(r) >> 52) & 0x7ff;
-    return er == 0 ? kXsEmaxLo : max(kXsEmaxLo, 1081 - er);
-}
-
-__device__ __forceinline__ bool xs_native(int emax, double r)
-{
-    return emax < xs_emax_lo(r) || emax > kXsEmaxHi;
-}
-
+// ---- FP64 with an exact neighbour sum (the arithmetic is in xsum.cuh) -----------------
+// The heat update in this arithmetic: u' = fma(r, L 2^(e - 1080), u) with the
+// exact numerator L = S - 6U, one or two FP64 instructions per point; its
+// error against the exact update of the same field is below r 24 2^-57 max|u|
+// plus two FP64 roundings.  e is tracked per step like the FIXED64 scale: slot
+// m % 3 of an FxState holds the largest |u| bit pattern of the field at step
+// m.  Fields outside the convertible range take Point<double, false>.
+// The field's largest exponent field at step m: slot m % 3 of its FxState.
 __device__ __forceinline__ int xs_emax(const FxState* fx, int m3)
 {
     return (int)(__ldcg(&fx->slot[m3].maxU) >> 52);
-}
-
-// r 2^(e - 1080), exact when e >= xs_emax_lo(r).
-__device__ __forceinline__ double xs_r2(double r, int emax)
-{
-    return r * __longlong_as_double((long long)(emax - 57) << 52);
-}
-
-// The fixed-point integer of the double with bit pattern `bits` (its exponent
-// field must not exceed emax): the mantissa with its implicit bit, times 2^5,
-// in ones' complement for negative values, shifted right arithmetically by
-// emax - e (at most 63) -- floor((u 2^(1080 - emax)) - [u < 0] 2^-t), within two
-// units of u 2^(1080 - emax).  Zeros and subnormals give 0 or -1 for emax >= 64.
-__device__ __forceinline__ long long xs_fix(long long bits, int emax)
-{
-    const unsigned hi = (unsigned)((unsigned long long)bits >> 32), lo = (unsigned)bits;
-    const unsigned s = (unsigned)((int)hi >> 31);   // 0 or all ones
-    const unsigned e = (hi >> 20) & 0x7ffu;
-    const unsigned t = min((unsigned)(emax - (int)e), 63u);
-    const unsigned mh = ((__funnelshift_l(lo, hi, 5) & 0x01ffffffu) | 0x02000000u) ^ s;
-    const unsigned ml = (lo << 5) ^ s;
-    return (long long)(((unsigned long long)mh << 32) | ml) >> t;
-}
-
-// x 2^(emax - 1080) rounded to the nearest double, ties to even (|x| < 2^62,
-// xs_emax_lo <= emax <= kXsEmaxHi, so the result is a normal number or zero).
-__device__ __forceinline__ double xs_unfix(long long x, int emax)
-{
-    const unsigned long long s = (unsigned long long)(x >> 63);
-    const unsigned long long a = ((unsigned long long)x ^ s) - s;
-    const int lz = __clzll((long long)a);                       // >= 2; 64 for a = 0
-    const unsigned long long n = a << ((lz - 1) & 63);          // leading one at bit 62
-    const unsigned long long q = (n + 0x1ffull + ((n >> 10) & 1ull)) >> 10;   // 2^52 <= q <= 2^53
-    // biased exponent emax + 6 - lz; q's bit 52 (or a carry to 53) adds into the exponent field
-    const unsigned hi = (unsigned)(q >> 32) + ((unsigned)(emax + 5 - lz) << 20) +
-                        ((unsigned)s & 0x80000000u);
-    const long long bits = (long long)(((unsigned long long)hi << 32) | (unsigned)q);
-    return a ? __longlong_as_double(bits) : 0.0;
-}
-
-// L = S - 6U of a point from its seven fixed-point values.
-__device__ __forceinline__ long long xs_numerator(long long c, long long xm, long long xp, long long ym,
-                                                  long long yp, long long zm, long long zp)
-{
-    return ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;
-}
-
-// u' = fma(r, L 2^(emax - 1080), uc): DPCONV converts L on the FP64 pipe and
-// scales r instead (r2 = xs_r2(r, emax)); both round the same exact product.
-template <bool DPCONV>
-__device__ __forceinline__ double xs_apply(double uc, long long L, double r, double r2, int emax)
-{
-    if constexpr (DPCONV) return __fma_rn(r2, __ll2double_rn(L), uc);
-    return __fma_rn(r, xs_unfix(L, emax), uc);
 }
 
 // The whole update from seven doubles (kernels that convert per point).
@@ -258,12 +178,6 @@ __device__ __forceinline__ double xs_point(double c, double xm, double xp, doubl
     return xs_apply<false>(c, L, r, 0.0, emax);
 }
 
-// |u| of a result as the high word of its bit pattern (the exponent field and
-// the top of the mantissa): what the per-step maximum needs.
-__device__ __forceinline__ unsigned xs_abs_hi(double v)
-{
-    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
-}
 
 // V consecutive x points per thread, moved as one 16-byte vector.
 template <typename T>
