@@ -271,16 +271,16 @@ int cg_destroy(hs_cg_t c)
     int rc = HS_OK;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cg_destroy: stream synchronize");
-    cudaFree(c->r);
-    cudaFree(c->p);
-    cudaFree(c->q);
-    cudaFree(c->partials);
-    cudaFree(c->S);
-    if (c->S_host) cudaFreeHost(c->S_host);
-    for (void* o : c->owned) cudaFree(o);
-    if (c->mx) cg_mixed_release(c->mx);
-    cudaFree(c->bx_dev[0]);
-    cudaFree(c->bx_dev[1]);
+    dev_free(c->r, c->stream);
+    dev_free(c->p, c->stream);
+    dev_free(c->q, c->stream);
+    dev_free(c->partials, c->stream);
+    dev_free(c->S, c->stream);
+    delete c->S_host;
+    for (void* o : c->owned) dev_free(o, c->stream);
+    if (c->mx) cg_mixed_release(c->mx, c->stream);
+    dev_free(c->bx_dev[0], c->stream);
+    dev_free(c->bx_dev[1], c->stream);
     delete c;
     return rc;
 }
@@ -299,9 +299,9 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream)
     c->grid = grid_for(n);
 #define CG_ALLOC(ptr, bytes)                                                 \
     do {                                                                     \
-        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                \
+        cudaError_t e_ = dev_alloc((void**)&(ptr), (bytes), c->stream);     \
         if (e_ != cudaSuccess) {                                             \
-            rc = cuda_fail(e_, "cg_create: cudaMalloc");                     \
+            rc = cuda_fail(e_, "cg_create: device allocation");               \
             cg_destroy(c);                                                   \
             return rc;                                                       \
         }                                                                    \
@@ -311,14 +311,12 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream)
     CG_ALLOC(c->q, sizeof(double) * n);
     CG_ALLOC(c->partials, sizeof(double) * 2 * c->grid);
     CG_ALLOC(c->S, sizeof(CgScalars));
-    {
-        cudaError_t e = cudaMallocHost((void**)&c->S_host, sizeof(CgScalars));
-        if (e != cudaSuccess) {
-            c->S_host = nullptr;
-            rc = cuda_fail(e, "cg_create: cudaMallocHost");
-            cg_destroy(c);
-            return rc;
-        }
+    // the host mirror of the scalars: ordinary memory (pinned memory would
+    // cost a device-wide synchronisation to allocate and to free)
+    c->S_host = new (std::nothrow) CgScalars();
+    if (!c->S_host) {
+        cg_destroy(c);
+        return fail(HS_ENOMEM, "cg_create: host allocation failed");
     }
     if (A->kind == HS_OP_CSR && A->host) {
         const size_t bytes[3] = {sizeof(int32_t) * (size_t)(n + 1), sizeof(int32_t) * (size_t)A->nnz,
@@ -364,7 +362,8 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     double* x = (double*)x_inout;
     if (host_buffers) {
         for (int t = 0; t < 2; ++t)
-            if (!c->bx_dev[t]) HS_TRY_CUDA(cudaMalloc((void**)&c->bx_dev[t], vbytes), "cg_run: staging buffer");
+            if (!c->bx_dev[t])
+                HS_TRY_CUDA(dev_alloc((void**)&c->bx_dev[t], vbytes, c->stream), "cg_run: staging buffer");
         HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[0], b_in, vbytes, cudaMemcpyHostToDevice, c->stream),
                     "cg_run: copy of b");
         HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[1], x_inout, vbytes, cudaMemcpyHostToDevice, c->stream),

@@ -237,7 +237,7 @@ struct hs_cg_batch {
     SysDev* d_sys;
     void* arena;               // r, p, q, partials, scalars of all systems
     CgScalars* d_S;
-    CgScalars* h_S;            // pinned, n entries
+    CgScalars* h_S;            // host mirror of the scalars, n entries
 };
 
 extern "C" {
@@ -248,9 +248,9 @@ int cg_batch_destroy(hs_cg_batch_t b)
     int rc = HS_OK;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cg_batch_destroy: synchronize");
-    cudaFree(b->d_sys);
-    cudaFree(b->arena);
-    if (b->h_S) cudaFreeHost(b->h_S);
+    dev_free(b->d_sys, b->stream);
+    dev_free(b->arena, b->stream);
+    delete[] b->h_S;
     delete b;
     return rc;
 }
@@ -290,9 +290,12 @@ int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* strea
     }
     b->total_blocks = (int32_t)blocks;
     const size_t bytes = sizeof(double) * (size_t)(3 * vec_total + part_total) + sizeof(CgScalars) * (size_t)n;
-    cudaError_t e = cudaMalloc(&b->arena, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_sys, sizeof(SysDev) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_S, sizeof(CgScalars) * (size_t)n);
+    cudaError_t e = dev_alloc(&b->arena, bytes, b->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&b->d_sys, sizeof(SysDev) * (size_t)n, b->stream);
+    if (e == cudaSuccess) {
+        b->h_S = new (std::nothrow) CgScalars[(size_t)n]();
+        if (!b->h_S) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         const int rc = cuda_fail(e, "cg_batch_create: allocation");
         cg_batch_destroy(b);

@@ -348,7 +348,7 @@ struct hs_cg {
     double* q;
     double* partials;      // 2 * grid doubles
     hcg::CgScalars* S;     // device scalars
-    hcg::CgScalars* S_host;  // pinned mirror
+    hcg::CgScalars* S_host;  // host mirror of the scalars
     void* owned[3];        // device copies of host CSR arrays
     double* bx_dev[2];     // device staging of host b and x (allocated on demand)
     int64_t staged_n;
@@ -358,5 +358,5 @@ struct hs_cg {
 namespace hcg {
 int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, double rtol,
                  int32_t max_iter, hs_cg_info* info);
-void cg_mixed_release(CgMixed* m);
+void cg_mixed_release(CgMixed* m, cudaStream_t s);
 }  // namespace hcg

@@ -62,7 +62,7 @@ struct hcg::CgMixed {
     float* val32;        // CSR values in FP32 (owned), else NULL
     double* partials;    // 2 * grid
     MxScalars* S;
-    MxScalars* S_host;   // pinned
+    MxScalars* S_host;   // host mirror
     double inner_rtol;
     int32_t max_inner;
 };
@@ -262,17 +262,17 @@ __global__ void __launch_bounds__(kCgBlock)
         x[t] += (double)d[t];
 }
 
-void cg_mixed_release(CgMixed* m)
+void cg_mixed_release(CgMixed* m, cudaStream_t s)
 {
     if (!m) return;
-    cudaFree(m->d);
-    cudaFree(m->r);
-    cudaFree(m->p);
-    cudaFree(m->q);
-    cudaFree(m->val32);
-    cudaFree(m->partials);
-    cudaFree(m->S);
-    if (m->S_host) cudaFreeHost(m->S_host);
+    dev_free(m->d, s);
+    dev_free(m->r, s);
+    dev_free(m->p, s);
+    dev_free(m->q, s);
+    dev_free(m->val32, s);
+    dev_free(m->partials, s);
+    dev_free(m->S, s);
+    delete m->S_host;
     delete m;
 }
 
@@ -290,7 +290,8 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
     double* x = (double*)x_inout;
     if (host_buffers) {
         for (int t = 0; t < 2; ++t)
-            if (!c->bx_dev[t]) HS_TRY_CUDA(cudaMalloc((void**)&c->bx_dev[t], vbytes), "cg_run: staging buffer");
+            if (!c->bx_dev[t])
+                HS_TRY_CUDA(dev_alloc((void**)&c->bx_dev[t], vbytes, c->stream), "cg_run: staging buffer");
         HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[0], b_in, vbytes, cudaMemcpyHostToDevice, c->stream),
                     "cg_run: copy of b");
         HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[1], x_inout, vbytes, cudaMemcpyHostToDevice, c->stream),
@@ -419,19 +420,23 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
     const int64_t n = c->A.n;
     const int G = c->grid;
     cudaError_t e = cudaSuccess;
+    const cudaStream_t s = c->stream;
     for (float** v : {&m->d, &m->r, &m->p, &m->q})
-        if (e == cudaSuccess) e = cudaMalloc((void**)v, sizeof(float) * (size_t)n);
+        if (e == cudaSuccess) e = dev_alloc((void**)v, sizeof(float) * (size_t)n, s);
     // the FP64 residual and A x live in the context's FP64 r and q; its p is not needed
     m->r64 = c->r;
     m->q64 = c->q;
-    cudaFree(c->p);
+    dev_free(c->p, s);
     c->p = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&m->partials, sizeof(double) * 3 * (size_t)G);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&m->S, sizeof(MxScalars));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&m->S_host, sizeof(MxScalars));
+    if (e == cudaSuccess) e = dev_alloc((void**)&m->partials, sizeof(double) * 3 * (size_t)G, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&m->S, sizeof(MxScalars), s);
+    if (e == cudaSuccess) {
+        m->S_host = new (std::nothrow) MxScalars();
+        if (!m->S_host) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess && c->A.kind == HS_OP_CSR) {
         const int64_t nnz = c->A.rowptr ? A->nnz : 0;
-        e = cudaMalloc((void**)&m->val32, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+        e = dev_alloc((void**)&m->val32, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1), s);
         if (e == cudaSuccess && nnz > 0) {
             k_mx_to_f32<<<grid_for(nnz), kCgBlock, 0, c->stream>>>(nnz, c->A.val, m->val32);
             e = cudaPeekAtLastError();

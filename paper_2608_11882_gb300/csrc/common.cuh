@@ -43,6 +43,18 @@ namespace hcg {
 
 constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
+// Device memory of handles and contexts comes from the stream-ordered
+// allocator on the object's own stream: unlike cudaMalloc/cudaFree these calls
+// never synchronise the whole device, so creating or releasing one object does
+// not stall the work other streams have in flight (a server that opens and
+// closes requests while others run).  Memory freed this way returns to the pool
+// once the stream's earlier work is done.
+inline cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) { return cudaMallocAsync(p, bytes, s); }
+inline void dev_free(void* p, cudaStream_t s)
+{
+    if (p) (void)cudaFreeAsync(p, s);
+}
+
 // Sum of v over a block of BLOCK threads, in a fixed order (warp shuffles,
 // then warp 0 over the per-warp sums).  The result is valid in thread 0.
 // sh must hold BLOCK/32 doubles.

@@ -689,10 +689,10 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     if (h->flags & HS_SCHED_FULL) h->tdepth = 1;
     const size_t bytes = (size_t)h->g.total * h->elem;
     for (int b = 0; b < 2; ++b) {
-        cudaError_t e = cudaMalloc(&h->buf[b], bytes);
+        cudaError_t e = dev_alloc(&h->buf[b], bytes, h->stream);
         if (e != cudaSuccess) {
             h->buf[b] = nullptr;
-            rc = cuda_fail(e, "heat_create: cudaMalloc");
+            rc = cuda_fail(e, "heat_create: device allocation");
             heat_destroy(h);
             return rc;
         }
@@ -704,7 +704,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
         }
     }
     {
-        cudaError_t e = cudaMalloc((void**)&h->err, sizeof(int));
+        cudaError_t e = dev_alloc((void**)&h->err, sizeof(int), h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "heat_create: error word");
@@ -751,7 +751,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
         }
     }
     if (h->arith == A_FX64 || h->arith == A_F64_XS) {
-        cudaError_t e = cudaMalloc((void**)&h->fx, sizeof(FxState));
+        cudaError_t e = dev_alloc((void**)&h->fx, sizeof(FxState), h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "heat_create: fixed-point state");
@@ -761,8 +761,8 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     }
     if (h->flags & HS_VARKAPPA) {
         const size_t bytes = (size_t)h->g.total * h->elem;
-        cudaError_t e = cudaMalloc(&h->kap, bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&h->fdt, bytes);
+        cudaError_t e = dev_alloc(&h->kap, bytes, h->stream);
+        if (e == cudaSuccess) e = dev_alloc(&h->fdt, bytes, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->kap, 0, bytes, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->fdt, 0, bytes, h->stream);
         if (e != cudaSuccess) {
@@ -899,15 +899,20 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device)
     }
     int rc = copy_interior(h, src, nullptr, dst, kind);
     if (rc != HS_OK) return rc;
-    HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
+    // status reads on the handle's own stream (a legacy-stream copy would also
+    // wait for every other blocking stream, e.g. a batch running elsewhere)
     int err = 0;
-    HS_TRY_CUDA(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost), "heat_read: error word");
+    HS_TRY_CUDA(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+                "heat_read: error word");
+    HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
     if (err)
         return fail(HS_ETIMEOUT, "heat_read: a bounded wait inside the temporally blocked kernel "
                                  "ran out; the field is not valid");
     if (h->arith == A_FX64) {
         FxState st;
-        HS_TRY_CUDA(cudaMemcpy(&st, h->fx, sizeof(st), cudaMemcpyDeviceToHost), "heat_read: state");
+        HS_TRY_CUDA(cudaMemcpyAsync(&st, h->fx, sizeof(st), cudaMemcpyDeviceToHost, h->stream),
+                    "heat_read: state");
+        HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
         if (st.nonfinite)
             return fail(HS_ERANGE, "heat_read: the uploaded field held NaN or Inf, which the "
                                    "fixed-point form cannot carry");
@@ -937,12 +942,11 @@ int heat_destroy(hs_heat_t h)
         cudaError_t e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "heat_destroy: stream synchronize");
     }
-    for (int b = 0; b < 2; ++b)
-        if (h->buf[b]) cudaFree(h->buf[b]);
-    if (h->fx) cudaFree(h->fx);
-    if (h->err) cudaFree(h->err);
-    if (h->kap) cudaFree(h->kap);
-    if (h->fdt) cudaFree(h->fdt);
+    for (int b = 0; b < 2; ++b) dev_free(h->buf[b], h->stream);
+    dev_free(h->fx, h->stream);
+    dev_free(h->err, h->stream);
+    dev_free(h->kap, h->stream);
+    dev_free(h->fdt, h->stream);
     delete h;
     return rc;
 }

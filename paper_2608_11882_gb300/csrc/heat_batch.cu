@@ -189,7 +189,7 @@ int heat_batch_destroy(hs_batch_t b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture) cudaStreamDestroy(b->capture);
-    cudaFree(b->arena);
+    dev_free(b->arena, b->stream);
     delete b;
     return rc;
 }
@@ -268,10 +268,10 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
     const size_t s_lg = align(sizeof(int32_t) * (list_grid.size() ? list_grid.size() : 1));
     b->counter_bytes = align(sizeof(unsigned long long) * (1 + (size_t)n) + sizeof(int));
     const size_t total = s_grids + s_si + s_li + s_sl + s_lg + b->counter_bytes;
-    cudaError_t e = cudaMalloc(&b->arena, total);
+    cudaError_t e = dev_alloc(&b->arena, total, b->stream);
     if (e != cudaSuccess) {
         b->arena = nullptr;
-        const int rc = cuda_fail(e, "heat_batch_create: cudaMalloc");
+        const int rc = cuda_fail(e, "heat_batch_create: device allocation");
         heat_batch_destroy(b);
         return rc;
     }
@@ -282,15 +282,22 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
     int32_t* d_sl = (int32_t*)(base + s_grids + s_si + s_li);
     int32_t* d_lg = (int32_t*)(base + s_grids + s_si + s_li + s_sl);
     b->counters = base + s_grids + s_si + s_li + s_sl + s_lg;
-    // grids are re-uploaded at each run (cur changes); the schedule once
-    e = cudaMemcpy(d_si, step_item0.data(), sizeof(int64_t) * step_item0.size(), cudaMemcpyHostToDevice);
+    // grids are re-uploaded at each run (cur changes); the schedule once.  The
+    // arena is ordered on the batch stream, so the copies are too (and finish
+    // before the host arrays go away).
+    const cudaStream_t bs = b->stream;
+    e = cudaMemcpyAsync(d_si, step_item0.data(), sizeof(int64_t) * step_item0.size(), cudaMemcpyHostToDevice, bs);
     if (e == cudaSuccess && !list_item0.empty())
-        e = cudaMemcpy(d_li, list_item0.data(), sizeof(int64_t) * list_item0.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(d_li, list_item0.data(), sizeof(int64_t) * list_item0.size(), cudaMemcpyHostToDevice,
+                            bs);
     if (e == cudaSuccess)
-        e = cudaMemcpy(d_sl, step_list0.data(), sizeof(int32_t) * step_list0.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(d_sl, step_list0.data(), sizeof(int32_t) * step_list0.size(), cudaMemcpyHostToDevice,
+                            bs);
     if (e == cudaSuccess && !list_grid.empty())
-        e = cudaMemcpy(d_lg, list_grid.data(), sizeof(int32_t) * list_grid.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_grids, hg.data(), sizeof(BatchGrid) * hg.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(d_lg, list_grid.data(), sizeof(int32_t) * list_grid.size(), cudaMemcpyHostToDevice, bs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_grids, hg.data(), sizeof(BatchGrid) * hg.size(), cudaMemcpyHostToDevice, bs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
     if (e != cudaSuccess) {
         const int rc = cuda_fail(e, "heat_batch_create: schedule upload");
         heat_batch_destroy(b);
@@ -330,8 +337,9 @@ static int batch_enqueue(hs_batch* b)
 {
     const int n = (int)b->handles.size();
     std::vector<BatchGrid> hg((size_t)n);
-    HS_TRY_CUDA(cudaMemcpy(hg.data(), b->dev.grids, sizeof(BatchGrid) * n, cudaMemcpyDeviceToHost),
+    HS_TRY_CUDA(cudaMemcpyAsync(hg.data(), b->dev.grids, sizeof(BatchGrid) * n, cudaMemcpyDeviceToHost, b->stream),
                 "heat_batch_run: grid table");
+    HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_run: grid table");
     bool changed = false;
     for (int i = 0; i < n; ++i) {
         HeatBatchView v;
@@ -400,9 +408,10 @@ int heat_batch_run(hs_batch_t b, int use_graph)
 int heat_batch_wait(hs_batch_t b)
 {
     if (!b) return fail(HS_EINVAL, "heat_batch_wait: NULL batch");
-    HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_wait: synchronize");
     int err = 0;
-    HS_TRY_CUDA(cudaMemcpy(&err, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost), "heat_batch_wait: status");
+    HS_TRY_CUDA(cudaMemcpyAsync(&err, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+                "heat_batch_wait: status");
+    HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_wait: synchronize");
     if (err) return fail(HS_ETIMEOUT, "heat_batch_wait: a bounded wait in the batch kernel ran out");
     return HS_OK;
 }

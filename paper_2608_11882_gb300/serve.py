@@ -6,9 +6,12 @@ arrived, a slot is free and its device memory fits the free-HBM budget; the
 admitted request's field stays resident on the device until it completes.
 Every tick all admitted heat requests advance together by up to `quantum`
 steps in ONE batched persistent launch (heat_batch_*), so requests that arrive
-while others are running join the next tick's batch.  CG requests are solved
-on worker threads, each with its own CUDA stream, so they overlap on the
-device with the heat batches and with each other.  The per-point and
+while others are running join the next tick's batch.  A tick's batch runs
+while the host admits and uploads new requests and reads back those the
+previous tick finished (on a stream of their own), so host work overlaps the
+device work.  CG requests are solved on worker threads, each with its own CUDA
+stream, so they overlap on the device with the heat batches and with each
+other.  The per-point and
 per-iteration arithmetic is the library's, and a request's result does not
 depend on what it ran beside: heat equals heat_step alone and CG equals
 cg_run alone, bit for bit.
@@ -88,8 +91,9 @@ def percentile(values, q: float) -> float:
 
 
 class GpuBackend:
-    """The library on the current CUDA device: heat handles advanced by
-    heat_batch, CG contexts on per-worker streams."""
+    """The library on the current CUDA device: heat handles (uploads and reads
+    on an I/O stream) advanced by heat_batch on a batch stream, CG contexts on
+    per-worker streams."""
 
     def __init__(self, workers: int = 4):
         import torch
@@ -97,28 +101,47 @@ class GpuBackend:
         import paper_2608_11882_gb300 as pkg
         self.torch = torch
         self.pkg = pkg
-        self.stream = torch.cuda.Stream()
+        self.stream = torch.cuda.Stream()      # heat batches
+        self.io_stream = torch.cuda.Stream()   # heat handles: create, upload, read, release
         self.pool = ThreadPoolExecutor(max_workers=workers)
         self._local = threading.local()
+        self._stage = None   # pinned staging for read-backs, grown on demand
 
     def free_bytes(self) -> int:
         return int(self.torch.cuda.mem_get_info()[0])
 
     def heat_open(self, req: Request):
         nz, ny, nx = req.shape
-        h = self.pkg.Heat(nx, ny, nz, req.r, dtype=req.dtype, stream=self.stream, tdepth=1)
+        h = self.pkg.Heat(nx, ny, nz, req.r, dtype=req.dtype, stream=self.io_stream, tdepth=1)
+        # pageable memory: pinning a buffer of every request's own size costs more than it saves
         h.upload(np.ascontiguousarray(req.payload, dtype=h.np_dtype))
         return h
 
+    def heat_launch(self, handles, steps):
+        """Start one tick's batch (returns at once; heat_wait ends it)."""
+        b = self.pkg.HeatBatch(handles, steps, stream=self.stream)
+        b.run(use_graph=False)
+        return b
+
+    def heat_wait(self, b) -> None:
+        b.wait()
+        b.close()
+
     def heat_advance(self, handles, steps) -> None:
-        with self.pkg.HeatBatch(handles, steps, stream=self.stream) as b:
-            b.run(use_graph=False)
-            b.wait()
+        self.heat_wait(self.heat_launch(handles, steps))
 
     def heat_close(self, h):
-        out = h.read()
+        # the device-to-host copy into pinned staging is fast; the host copy
+        # into the result array follows (a pageable destination is far slower)
+        torch = self.torch
+        tdt = torch.float64 if h.np_dtype == np.float64 else torch.float32
+        nbytes = h.count * np.dtype(h.np_dtype).itemsize
+        if self._stage is None or self._stage.numel() < nbytes:
+            self._stage = torch.empty(max(nbytes, 1 << 26), dtype=torch.uint8, pin_memory=True)
+        view = self._stage[:nbytes].view(tdt)
+        h.read(view)
         h.close()
-        return out
+        return view.numpy().reshape(h.shape).copy()
 
     def _cg_job(self, req: Request):
         torch = self.torch
@@ -127,7 +150,8 @@ class GpuBackend:
             s = self._local.stream = torch.cuda.Stream()
         nz, ny, nx = req.shape
         with torch.cuda.stream(s):
-            b = torch.from_numpy(np.ascontiguousarray(req.payload, dtype=np.float64)).cuda(non_blocking=False)
+            b = torch.from_numpy(np.ascontiguousarray(req.payload, dtype=np.float64)).pin_memory()
+            b = b.cuda(non_blocking=True)
             with self.pkg.CG(self.pkg.Operator.stencil(nx, ny, nz), stream=s) as cg:
                 x, info = cg.run(b, rtol=req.rtol, max_iter=req.max_iter)
             out = x.cpu().numpy()
@@ -169,15 +193,26 @@ class Server:
             if device_bytes(q) > self.budget:
                 self.rejected.append(q.rid)
         pending = [q for q in pending if q.rid not in set(self.rejected)]
+        launch = getattr(self.backend, "heat_launch", None)
         t0 = self.clock()
         used = 0
         heat = {}          # rid -> [req, handle, remaining, admitted]
         cg = {}            # rid -> [req, future, admitted]
         results = {}
+        inflight = None    # (token, [(rid, steps)]) of the tick on the device
         i = 0
-        while i < len(pending) or heat or cg:
-            now = self.clock() - t0
+        while i < len(pending) or heat or cg or inflight is not None:
+            worked = False
+            # the tick in flight ends: its requests have advanced
+            if inflight is not None:
+                token, parts = inflight
+                self.backend.heat_wait(token)
+                for rid, st in parts:
+                    heat[rid][2] -= st
+                inflight = None
+                worked = True
             # admit everything that has arrived and fits
+            now = self.clock() - t0
             while i < len(pending) and pending[i].arrival <= now:
                 q = pending[i]
                 need = device_bytes(q)
@@ -191,21 +226,26 @@ class Server:
                 i += 1
             self.peak_bytes = max(self.peak_bytes, used)
             self.peak_slots = max(self.peak_slots, len(heat) + len(cg))
-            worked = False
-            if heat:
-                live = [v for v in heat.values() if v[2] > 0]
-                if live:
-                    steps = [min(self.quantum, v[2]) for v in live]
-                    self.backend.heat_advance([v[1] for v in live], steps)
-                    for v, s in zip(live, steps):
-                        v[2] -= s
-                    worked = True
-                now = self.clock() - t0
-                for rid in [r for r, v in heat.items() if v[2] == 0]:
-                    q, h, _, adm = heat.pop(rid)
-                    out = self.backend.heat_close(h)
-                    results[rid] = Result(rid, "heat", q.arrival, adm, self.clock() - t0, out)
-                    used -= device_bytes(q)
+            # start the next tick: every admitted heat request with steps left
+            live = [(rid, v) for rid, v in heat.items() if v[2] > 0]
+            if live:
+                steps = [min(self.quantum, v[2]) for _, v in live]
+                handles = [v[1] for _, v in live]
+                if launch is not None:
+                    inflight = (launch(handles, steps), [(rid, st) for (rid, _), st in zip(live, steps)])
+                else:
+                    self.backend.heat_advance(handles, steps)
+                    for (_, v), st in zip(live, steps):
+                        v[2] -= st
+                worked = True
+            # read back and release the finished heat requests (while the tick runs)
+            busy = {rid for rid, _ in inflight[1]} if inflight is not None else set()
+            for rid in [r for r, v in heat.items() if v[2] == 0 and r not in busy]:
+                q, h, _, adm = heat.pop(rid)
+                out = self.backend.heat_close(h)
+                results[rid] = Result(rid, "heat", q.arrival, adm, self.clock() - t0, out)
+                used -= device_bytes(q)
+                worked = True
             for rid in [r for r, v in cg.items() if v[1].done()]:
                 q, fut, adm = cg.pop(rid)
                 out, info = fut.result()

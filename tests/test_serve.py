@@ -107,3 +107,61 @@ def test_percentiles_and_summary():
     res = Server(FakeBackend(), quantum=8).run(reqs)
     s = summarize(res, reqs, 1.0)
     assert s["requests"] == 20 and s["latency_s"]["p99"] >= s["latency_s"]["p50"]
+
+
+class PipelinedBackend(FakeBackend):
+    """A tick starts at heat_launch and its steps land only at heat_wait, as on
+    the device; reading a handle that a running tick still advances is an error."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.running = None
+        self.launches = 0
+
+    def heat_launch(self, handles, steps):
+        assert self.running is None, "one tick at a time"
+        self.running = (handles, list(steps))
+        self.launches += 1
+        self.advances.append(([h["rid"] for h in handles], list(steps)))
+        return self.launches
+
+    def heat_wait(self, token):
+        assert self.running is not None and token == self.launches
+        for h, s in zip(*self.running):
+            h["done"] += s
+        self.running = None
+
+    def heat_close(self, h):
+        assert self.running is None or all(h is not x for x in self.running[0]), "read while in flight"
+        return super().heat_close(h)
+
+
+def test_pipelined_ticks_give_exact_steps_and_never_read_in_flight():
+    be = PipelinedBackend()
+    reqs = [heat(i, steps=s, arrival=0.0) for i, s in enumerate([1, 64, 65, 200, 0, 7, 130])]
+    res = Server(be, quantum=64).run(reqs)
+    assert [r.output for r in res] == [1, 64, 65, 200, 0, 7, 130]
+    assert be.running is None and not be.open
+    assert all(max(st) <= 64 for _, st in be.advances)
+
+
+def test_pipelined_late_arrivals_join():
+    t = {"now": 0.0}
+
+    def clock():
+        return t["now"]
+
+    def sleep(dt):
+        t["now"] += max(dt, 1e-4)
+
+    class Timed(PipelinedBackend):
+        def heat_wait(self, token):
+            super().heat_wait(token)
+            t["now"] += 0.005
+
+    be = Timed()
+    reqs = [heat(0, steps=2000, arrival=0.0), heat(1, steps=100, arrival=0.01)]
+    res = Server(be, quantum=64, clock=clock, sleep=sleep).run(reqs)
+    assert [r.output for r in res] == [2000, 100]
+    assert any(rids == [0, 1] for rids, _ in be.advances)
+    assert res[1].completed < res[0].completed
