@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(kCgBlock)
     }
 }
 
-// q = A p fused with p.q; the last block forms alpha = rho / p.q.
-template <int KIND>
+// q = A p fused with p.q; the last block forms alpha = rho / p.q.  MODE is
+// the operator's SpmvMode.
+template <int MODE>
 __global__ void __launch_bounds__(kCgBlock)
     k_cg_spmv_dot(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
                   CgScalars* S)
@@ -88,13 +89,12 @@ __global__ void __launch_bounds__(kCgBlock)
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
-    const int64_t row0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * kCgBlock;
-    if (KIND == HS_OP_STENCIL7) {
+    if (MODE == SP_STAGED) {
         pq = spmv_stencil_blocks(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
     } else {
-        for (int64_t row = row0; row < A.n; row += stride) {
-            const double qv = apply_row<KIND>(A, p, row);
+        for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
+             row += (int64_t)gridDim.x * kCgBlock) {
+            const double qv = MODE == SP_CSR ? apply_csr_row(A, p, row) : apply_stencil_row(A, p, row);
             q[row] = qv;
             pq = __fma_rn(__ldg(p + row), qv, pq);
         }
@@ -380,7 +380,8 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
                 "cg_run: scalar init");
     int rc = launch_apply(c->A, x, c->q, c->stream);   // q = A x0
     if (rc != HS_OK) return rc;
-    const int track = c->A.kind == HS_OP_STENCIL7;
+    const int mode = spmv_mode(c->A, c->grid);
+    const int track = mode == SP_STAGED;   // the staged SpMV needs p's largest exponent
     k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S, track);
     HS_CHECK_LAUNCH("cg: start kernel");
 
@@ -396,12 +397,16 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
         for (int32_t t = 0; t < todo; ++t) {
             // x lives either in the caller's buffer or in the staging buffer
             const int64_t nn = n;
-            if (c->A.kind == HS_OP_STENCIL7)
-                k_cg_spmv_dot<HS_OP_STENCIL7><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q,
-                                                                                   c->partials, c->S);
-            else
-                k_cg_spmv_dot<HS_OP_CSR><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q,
-                                                                              c->partials, c->S);
+            switch (mode) {
+            case SP_STAGED:
+                k_cg_spmv_dot<SP_STAGED><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+                break;
+            case SP_ROWS:
+                k_cg_spmv_dot<SP_ROWS><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+                break;
+            default:
+                k_cg_spmv_dot<SP_CSR><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+            }
             HS_CHECK_LAUNCH("cg: spmv+dot kernel");
             k_cg_update<<<c->grid, kCgBlock, 0, c->stream>>>(nn, x, c->r, c->p, c->q, c->partials, c->S);
             HS_CHECK_LAUNCH("cg: update kernel");

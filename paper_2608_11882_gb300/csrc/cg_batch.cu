@@ -29,7 +29,7 @@ struct SysDev {
     int32_t block0;     // first block of this system in the batch grid
     int32_t nblocks;
     int32_t max_iter;
-    int32_t pad;
+    int32_t mode;       // SpmvMode of the operator with this block count
 };
 
 // System of this block (binary search over block0) and the block's index in it.
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
     }
     const double rr_blk = block_sum<kCgBlock>(rr, sh);
     const double bb_blk = block_sum<kCgBlock>(bb, sh);
-    if (s.A.kind == HS_OP_STENCIL7) cg_fold_pmax(pm, s.S, 0, local == 0);
+    if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, 0, local == 0);
     if (threadIdx.x == 0) s.partials[s.nblocks + local] = bb_blk;
     if (!arrive_last_sys(rr_blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho = sum_partials_n(s.partials, s.nblocks, sh);
@@ -124,20 +124,23 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
     }
 }
 
+// One kernel per SpmvMode, so each has its own register budget; blocks of
+// the other modes' systems return at once.
+template <int MODE>
 __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, int nsys)
 {
     int local;
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
-    if (*(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
+    if (s.mode != MODE || *(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
     // as k_cg_spmv_dot: the same rows per thread and per-row arithmetic, so the same results
     const int64_t row0 = (int64_t)local * kCgBlock + threadIdx.x;
     const int64_t stride = (int64_t)s.nblocks * kCgBlock;
-    if (s.A.kind == HS_OP_STENCIL7) {
+    if (MODE == SP_STAGED) {
         pq = spmv_stencil_blocks(s.A, s.p, s.q, cg_pemax(s.S), local, s.nblocks);
     } else for (int64_t row = row0; row < s.A.n; row += stride) {
-        const double qv = apply_sys(s.A, s.p, row);
+        const double qv = MODE == SP_CSR ? apply_csr_row(s.A, s.p, row) : apply_stencil_row(s.A, s.p, row);
         s.q[row] = qv;
         pq = __fma_rn(__ldg(s.p + row), qv, pq);
     }
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int
         s.p[t] = v;
         pm = max(pm, xs_abs_hi(v));
     }
-    if (s.A.kind == HS_OP_STENCIL7) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
+    if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
 }
 
 // ||b - A x||^2 into rr_true (q = A x from k_cgb_apply_x).
@@ -232,6 +235,7 @@ struct hs_cg_batch {
     cudaStream_t stream;
     int32_t n;
     int32_t total_blocks;
+    bool has_mode[3];          // SpmvModes present (one SpMV kernel each)
     std::vector<SysDev> sys;   // host copy (b, x filled per run)
     std::vector<int64_t> rows;
     SysDev* d_sys;
@@ -278,6 +282,8 @@ int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* strea
         memset(&s, 0, sizeof(s));
         s.A = to_dev(&ops[i]);
         s.nblocks = grid_for(s.A.n);
+        s.mode = spmv_mode(s.A, s.nblocks);
+        b->has_mode[s.mode] = true;
         s.block0 = (int32_t)blocks;
         blocks += s.nblocks;
         b->rows[(size_t)i] = s.A.n;
@@ -363,7 +369,9 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
         if (all || enqueued >= max_iter) break;
         const int32_t todo = (max_iter - enqueued < chunk) ? max_iter - enqueued : chunk;
         for (int32_t t = 0; t < todo; ++t) {
-            CGB_LAUNCH(k_cgb_spmv_dot, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_STAGED]) CGB_LAUNCH(k_cgb_spmv_dot<SP_STAGED>, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_ROWS]) CGB_LAUNCH(k_cgb_spmv_dot<SP_ROWS>, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_CSR]) CGB_LAUNCH(k_cgb_spmv_dot<SP_CSR>, "cg batch: spmv+dot kernel");
             CGB_LAUNCH(k_cgb_update, "cg batch: update kernel");
             CGB_LAUNCH(k_cgb_pupdate, "cg batch: p update kernel");
         }

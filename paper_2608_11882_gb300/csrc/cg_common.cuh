@@ -313,6 +313,22 @@ __device__ __forceinline__ double spmv_stencil_blocks(const OpDev& A, const doub
     return pq;
 }
 
+// SpMV kernels, chosen per operator on the host: the matrix-free operator is
+// staged (exact-sum form) when its grid gives every block at least one (tile,
+// chunk) item of 4 or more planes, and runs row by row on the FP64 pipe
+// otherwise -- a rule of the operator and the block count only, so a batch
+// and a single solve pick the same kernel.  Separate kernels keep the staged
+// kernel's 64 registers from lowering the others' occupancy.
+enum SpmvMode { SP_ROWS = 0, SP_CSR = 1, SP_STAGED = 2 };
+
+__host__ __device__ inline int spmv_mode(const OpDev& A, int nblocks)
+{
+    if (A.kind == HS_OP_CSR) return SP_CSR;
+    const SpmvPlan P = spmv_plan(A, nblocks);
+    return P.tiles * (A.nz / 4) >= nblocks ? SP_STAGED : SP_ROWS;
+}
+
+
 // Folds a block's largest |p| high word (m, per thread) into S->pmax[slot] and,
 // from the system's first block, clears the slot after it.  All threads call it.
 __device__ __forceinline__ void cg_fold_pmax(unsigned m, CgScalars* S, int slot, bool first_block)
