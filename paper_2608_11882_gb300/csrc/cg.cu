@@ -123,14 +123,8 @@ __global__ void __launch_bounds__(kCgBlock)
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     const double alpha = S->alpha;
-    double rr = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * kCgBlock) {
-        x[t] = __fma_rn(alpha, p[t], x[t]);
-        const double rt = __fma_rn(-alpha, q[t], r[t]);
-        r[t] = rt;
-        rr = __fma_rn(rt, rt, rr);
-    }
+    const double rr = cg_update_rows(n, x, r, p, q, alpha, (int64_t)blockIdx.x * kCgBlock + threadIdx.x,
+                                     (int64_t)gridDim.x * kCgBlock);
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double rho_new = sum_partials(partials, gridDim.x, sh);
@@ -154,21 +148,10 @@ __global__ void __launch_bounds__(kCgBlock)
 {
     if (*(volatile int32_t*)&S->done) return;
     const double beta = S->beta;
-    if (!track_pmax) {
-        for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-             t += (int64_t)gridDim.x * kCgBlock)
-            p[t] = __fma_rn(beta, p[t], r[t]);
-        return;
-    }
-    unsigned pm = 0;
-    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * kCgBlock) {
-        const double v = __fma_rn(beta, p[t], r[t]);
-        p[t] = v;
-        pm = max(pm, xs_abs_hi(v));
-    }
+    const unsigned pm = cg_pupdate_rows(n, r, p, beta, (int64_t)blockIdx.x * kCgBlock + threadIdx.x,
+                                        (int64_t)gridDim.x * kCgBlock);
     // the update kernel has counted this iteration: p is the next one's direction
-    cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
+    if (track_pmax) cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
 }
 
 // ||b - q||^2 into S->rr_true (q = A x).

@@ -165,14 +165,8 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_update(const SysDev* sys, int 
     if (*(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
     __shared__ double sh[kCgBlock / 32];
     const double alpha = s.S->alpha;
-    double rr = 0.0;
-    for (int64_t t = (int64_t)local * kCgBlock + threadIdx.x; t < s.A.n;
-         t += (int64_t)s.nblocks * kCgBlock) {
-        s.x[t] = __fma_rn(alpha, s.p[t], s.x[t]);
-        const double rt = __fma_rn(-alpha, s.q[t], s.r[t]);
-        s.r[t] = rt;
-        rr = __fma_rn(rt, rt, rr);
-    }
+    const double rr = cg_update_rows(s.A.n, s.x, s.r, s.p, s.q, alpha, (int64_t)local * kCgBlock + threadIdx.x,
+                                     (int64_t)s.nblocks * kCgBlock);
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho_new = sum_partials_n(s.partials, s.nblocks, sh);
@@ -196,13 +190,8 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int
     // the update kernel of this iteration has already counted it
     if (*(volatile int32_t*)&s.S->done) return;
     const double beta = s.S->beta;
-    unsigned pm = 0;
-    for (int64_t t = (int64_t)local * kCgBlock + threadIdx.x; t < s.A.n;
-         t += (int64_t)s.nblocks * kCgBlock) {
-        const double v = __fma_rn(beta, s.p[t], s.r[t]);
-        s.p[t] = v;
-        pm = max(pm, xs_abs_hi(v));
-    }
+    const unsigned pm = cg_pupdate_rows(s.A.n, s.r, s.p, beta, (int64_t)local * kCgBlock + threadIdx.x,
+                                        (int64_t)s.nblocks * kCgBlock);
     if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
 }
 

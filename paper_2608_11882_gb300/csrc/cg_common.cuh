@@ -329,6 +329,73 @@ __host__ __device__ inline int spmv_mode(const OpDev& A, int nblocks)
 }
 
 
+// ---- the vector updates of a CG iteration, shared by single and batched CG -----------
+// A system's rows are taken as pairs of consecutive values by threads t0,
+// t0 + stride, ...; the odd last value by thread t0 == 0.  The solver's own
+// vectors start 16-byte aligned and move as 16-byte vectors; the caller's x
+// does too when it is aligned, value by value otherwise (same pairs, same
+// order).  The per-value arithmetic is the textbook one; single and batched CG
+// use these with the same partition, so their dot products add in the same
+// order.
+
+// x += alpha p, r -= alpha q; returns this thread's share of r.r.
+__device__ __forceinline__ double cg_update_rows(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                 const double* __restrict__ p, const double* __restrict__ q,
+                                                 double alpha, int64_t t0, int64_t stride)
+{
+    double rr = 0.0;
+    const int64_t npairs = n >> 1;
+    const bool xvec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    for (int64_t t = t0; t < npairs; t += stride) {
+        const double2 pv = reinterpret_cast<const double2*>(p)[t];
+        const double2 qv = reinterpret_cast<const double2*>(q)[t];
+        double2 xv = xvec ? reinterpret_cast<double2*>(x)[t] : make_double2(x[2 * t], x[2 * t + 1]);
+        double2 rv = reinterpret_cast<double2*>(r)[t];
+        xv.x = __fma_rn(alpha, pv.x, xv.x);
+        xv.y = __fma_rn(alpha, pv.y, xv.y);
+        rv.x = __fma_rn(-alpha, qv.x, rv.x);
+        rv.y = __fma_rn(-alpha, qv.y, rv.y);
+        if (xvec) {
+            reinterpret_cast<double2*>(x)[t] = xv;
+        } else {
+            x[2 * t] = xv.x;
+            x[2 * t + 1] = xv.y;
+        }
+        reinterpret_cast<double2*>(r)[t] = rv;
+        rr = __fma_rn(rv.x, rv.x, rr);
+        rr = __fma_rn(rv.y, rv.y, rr);
+    }
+    if ((n & 1) && t0 == 0) {
+        x[n - 1] = __fma_rn(alpha, p[n - 1], x[n - 1]);
+        const double rt = __fma_rn(-alpha, q[n - 1], r[n - 1]);
+        r[n - 1] = rt;
+        rr = __fma_rn(rt, rt, rr);
+    }
+    return rr;
+}
+
+// p = r + beta p; returns the largest |p| high word of this thread's values.
+__device__ __forceinline__ unsigned cg_pupdate_rows(int64_t n, const double* __restrict__ r,
+                                                    double* __restrict__ p, double beta, int64_t t0,
+                                                    int64_t stride)
+{
+    unsigned pm = 0;
+    const int64_t npairs = n >> 1;
+    for (int64_t t = t0; t < npairs; t += stride) {
+        const double2 a = reinterpret_cast<const double2*>(p)[t];
+        const double2 b = reinterpret_cast<const double2*>(r)[t];
+        const double2 v = make_double2(__fma_rn(beta, a.x, b.x), __fma_rn(beta, a.y, b.y));
+        reinterpret_cast<double2*>(p)[t] = v;
+        pm = max(pm, max(xs_abs_hi(v.x), xs_abs_hi(v.y)));
+    }
+    if ((n & 1) && t0 == 0) {
+        const double v = __fma_rn(beta, p[n - 1], r[n - 1]);
+        p[n - 1] = v;
+        pm = max(pm, xs_abs_hi(v));
+    }
+    return pm;
+}
+
 // Folds a block's largest |p| high word (m, per thread) into S->pmax[slot] and,
 // from the system's first block, clears the slot after it.  All threads call it.
 __device__ __forceinline__ void cg_fold_pmax(unsigned m, CgScalars* S, int slot, bool first_block)
