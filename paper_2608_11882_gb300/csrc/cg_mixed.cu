@@ -87,14 +87,10 @@ struct Acc32 {
 };
 
 __device__ __forceinline__ float apply32_stencil(const OpDev32& A, const float* __restrict__ p,
-                                                 int64_t row)
+                                                 int64_t row, int i, int j, int k)
 {
     const int nx = A.nx, ny = A.ny;
     const int64_t sxy = (int64_t)nx * ny;
-    const int i = (int)(row % nx);
-    const int64_t jk = row / nx;
-    const int j = (int)(jk % ny);
-    const int k = (int)(jk / ny);
     const float zm = k > 0 ? __ldg(p + row - sxy) : 0.0f;
     const float ym = j > 0 ? __ldg(p + row - nx) : 0.0f;
     const float xm = i > 0 ? __ldg(p + row - 1) : 0.0f;
@@ -114,12 +110,6 @@ __device__ __forceinline__ float apply32_csr(const OpDev32& A, const float* __re
     return s;
 }
 
-template <int KIND>
-__device__ __forceinline__ float apply32(const OpDev32& A, const float* __restrict__ p, int64_t row)
-{
-    if (KIND == HS_OP_STENCIL7) return apply32_stencil(A, p, row);
-    return apply32_csr(A, p, row);
-}
 
 __global__ void __launch_bounds__(kCgBlock)
     k_mx_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst)
@@ -194,11 +184,23 @@ __global__ void __launch_bounds__(kCgBlock)
     if (*(volatile int32_t*)&S->inner_done) return;
     __shared__ double sh[kCgBlock / 32];
     Acc32 pq;
-    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
-         row += (int64_t)gridDim.x * kCgBlock) {
-        const float qv = apply32<KIND>(A, p, row);
-        q[row] = qv;
-        pq.add(__ldg(p + row), qv);
+    const int64_t row0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * kCgBlock;
+    if (KIND == HS_OP_STENCIL7) {
+        if (row0 < A.n) {
+            RowWalk w(A, row0, stride);   // coordinates stepped, not divided out
+            for (int64_t row = row0; row < A.n; row += stride, w.next(A)) {
+                const float qv = apply32_stencil(A, p, row, w.i, w.j, w.k);
+                q[row] = qv;
+                pq.add(__ldg(p + row), qv);
+            }
+        }
+    } else {
+        for (int64_t row = row0; row < A.n; row += stride) {
+            const float qv = apply32_csr(A, p, row);
+            q[row] = qv;
+            pq.add(__ldg(p + row), qv);
+        }
     }
     const double blk = block_sum<kCgBlock>(pq.total(), sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
@@ -221,13 +223,37 @@ __global__ void __launch_bounds__(kCgBlock)
     __shared__ double sh[kCgBlock / 32];
     const float alpha = (float)S->alpha;
     Acc32 rr;
-    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * kCgBlock) {
-        d[t] = __fmaf_rn(alpha, p[t], d[t]);
-        const float rt = __fmaf_rn(-alpha, q[t], r[t]);
-        r[t] = rt;
-        rr.add(rt, rt);
+    // groups of four values as 16-byte vectors (the FP32 vectors start aligned),
+    // the last n % 4 values by thread 0
+    const int64_t t0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x, stride = (int64_t)gridDim.x * kCgBlock;
+    const int64_t n4 = n >> 2;
+    for (int64_t t = t0; t < n4; t += stride) {
+        const float4 pv = reinterpret_cast<const float4*>(p)[t];
+        const float4 qv = reinterpret_cast<const float4*>(q)[t];
+        float4 dv = reinterpret_cast<float4*>(d)[t];
+        float4 rv = reinterpret_cast<float4*>(r)[t];
+        dv.x = __fmaf_rn(alpha, pv.x, dv.x);
+        dv.y = __fmaf_rn(alpha, pv.y, dv.y);
+        dv.z = __fmaf_rn(alpha, pv.z, dv.z);
+        dv.w = __fmaf_rn(alpha, pv.w, dv.w);
+        rv.x = __fmaf_rn(-alpha, qv.x, rv.x);
+        rv.y = __fmaf_rn(-alpha, qv.y, rv.y);
+        rv.z = __fmaf_rn(-alpha, qv.z, rv.z);
+        rv.w = __fmaf_rn(-alpha, qv.w, rv.w);
+        reinterpret_cast<float4*>(d)[t] = dv;
+        reinterpret_cast<float4*>(r)[t] = rv;
+        rr.add(rv.x, rv.x);
+        rr.add(rv.y, rv.y);
+        rr.add(rv.z, rv.z);
+        rr.add(rv.w, rv.w);
     }
+    if (t0 == 0)
+        for (int64_t t = n4 << 2; t < n; ++t) {
+            d[t] = __fmaf_rn(alpha, p[t], d[t]);
+            const float rt = __fmaf_rn(-alpha, q[t], r[t]);
+            r[t] = rt;
+            rr.add(rt, rt);
+        }
     const double blk = block_sum<kCgBlock>(rr.total(), sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double rho_new = sum_partials(partials, gridDim.x, sh);
@@ -248,9 +274,19 @@ __global__ void __launch_bounds__(kCgBlock)
 {
     if (*(volatile int32_t*)&S->inner_done) return;
     const float beta = (float)S->beta;
-    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * kCgBlock)
-        p[t] = __fmaf_rn(beta, p[t], r[t]);
+    const int64_t t0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x, stride = (int64_t)gridDim.x * kCgBlock;
+    const int64_t n4 = n >> 2;
+    for (int64_t t = t0; t < n4; t += stride) {
+        const float4 rv = reinterpret_cast<const float4*>(r)[t];
+        float4 pv = reinterpret_cast<float4*>(p)[t];
+        pv.x = __fmaf_rn(beta, pv.x, rv.x);
+        pv.y = __fmaf_rn(beta, pv.y, rv.y);
+        pv.z = __fmaf_rn(beta, pv.z, rv.z);
+        pv.w = __fmaf_rn(beta, pv.w, rv.w);
+        reinterpret_cast<float4*>(p)[t] = pv;
+    }
+    if (t0 == 0)
+        for (int64_t t = n4 << 2; t < n; ++t) p[t] = __fmaf_rn(beta, p[t], r[t]);
 }
 
 // x += d in FP64.
