@@ -329,38 +329,6 @@ __host__ __device__ inline int spmv_mode(const OpDev& A, int nblocks)
 }
 
 
-// Grid coordinates (i, j, k) of a thread's rows in a grid-stride loop over a
-// matrix-free operator's rows (any struct with nx, ny, nz), stepped with
-// carries instead of divided out: the stride's own coordinates are added and
-// wrapped once per axis.
-struct RowWalk {
-    int i, j, k;
-    int di, dj;
-    int64_t dk;
-    template <typename Op>
-    __device__ __forceinline__ RowWalk(const Op& A, int64_t row, int64_t stride)
-    {
-        const int64_t sxy = (int64_t)A.nx * A.ny;
-        i = (int)(row % A.nx);
-        j = (int)((row / A.nx) % A.ny);
-        k = (int)(row / sxy);
-        di = (int)(stride % A.nx);
-        dj = (int)((stride / A.nx) % A.ny);
-        dk = stride / sxy;
-    }
-    template <typename Op>
-    __device__ __forceinline__ void next(const Op& A)
-    {
-        i += di;
-        int c = i >= A.nx;
-        if (c) i -= A.nx;
-        j += dj + c;
-        c = j >= A.ny;
-        if (c) j -= A.ny;
-        k = (int)min((int64_t)k + dk + c, (int64_t)INT32_MAX);   // past the last plane ends the loop anyway
-    }
-};
-
 // ---- the vector updates of a CG iteration, shared by single and batched CG -----------
 // A system's rows are taken as pairs of consecutive values by threads t0,
 // t0 + stride, ...; the odd last value by thread t0 == 0.  The solver's own

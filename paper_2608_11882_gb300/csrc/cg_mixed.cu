@@ -86,21 +86,6 @@ struct Acc32 {
     __device__ __forceinline__ double total() const { return hi + (double)lo; }
 };
 
-__device__ __forceinline__ float apply32_stencil(const OpDev32& A, const float* __restrict__ p,
-                                                 int64_t row, int i, int j, int k)
-{
-    const int nx = A.nx, ny = A.ny;
-    const int64_t sxy = (int64_t)nx * ny;
-    const float zm = k > 0 ? __ldg(p + row - sxy) : 0.0f;
-    const float ym = j > 0 ? __ldg(p + row - nx) : 0.0f;
-    const float xm = i > 0 ? __ldg(p + row - 1) : 0.0f;
-    const float xp = i < nx - 1 ? __ldg(p + row + 1) : 0.0f;
-    const float yp = j < ny - 1 ? __ldg(p + row + nx) : 0.0f;
-    const float zp = k < A.nz - 1 ? __ldg(p + row + sxy) : 0.0f;
-    const float s = ((zm + ym) + (xm + xp)) + (yp + zp);
-    return __fmaf_rn(6.0f, __ldg(p + row), -s);
-}
-
 __device__ __forceinline__ float apply32_csr(const OpDev32& A, const float* __restrict__ p, int64_t row)
 {
     float s = 0.0f;
@@ -187,12 +172,40 @@ __global__ void __launch_bounds__(kCgBlock)
     const int64_t row0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * kCgBlock;
     if (KIND == HS_OP_STENCIL7) {
-        if (row0 < A.n) {
-            RowWalk w(A, row0, stride);   // coordinates stepped, not divided out
-            for (int64_t row = row0; row < A.n; row += stride, w.next(A)) {
-                const float qv = apply32_stencil(A, p, row, w.i, w.j, w.k);
-                q[row] = qv;
-                pq.add(__ldg(p + row), qv);
+        // (tile of 32 x 8 columns, chunk of z-planes) items taken by the blocks
+        // in a fixed order; a thread marches up its column with the values at
+        // k-1, k, k+1 in registers, the in-plane neighbours through L1
+        const int nx = A.nx, ny = A.ny, nz = A.nz;
+        const int64_t sxy = (int64_t)nx * ny;
+        const int tiles_x = (nx + 31) / 32;
+        const int64_t tiles = (int64_t)tiles_x * ((ny + 7) / 8);
+        int64_t chunks = (2 * (int64_t)gridDim.x + tiles - 1) / tiles;
+        const int64_t maxc = nz / 4 > 1 ? nz / 4 : 1;
+        if (chunks > maxc) chunks = maxc;
+        const int kc = (int)((nz + chunks - 1) / chunks);
+        chunks = (nz + kc - 1) / kc;
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        for (int64_t item = blockIdx.x; item < tiles * chunks; item += gridDim.x) {
+            const int64_t tile = item % tiles;
+            const int i = (int)(tile % tiles_x) * 32 + tx, j = (int)(tile / tiles_x) * 8 + ty;
+            const int kb = (int)(item / tiles) * kc, ke = min(kb + kc, nz);
+            if (i >= nx || j >= ny) continue;
+            int64_t c = (int64_t)kb * sxy + (int64_t)j * nx + i;
+            float below = kb > 0 ? __ldg(p + c - sxy) : 0.0f;
+            float cur = __ldg(p + c);
+            for (int k = kb; k < ke; ++k) {
+                const float above = k < nz - 1 ? __ldg(p + c + sxy) : 0.0f;
+                const float ym = j > 0 ? __ldg(p + c - nx) : 0.0f;
+                const float xm = i > 0 ? __ldg(p + c - 1) : 0.0f;
+                const float xp = i < nx - 1 ? __ldg(p + c + 1) : 0.0f;
+                const float yp = j < ny - 1 ? __ldg(p + c + nx) : 0.0f;
+                const float sum = ((below + ym) + (xm + xp)) + (yp + above);
+                const float qv = __fmaf_rn(6.0f, cur, -sum);
+                q[c] = qv;
+                pq.add(cur, qv);
+                below = cur;
+                cur = above;
+                c += sxy;
             }
         }
     } else {
