@@ -39,6 +39,7 @@ FP64_INSTR_PEAK_T = 0.625
 
 # heat arithmetic modes: Heat() keywords, the arithmetic type, algorithmic bytes per LUP,
 # and the roof that binds the Interior kernel
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (the measured copy rate is the roofline peak)
 HEAT_MODES = {
     # plain FP64 handle: FP64 fields, exact int64 neighbour sum, one FP64 FMA per point
     "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "hbm",
@@ -275,6 +276,7 @@ def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind, tdepth=1):
                 "hbm_peak_kind": peak_kind, "interior_ms_per_launch": int_ms}
     return {"bound": "hbm", "kernel": name, "achieved": hbm_rate, "peak": hbm_gbs, "unit": "GB/s",
             "frac": hbm_rate / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
+            "frac_of_nominal": hbm_rate / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
             "bytes_per_lup": spec["bytes"], "steps_per_launch": tdepth,
             "effective_gbs": hbm_rate * tdepth, "interior_ms_per_launch": int_ms}
 
@@ -296,6 +298,7 @@ def cpu_baseline(args, threads):
     steps = int(max(2, min(200, 12.0 / max(t1, 1e-3))))
     _, secs = oracle.heat_run(u0, args.r, steps, threads=threads, return_seconds=True)
     glups = n ** 3 * steps / secs / 1e9
+    _, secs1 = oracle.heat_run(u0, args.r, 2, threads=1, return_seconds=True)   # one core, two steps
     m = args.cg_n
     b = cg_rhs(m ** 3, seed=SEED)
     cg_iters = 20
@@ -303,7 +306,8 @@ def cpu_baseline(args, threads):
     return {"value": glups, "unit": "GLUP/s", "cores": threads, "kind": "oracle",
             "sample": f"heat {n}^3 FP64 r={args.r}, {steps} of {args.heat_steps} steps, timed step "
                       f"loop only; CG matrix-free {m}^3, {cg_iters} iterations",
-            "cg_matrix_free_its_per_s": cg_iters / info["loop_seconds"]}
+            "cg_matrix_free_its_per_s": cg_iters / info["loop_seconds"],
+            "single_core_glups": n ** 3 * 2 / secs1 / 1e9}
 
 
 def run_reference(args):
@@ -508,6 +512,8 @@ def run_ours(args):
                        "ms_per_solve": statistics.median(seg["cg_csr"]),
                        "relres_true": infos[-1][1]["relres_true"]}},
         "latency_ms": {k: {"p50": pct(v, 0.5), "p99": pct(v, 0.99)} for k, v in seg.items()},
+        # (max - min) / median of each segment over the timed steps
+        "variability": {k: (max(v) - min(v)) / statistics.median(v) for k, v in seg.items()},
         "roofline": roofline,
         "clocks": clock_info,
         "gpu_launches": launches,
@@ -709,16 +715,19 @@ def run_serving(args):
 
     from paper_2608_11882_gb300.build import build
     build()
-    from paper_2608_11882_gb300.serve import GpuBackend, Server, poisson_trace, summarize
+    from paper_2608_11882_gb300.serve import GpuBackend, Server, poisson_trace, predict_seconds, summarize
 
     base = poisson_trace(args.requests, rate=1.0, seed=SEED)   # arrivals for rate 1, rescaled below
     unit = [q.arrival for q in base]
+    cal = GpuBackend(workers=1)
+    kbars = cal.calibrate()   # the paper's k-bar model, fitted on this GPU (heat_step alone)
+    cal.close()
 
     def serve(scale):
         for q, a in zip(base, unit):
             q.arrival = a * scale
         be = GpuBackend(workers=4)
-        srv = Server(be, quantum=64, max_slots=32)
+        srv = Server(be, quantum=64, max_slots=32, kbars=kbars)
         res = srv.run(base)
         be.close()
         out = summarize(res, base, srv.makespan)
@@ -731,7 +740,9 @@ def run_serving(args):
     line = {"workload": f"serving: {args.requests} Poisson-arrival requests (heat 75% / CG 25%), "
                         "edges log-uniform [32, 384], steps log-uniform [10, 2000], FP32/FP64 50/50, "
                         "CG rtol 1e-8", "seed": SEED,
-            "closed_loop": closed, "capacity_req_per_s": capacity, "loads": {}}
+            "closed_loop": closed, "capacity_req_per_s": capacity, "loads": {},
+            "kbar_s_per_point_step": kbars,
+            "predicted_heat_device_s": sum(predict_seconds(q, kbars) for q in base if q.kind == "heat")}
     for load in (0.5, 0.7, 0.9):
         line["loads"][str(load)] = serve(1.0 / (load * capacity))
     torch.cuda.synchronize()

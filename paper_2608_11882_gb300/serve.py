@@ -81,6 +81,26 @@ def device_bytes(req: Request) -> int:
     return 5 * 8 * req.points
 
 
+def kbar(samples) -> float:
+    """The paper's per-point cost model (Section 5.6): one step costs
+    t_step = k (N-2)^3 for (N-2)^3 computed points, so each grid size gives
+    k = T_total / (n_steps (N-2)^3), and k-bar is the plain mean of k over the
+    sizes measured.  samples: (points, steps, seconds) per grid size, points =
+    the interior points (N-2)^3.  (The paper's printed rearrangement multiplies
+    by (N-2)^3 where the division is meant.)"""
+    ks = [t / (steps * pts) for pts, steps, t in samples]
+    if not ks:
+        raise ValueError("kbar needs at least one sample")
+    return sum(ks) / len(ks)
+
+
+def predict_seconds(req: Request, kbars: dict) -> float:
+    """Standalone device time of a heat request by the k-bar model of its
+    arithmetic: k-bar * points * steps (nan when no k-bar is known)."""
+    k = kbars.get(req.dtype) if kbars else None
+    return float(k) * req.points * req.steps if (k and req.kind == "heat") else float("nan")
+
+
 def percentile(values, q: float) -> float:
     """Nearest-rank percentile (q in [0, 100])."""
     if not values:
@@ -109,6 +129,26 @@ class GpuBackend:
 
     def free_bytes(self) -> int:
         return int(self.torch.cuda.mem_get_info()[0])
+
+    def calibrate(self, edges=(96, 160, 256), steps=40) -> dict:
+        """k-bar per arithmetic from heat_step alone on this device (CUDA events
+        around `steps` steps of an edge^3 grid, one warm-up pass each)."""
+        torch = self.torch
+        out = {}
+        for dt in ("f64", "f32"):
+            samples = []
+            for n in edges:
+                with self.pkg.Heat(n, n, n, 0.1, dtype=dt, stream=self.stream, tdepth=1) as h:
+                    h.upload(np.random.default_rng(n).uniform(-1, 1, (n, n, n)).astype(h.np_dtype))
+                    h.step(4)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(self.stream)
+                    h.step(steps)
+                    e1.record(self.stream)
+                    e1.synchronize()
+                    samples.append((n ** 3, steps, e0.elapsed_time(e1) * 1e-3))
+            out[dt] = kbar(samples)
+        return out
 
     def heat_open(self, req: Request):
         nz, ny, nx = req.shape
@@ -174,8 +214,11 @@ class Server:
 
     def __init__(self, backend, hbm_budget: int | None = None, reserve: int = 2 << 30,
                  max_slots: int = 32, quantum: int = 64, clock=time.perf_counter,
-                 sleep=time.sleep):
+                 sleep=time.sleep, kbars: dict | None = None):
+        """kbars: k-bar per arithmetic (GpuBackend.calibrate); each heat result
+        then carries its predicted standalone device time in info["predicted_s"]."""
         self.backend = backend
+        self.kbars = kbars or {}
         self.budget = hbm_budget if hbm_budget is not None else max(0, backend.free_bytes() - reserve)
         self.max_slots = max_slots
         self.quantum = quantum
@@ -243,7 +286,8 @@ class Server:
             for rid in [r for r, v in heat.items() if v[2] == 0 and r not in busy]:
                 q, h, _, adm = heat.pop(rid)
                 out = self.backend.heat_close(h)
-                results[rid] = Result(rid, "heat", q.arrival, adm, self.clock() - t0, out)
+                results[rid] = Result(rid, "heat", q.arrival, adm, self.clock() - t0, out,
+                                      {"predicted_s": predict_seconds(q, self.kbars)})
                 used -= device_bytes(q)
                 worked = True
             for rid in [r for r, v in cg.items() if v[1].done()]:

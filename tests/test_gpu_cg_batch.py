@@ -69,3 +69,24 @@ def test_batch_workload_64_solves(pkg):
         shape, op, b = sy[k]
         r = b - oracle.lap7_apply(xs[k].cpu().numpy().reshape(shape)).reshape(-1)
         assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(b)
+
+
+def test_batch_with_staged_system_equals_single_bitwise(pkg):
+    """A batch that holds a grid large enough for the staged exact-sum SpMV
+    (176^3, one item of 4+ planes per block), a small matrix-free grid (row
+    kernel) and a CSR system: each equals its own cg_run bit for bit."""
+    big = (176, 176, 176)
+    ops = [(big, pkg.Operator.stencil(*big[::-1]), cg_rhs(176 ** 3, seed=91)),
+           ((20, 24, 28), pkg.Operator.stencil(28, 24, 20), cg_rhs(20 * 24 * 28, seed=92))]
+    arrs = [dev(a) for a in lap7_csr(30, 22, 18)]
+    ops.append(((18, 22, 30), pkg.Operator.csr(*arrs), cg_rhs(18 * 22 * 30, seed=93)))
+    with pkg.CGBatch([o[1] for o in ops]) as cb:
+        xs, infos = cb.run([dev(o[2]) for o in ops], rtol=1e-8, max_iter=5000)
+    for (shape, op, b), x, info in zip(ops, xs, infos):
+        with pkg.CG(op) as cg:
+            x1, i1 = cg.run(dev(b), rtol=1e-8, max_iter=5000)
+        assert info["iters"] == i1["iters"] and info["converged"]
+        assert np.array_equal(x.cpu().numpy(), x1.cpu().numpy())
+    shape, _, b = ops[0]
+    r = b - oracle.lap7_apply(xs[0].cpu().numpy().reshape(shape), threads=oracle.max_threads()).reshape(-1)
+    assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(b)

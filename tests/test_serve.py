@@ -165,3 +165,21 @@ def test_pipelined_late_arrivals_join():
     assert [r.output for r in res] == [2000, 100]
     assert any(rids == [0, 1] for rids, _ in be.advances)
     assert res[1].completed < res[0].completed
+
+
+def test_kbar_follows_the_papers_model():
+    """t_step = k (N-2)^3: timings generated from known k per size give back
+    their mean; the prediction scales with points and steps."""
+    from paper_2608_11882_gb300.serve import kbar, predict_seconds
+    ks = {64: 2e-12, 128: 3e-12, 256: 4e-12}
+    samples = [(n ** 3, 50, 50 * k * n ** 3) for n, k in ks.items()]
+    assert abs(kbar(samples) - 3e-12) < 1e-24
+    q = heat(0, shape=(10, 20, 30), steps=7)
+    assert abs(predict_seconds(q, {"f64": 3e-12}) - 3e-12 * 6000 * 7) < 1e-20
+    assert predict_seconds(q, {}) != predict_seconds(q, {})   # nan without a model
+
+
+def test_results_carry_predictions():
+    reqs = [heat(0, steps=10), heat(1, steps=0)]
+    res = Server(FakeBackend(), quantum=8, kbars={"f64": 1e-12}).run(reqs)
+    assert abs(res[0].info["predicted_s"] - 1e-12 * 512 * 10) < 1e-20
