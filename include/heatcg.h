@@ -276,6 +276,9 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
  * 24 2^-57 max|p| plus one rounding, where FP64 arithmetic rounds about seven
  * times; a p whose exponents fall outside the convertible range (see
  * HS_FP64_PIPE) takes FP64 arithmetic.  op_apply always computes in FP64.
+ * On grids large enough for the shared-memory-staged SpMV, an even nx lets
+ * the kernel stage p by TMA (same results bit for bit; a bounded wait in it
+ * that runs out stops the solve with HS_ETIMEOUT).
  * Synchronises the stream.  Returns HS_OK when converged, HS_ENOCONV when
  * max_iter iterations ran without reaching rtol (x and info are still
  * filled), or an error code.  info may be NULL. */

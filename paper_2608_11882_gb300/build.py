@@ -18,9 +18,9 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libheatcg.so"
 SOURCES = ["api.cu", "heat.cu", "heat_tb.cu", "heat_stream.cu", "heat_batch.cu", "heat_vk.cu", "cg.cu",
-           "cg_mixed.cu", "cg_batch.cu"]
+           "cg_spmv_tma.cu", "cg_mixed.cu", "cg_batch.cu"]
 HEADERS = [ROOT / "include" / "heatcg.h", CSRC / "common.cuh", CSRC / "heat_common.cuh", CSRC / "tma.cuh",
-           CSRC / "cg_common.cuh"]
+           CSRC / "cg_common.cuh", CSRC / "xsum.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

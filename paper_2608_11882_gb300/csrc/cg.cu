@@ -365,6 +365,10 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     if (rc != HS_OK) return rc;
     const int mode = spmv_mode(c->A, c->grid);
     const int track = mode == SP_STAGED;   // the staged SpMV needs p's largest exponent
+    // the staged SpMV takes p through TMA when the grid and the vectors allow
+    CUtensorMap pmap;
+    const bool tma = mode == SP_STAGED && spmv_tma_eligible(c->A, c->p, c->q, c->grid) &&
+                     spmv_tma_map(&pmap, c->A, c->p) == 0;
     k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S, track);
     HS_CHECK_LAUNCH("cg: start kernel");
 
@@ -382,7 +386,13 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
             const int64_t nn = n;
             switch (mode) {
             case SP_STAGED:
-                k_cg_spmv_dot<SP_STAGED><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+                if (tma) {
+                    rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, c->grid, c->stream);
+                    if (rc != HS_OK) return rc;
+                } else {
+                    k_cg_spmv_dot<SP_STAGED><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials,
+                                                                                  c->S);
+                }
                 break;
             case SP_ROWS:
                 k_cg_spmv_dot<SP_ROWS><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
@@ -415,6 +425,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     const CgScalars f = *c->S_host;
     const bool converged = (f.done == 1);
     if (f.done == 2) return fail(HS_ECUDA, "cg_run: breakdown, p.q <= 0 (operator not positive definite?)");
+    if (f.done == 3) return fail(HS_ETIMEOUT, "cg_run: a bounded wait in the TMA-staged SpMV ran out");
     if (info) {
         info->iters = f.iters;
         info->relres_recur = f.relres;

@@ -1,6 +1,7 @@
 // Definitions shared by the CG solvers: device scalars, the operator as the
 // kernels see it, the context behind hs_cg_t, and host helpers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,7 +20,8 @@ struct CgScalars {
     double rtol;
     double relres;     // sqrt(rho)/||b|| at the last check
     double rr_true;    // ||b - A x||^2 at exit
-    int32_t done;      // 1: converged (or nothing to do); 2: breakdown (p.q <= 0)
+    int32_t done;      // 1: converged (or nothing to do); 2: breakdown (p.q <= 0);
+                       // 3: a bounded wait of the TMA-staged SpMV ran out
     int32_t iters;
     uint32_t ticket;   // blocks finished in the running reduction
     int32_t zero_rhs;  // ||b|| == 0
@@ -136,13 +138,15 @@ struct SpmvPlan {
     int tiles_x, kc;       // tiles per row of tiles, planes per chunk
 };
 
-// About two work items per block, at least 4 planes per chunk.
+// About one work item per block (the longest chunks that still give every
+// block work: each item restages its first and last planes and waits for its
+// first loads), at least 4 planes per chunk.
 __host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A, int nblocks)
 {
     SpmvPlan P;
     P.tiles_x = (A.nx + kSpTW - 1) / kSpTW;
     P.tiles = (int64_t)P.tiles_x * ((A.ny + kSpTY - 1) / kSpTY);
-    int64_t chunks = (2 * (int64_t)nblocks + P.tiles - 1) / P.tiles;
+    int64_t chunks = ((int64_t)nblocks + P.tiles - 1) / P.tiles;
     const int64_t maxc = A.nz / 4 > 1 ? A.nz / 4 : 1;
     if (chunks > maxc) chunks = maxc;
     if (chunks < 1) chunks = 1;
@@ -414,6 +418,14 @@ __device__ __forceinline__ void cg_fold_pmax(unsigned m, CgScalars* S, int slot,
 }
 
 struct CgMixed;   // mixed-precision state (cg_mixed.cu)
+
+// The TMA-staged form of the SP_STAGED SpMV (cg_spmv_tma.cu) for single
+// solves: eligible when nx is even and p, q are 16-byte aligned; the tensor
+// map spans p (spmv_tma_map returns 0 on success).
+bool spmv_tma_eligible(const OpDev& A, const double* p, const double* q, int nblocks);
+int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p);
+int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
+                    int nblocks, cudaStream_t stream);
 
 int check_op(const hs_op* A);
 OpDev to_dev(const hs_op* A);

@@ -90,3 +90,23 @@ def test_batch_with_staged_system_equals_single_bitwise(pkg):
     shape, _, b = ops[0]
     r = b - oracle.lap7_apply(xs[0].cpu().numpy().reshape(shape), threads=oracle.max_threads()).reshape(-1)
     assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("shape", [(200, 101, 190), (160, 120, 177)])
+def test_ragged_staged_grid_single_equals_batch(pkg, shape):
+    """Ragged grids large enough for the staged SpMV.  With nx even (190) a
+    single solve stages p by TMA, whose boxes reach past the grid's last
+    column, row and plane and read zeros there; with nx odd (177) it stages p
+    with loads.  A batch of one takes the load-staged kernel either way: the
+    two agree bit for bit, and the solution meets rtol by the oracle."""
+    nz, ny, nx = shape
+    b = cg_rhs(nx * ny * nz, seed=94)
+    op = pkg.Operator.stencil(nx, ny, nz)
+    with pkg.CG(op) as cg:
+        x1, i1 = cg.run(dev(b), rtol=1e-8, max_iter=5000)
+    with pkg.CGBatch([op]) as cb:
+        xs, infos = cb.run([dev(b)], rtol=1e-8, max_iter=5000)
+    assert i1["converged"] and infos[0]["iters"] == i1["iters"]
+    assert np.array_equal(xs[0].cpu().numpy(), x1.cpu().numpy())
+    r = b - oracle.lap7_apply(x1.cpu().numpy().reshape(shape), threads=oracle.max_threads()).reshape(-1)
+    assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(b)
