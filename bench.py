@@ -40,6 +40,12 @@ FP64_INSTR_PEAK_T = 0.625
 # heat arithmetic modes: Heat() keywords, the arithmetic type, algorithmic bytes per LUP,
 # and the roof that binds the Interior kernel
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (the measured copy rate is the roofline peak)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, from one ncu capture of the kernel as it stands, keyed by
+# (arithmetic, grid edge, steps per launch): the FP64 exact-sum Interior kernel
+# on 512^3 read 1121.7 MB and wrote 1029.2 MB per launch (mean of 2 launches).
+# Re-capture after any change to that kernel; sizes not listed report null.
+KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2150913408}
 HEAT_MODES = {
     # plain FP64 handle: FP64 fields, exact int64 neighbour sum, one FP64 FMA per point
     "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "hbm",
@@ -274,8 +280,11 @@ def interior_roofline(mode_name, n, int_ms, hbm_gbs, peak_kind, tdepth=1):
                 "unit": "T FP64-instr/s", "frac": rate / FP64_INSTR_PEAK_T, "traffic": None,
                 "hbm_achieved_gbs": hbm_rate, "hbm_peak_gbs": hbm_gbs, "hbm_frac": hbm_rate / hbm_gbs,
                 "hbm_peak_kind": peak_kind, "interior_ms_per_launch": int_ms}
+    traffic = KERNEL_TRAFFIC_BYTES.get((mode_name, n, tdepth))
     return {"bound": "hbm", "kernel": name, "achieved": hbm_rate, "peak": hbm_gbs, "unit": "GB/s",
-            "frac": hbm_rate / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
+            "frac": hbm_rate / hbm_gbs, "traffic": traffic,
+            "traffic_per_algorithmic": None if traffic is None else traffic / (lup * spec["bytes"]),
+            "peak_kind": peak_kind,
             "frac_of_nominal": hbm_rate / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
             "bytes_per_lup": spec["bytes"], "steps_per_launch": tdepth,
             "effective_gbs": hbm_rate * tdepth, "interior_ms_per_launch": int_ms}
