@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kCgBlock)
     k_cg_spmv_dot(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
                   CgScalars* S)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kCgBlock)
             pq = __fma_rn(__ldg(p + row), qv, pq);
         }
     }
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double tot = sum_partials(partials, gridDim.x, sh);
@@ -120,11 +122,13 @@ __global__ void __launch_bounds__(kCgBlock)
                 const double* __restrict__ p, const double* __restrict__ q, double* partials,
                 CgScalars* S)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     const double alpha = S->alpha;
     const double rr = cg_update_rows(n, x, r, p, q, alpha, (int64_t)blockIdx.x * kCgBlock + threadIdx.x,
                                      (int64_t)gridDim.x * kCgBlock);
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double rho_new = sum_partials(partials, gridDim.x, sh);
@@ -146,10 +150,12 @@ __global__ void __launch_bounds__(kCgBlock)
     k_cg_pupdate(int64_t n, const double* __restrict__ r, double* __restrict__ p, CgScalars* S,
                  int track_pmax)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     const double beta = S->beta;
     const unsigned pm = cg_pupdate_rows(n, r, p, beta, (int64_t)blockIdx.x * kCgBlock + threadIdx.x,
                                         (int64_t)gridDim.x * kCgBlock);
+    allow_dependents();
     // the update kernel has counted this iteration: p is the next one's direction
     if (track_pmax) cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
 }
@@ -390,20 +396,24 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
                     rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, c->grid, c->stream);
                     if (rc != HS_OK) return rc;
                 } else {
-                    k_cg_spmv_dot<SP_STAGED><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials,
-                                                                                  c->S);
+                    (void)launch_dependent(k_cg_spmv_dot<SP_STAGED>, c->grid, kCgBlock, c->stream, c->A,
+                                           (const double*)c->p, c->q, c->partials, c->S);
                 }
                 break;
             case SP_ROWS:
-                k_cg_spmv_dot<SP_ROWS><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+                (void)launch_dependent(k_cg_spmv_dot<SP_ROWS>, c->grid, kCgBlock, c->stream, c->A,
+                                       (const double*)c->p, c->q, c->partials, c->S);
                 break;
             default:
-                k_cg_spmv_dot<SP_CSR><<<c->grid, kCgBlock, 0, c->stream>>>(c->A, c->p, c->q, c->partials, c->S);
+                (void)launch_dependent(k_cg_spmv_dot<SP_CSR>, c->grid, kCgBlock, c->stream, c->A,
+                                       (const double*)c->p, c->q, c->partials, c->S);
             }
             HS_CHECK_LAUNCH("cg: spmv+dot kernel");
-            k_cg_update<<<c->grid, kCgBlock, 0, c->stream>>>(nn, x, c->r, c->p, c->q, c->partials, c->S);
+            (void)launch_dependent(k_cg_update, c->grid, kCgBlock, c->stream, nn, x, c->r, (const double*)c->p,
+                                   (const double*)c->q, c->partials, c->S);
             HS_CHECK_LAUNCH("cg: update kernel");
-            k_cg_pupdate<<<c->grid, kCgBlock, 0, c->stream>>>(nn, c->r, c->p, c->S, track);
+            (void)launch_dependent(k_cg_pupdate, c->grid, kCgBlock, c->stream, nn, (const double*)c->r, c->p,
+                                   c->S, track);
             HS_CHECK_LAUNCH("cg: p update kernel");
         }
         enqueued += todo;

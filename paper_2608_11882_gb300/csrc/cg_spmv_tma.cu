@@ -215,13 +215,17 @@ __global__ void __launch_bounds__(kCgBlock, 4)
     __shared__ __align__(128) long long stage[kSpNst * kSpStage];
     __shared__ __align__(8) uint64_t bars[kSpNst];
     __shared__ double sh[kCgBlock / 32];
-    if (*(volatile int32_t*)&S->done) return;
+    __shared__ int32_t s_done;
     const int tid = threadIdx.x;
+    grid_dependency_wait();   // p, the scalars and the stop flag come from the kernels before
     if (tid == 0) {
+        // one read for the block: another block's abort may change the flag
+        s_done = *(volatile int32_t*)&S->done;
         for (int s = 0; s < kSpNst; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (s_done) return;
     const int emax = cg_pemax(S);
     const bool conv = cg_xs_ok(emax);
     const SpmvPlan P = spmv_plan(A, gridDim.x);
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(kCgBlock, 4)
         if (tid == 0) atomicExch(reinterpret_cast<int*>(&S->done), 3);
         return;
     }
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double tot = sum_partials(partials, gridDim.x, sh);
@@ -269,7 +274,7 @@ int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p)
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
                     int nblocks, cudaStream_t stream)
 {
-    k_cg_spmv_tma<<<nblocks, kCgBlock, 0, stream>>>(map, A, q, partials, S);
+    (void)launch_dependent(k_cg_spmv_tma, nblocks, kCgBlock, stream, map, A, q, partials, S);
     HS_CHECK_LAUNCH("cg: spmv+dot kernel (TMA-staged)");
     return HS_OK;
 }

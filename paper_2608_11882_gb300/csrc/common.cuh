@@ -55,6 +55,32 @@ inline void dev_free(void* p, cudaStream_t s)
     if (p) (void)cudaFreeAsync(p, s);
 }
 
+// Programmatic dependent launch.  A kernel started by launch_dependent() may
+// begin while the kernel before it on the stream is still finishing: it runs
+// its own set-up, then grid_dependency_wait() holds it until that kernel has
+// completed and its writes are visible.  allow_dependents() marks the point
+// from which this block no longer needs its SM to itself; once every block
+// of the grid has passed it (or exited), the next kernel may start to launch.
+// In a launch without the attribute both are no-ops.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Sum of v over a block of BLOCK threads, in a fixed order (warp shuffles,
 // then warp 0 over the per-warp sums).  The result is valid in thread 0.
 // sh must hold BLOCK/32 doubles.
