@@ -93,7 +93,11 @@ __device__ __forceinline__ void fx_finish(unsigned long long m, FxState* fx, int
     if (tid == 0) {
         unsigned long long b = 0;
         for (int w = 0; w < NT / 32; ++w) b = wmax[w] > b ? wmax[w] : b;
-        atomicMax(&fx->slot[(m3 + 1) % 3].maxU, b);
+        // the slot only grows during a step: a block whose maximum is already
+        // there skips the atomic, so thousands of blocks finishing together
+        // do not queue on one address
+        unsigned long long* mu = &fx->slot[(m3 + 1) % 3].maxU;
+        if (b > *(volatile unsigned long long*)mu) atomicMax(mu, b);
         if (leader) {
             fx->slot[(m3 + 1) % 3].E = fx->slot[m3].E + k;
             fx->slot[(m3 + 2) % 3].maxU = 0;

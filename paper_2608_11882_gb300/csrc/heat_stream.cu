@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(32 * RY)
             if (nvalid == V) {
                 st_vec(out, v);
             } else {
-                for (int i = 0; i < nvalid; ++i) out[i] = v[i];
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (i < nvalid) out[i] = v[i];
             }
             if constexpr (kIsFixed<T>) {
 #pragma unroll
@@ -306,7 +308,9 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
             if (nvalid == V) {
                 st_vec(out, v);
             } else {
-                for (int i = 0; i < nvalid; ++i) out[i] = v[i];
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (i < nvalid) out[i] = v[i];
             }
 #pragma unroll
             for (int i = 0; i < V; ++i) {

@@ -171,7 +171,9 @@ __global__ void __launch_bounds__(32 * RY, 1)
                 if (nvalid == V)
                     st_vec(o, v);
                 else
-                    for (int i = 0; i < nvalid; ++i) o[i] = v[i];
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (i < nvalid) o[i] = v[i];
                 if constexpr (kIsFixed<T>) {
 #pragma unroll
                     for (int i = 0; i < V; ++i) {
