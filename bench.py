@@ -413,8 +413,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     hsteps = args.heat_steps
-    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range(hsteps)]
 
     step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     step_launches = [0]
@@ -431,12 +429,10 @@ def run_ours(args):
             step_launches[0] = nat.launch_count() - l0
             step_ev[1].record(stream)
         elif timed_interior:
-            for s in range(hsteps):
-                heat.boundary()
-                pairs[s][0].record(stream)
-                heat.interior()
-                pairs[s][1].record(stream)
-                heat.swap()
+            # the library brackets each Interior launch with events on this stream
+            heat.time_interior(True)
+            heat.step(hsteps)
+            heat.time_interior(False)
         else:
             heat.step(hsteps)
         heat.read(u_out_dev)
@@ -472,7 +468,7 @@ def run_ours(args):
         if heat.tdepth > 1:
             interior_ms.append(step_ev[0].elapsed_time(step_ev[1]) / step_launches[0])
         else:
-            interior_ms.append(sum(a.elapsed_time(b) for a, b in pairs) / hsteps)
+            interior_ms.append(heat.interior_time()[0])
         infos.append((i_mf, i_csr))
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -570,12 +566,8 @@ def run_ours(args):
                 nl = nat.launch_count() - l0
                 step_ev[1].record(stream)
             else:
-                for s in range(hsteps):
-                    h.boundary()
-                    pairs[s][0].record(stream)
-                    h.interior()
-                    pairs[s][1].record(stream)
-                    h.swap()
+                h.time_interior(True)
+                h.step(hsteps)
             out = torch.empty_like(src)
             h.read(out)
             ev1.record(stream)
@@ -583,7 +575,7 @@ def run_ours(args):
             if h.tdepth > 1:
                 ims = step_ev[0].elapsed_time(step_ev[1]) / nl
             else:
-                ims = sum(a.elapsed_time(b) for a, b in pairs) / hsteps
+                ims = h.interior_time()[0]
             return ev0.elapsed_time(ev1), ims, out
 
         fields = {args.heat_mode: u_out_dev}

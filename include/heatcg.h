@@ -147,7 +147,11 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device);
  * kernel on the first and last interior k-planes and the Interior kernel on
  * the planes between them (Algorithms BOUNDARY and INTERIOR; on one GPU the
  * planes a k-split would exchange are the outermost interior planes), then
- * swaps the buffers by pointer (Algorithm "1-GPU Baseline").  With tdepth
+ * swaps the buffers by pointer (Algorithm "1-GPU Baseline").  On grids of
+ * 2^22 points or more the Boundary kernel runs on a side stream of the
+ * handle, forked from and joined back to the handle's stream every step, so
+ * it overlaps the Interior kernel (the two write disjoint planes); the
+ * handle's stream still orders everything after the step.  With tdepth
  * L >= 2 each pass over HBM advances L steps (temporal blocking: tiles with
  * an L-wide halo stream up the k axis, the intermediate time levels living
  * in shared memory and registers), then swaps; a remainder of n_steps is done
@@ -166,6 +170,17 @@ int heat_step(hs_heat_t h, int64_t n_steps);
 int heat_interior(hs_heat_t h);
 int heat_boundary(hs_heat_t h);
 int heat_swap(hs_heat_t h);
+
+/* Interior-kernel timing, for measuring the kernel against its roofline
+ * inside a running step loop.  heat_time_interior(h, 1) makes heat_step (at
+ * tdepth 1) bracket every Interior launch with a pair of timing CUDA events
+ * on the handle's stream; heat_time_interior(h, 0) stops it.
+ * heat_interior_time waits for the last recorded launch, writes the mean
+ * duration in milliseconds of the launches recorded since the previous call
+ * (0 if none) and their count, and clears the record.  Either output may be
+ * NULL.  The events belong to the handle (freed by heat_destroy). */
+int heat_time_interior(hs_heat_t h, int enable);
+int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches);
 
 /* Copy the current interior field to dst (nx*ny*nz elements, x fastest):
  * host memory if dst_is_device == 0, device memory otherwise.  Synchronises

@@ -67,6 +67,8 @@ def _load():
         "heat_swap": [vp],
         "heat_read": [vp, vp, ctypes.c_int],
         "heat_steps_done": [vp, ctypes.POINTER(i64)],
+        "heat_time_interior": [vp, ctypes.c_int],
+        "heat_interior_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
         "heat_get_tdepth": [vp, ctypes.POINTER(i32)],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
@@ -155,6 +157,16 @@ def heat_steps_done(h: int) -> int:
     s = ctypes.c_int64()
     check(lib.heat_steps_done(h, ctypes.byref(s)), "heat_steps_done")
     return s.value
+
+
+def heat_time_interior(h: int, enable: bool) -> None:
+    check(lib.heat_time_interior(h, int(bool(enable))), "heat_time_interior")
+
+
+def heat_interior_time(h: int):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    check(lib.heat_interior_time(h, ctypes.byref(ms), ctypes.byref(n)), "heat_interior_time")
+    return ms.value, n.value
 
 
 def heat_get_tdepth(h: int) -> int:

@@ -103,6 +103,16 @@ class Heat:
     def steps_done(self) -> int:
         return native.heat_steps_done(self.handle)
 
+    def time_interior(self, enable: bool = True):
+        """Bracket every Interior launch of ``step`` with timing events."""
+        native.heat_time_interior(self.handle, enable)
+        return self
+
+    def interior_time(self):
+        """(mean milliseconds, launches) of the Interior launches timed since
+        the last call; waits for the last one."""
+        return native.heat_interior_time(self.handle)
+
     def close(self):
         if getattr(self, "handle", None):
             native.heat_destroy(self.handle)

@@ -37,6 +37,7 @@
 // and ny+1 and the x-boundary cells hold the Dirichlet zeros in both buffers
 // and are never written after creation, so a pointer swap keeps them intact.
 #include <cmath>
+#include <vector>
 #include <cstdlib>
 #include <new>
 #include <type_traits>
@@ -311,9 +312,20 @@ struct hs_heat {
     void* kap;             // HS_VARKAPPA: kappa on every padded node
     void* fdt;             // HS_VARKAPPA: dt f on the interior
     double vbx, vby, vbz;  // HS_VARKAPPA: dt / (2 h_d^2)
+    // Large grids run each step's Boundary kernel on a side stream, beside the
+    // Interior kernel: forked from `stream` after the previous step (ev_fork)
+    // and joined back before the next one (ev_join).  Null: one stream.
+    cudaStream_t bstream;
+    cudaEvent_t ev_fork, ev_join;
+    // heat_time_interior: event pairs around the Interior launches of heat_step
+    bool timing;
+    std::vector<cudaEvent_t> tev;   // 2 per recorded launch, reused
+    size_t tev_used;                // pairs recorded since the last heat_interior_time
 };
 
 namespace {
+
+constexpr int64_t kForkMinPoints = (int64_t)1 << 22;
 
 constexpr uint32_t kKnownFlags =
     HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64 | HS_VARKAPPA | HS_FP64_PIPE;
@@ -408,12 +420,12 @@ int launch_interior_t(hs_heat* h, T param)
 }
 
 template <typename T, bool EXACT>
-int launch_boundary_t(hs_heat* h, T param)
+int launch_boundary_t(hs_heat* h, T param, cudaStream_t s)
 {
     const HeatGeom& g = h->g;
     dim3 block(kBX, kBY, 1);
     dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz >= 2 ? 2 : 1);
-    k_heat_boundary<T, EXACT><<<grid, block, 0, h->stream>>>(
+    k_heat_boundary<T, EXACT><<<grid, block, 0, s>>>(
         (const T*)h->buf[h->cur], (T*)h->buf[1 - h->cur], g, param, h->fx, (int)(h->fxseq % 3));
     HS_CHECK_LAUNCH("heat boundary kernel");
     return HS_OK;
@@ -457,7 +469,7 @@ int launch_stream_interior(hs_heat* h)
     return stream_launch(c);
 }
 
-int launch_part_xs(hs_heat* h, Part p)
+int launch_part_xs(hs_heat* h, Part p, cudaStream_t s)
 {
     const HeatGeom& g = h->g;
     const double* src = (const double*)h->buf[h->cur];
@@ -466,7 +478,7 @@ int launch_part_xs(hs_heat* h, Part p)
     if (p == P_INTERIOR) return launch_stream_interior(h);
     if (p == P_BOUNDARY) {
         dim3 grid((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz >= 2 ? 2 : 1);
-        k_heat_boundary_xs<<<grid, dim3(kBX, kBY, 1), 0, h->stream>>>(src, dst, g, h->r, h->fx, m3);
+        k_heat_boundary_xs<<<grid, dim3(kBX, kBY, 1), 0, s>>>(src, dst, g, h->r, h->fx, m3);
         HS_CHECK_LAUNCH("heat boundary kernel (FP64 exact sum)");
         return HS_OK;
     }
@@ -479,18 +491,18 @@ int launch_part_xs(hs_heat* h, Part p)
 }
 
 template <typename T, bool EXACT>
-int launch_part(hs_heat* h, Part p, T param)
+int launch_part(hs_heat* h, Part p, T param, cudaStream_t s)
 {
     // FP64 is bound by the FP64 pipe, where the register z-march issues the
     // fewest extra instructions; the HBM-bound arithmetics stream through TMA.
     if (p == P_INTERIOR)
         return std::is_same<T, double>::value ? launch_interior_t<T, EXACT>(h, param)
                                               : launch_stream_interior(h);
-    if (p == P_BOUNDARY) return launch_boundary_t<T, EXACT>(h, param);
+    if (p == P_BOUNDARY) return launch_boundary_t<T, EXACT>(h, param, s);
     return launch_full_t<T, EXACT>(h, param);
 }
 
-int vk_part(hs_heat* h, Part p)
+int vk_part(hs_heat* h, Part p, cudaStream_t s)
 {
     VkCall c;
     c.part = (p == P_INTERIOR) ? 0 : 1;
@@ -504,21 +516,43 @@ int vk_part(hs_heat* h, Part p)
     c.by = h->vby;
     c.bz = h->vbz;
     c.kchunk = h->kchunk;
-    c.stream = h->stream;
+    c.stream = s;
     return vk_launch(c);
 }
 
-int do_part(hs_heat* h, Part p)
+// Launches one part of a step.  The Boundary kernel goes to stream s (the
+// handle's own stream unless given); the other parts always to h->stream.
+int do_part(hs_heat* h, Part p, cudaStream_t s = nullptr)
 {
-    if (h->flags & HS_VARKAPPA) return vk_part(h, p);
+    if (!s || p != P_BOUNDARY) s = h->stream;
+    if (h->flags & HS_VARKAPPA) return vk_part(h, p, s);
     switch (h->arith) {
-    case A_F64: return launch_part<double, false>(h, p, h->r);
-    case A_F64_EXACT: return launch_part<double, true>(h, p, h->r);
-    case A_F32: return launch_part<float, false>(h, p, (float)h->r);
-    case A_FX64: return launch_part<long long, false>(h, p, h->R);
-    case A_F64_XS: return launch_part_xs(h, p);
+    case A_F64: return launch_part<double, false>(h, p, h->r, s);
+    case A_F64_EXACT: return launch_part<double, true>(h, p, h->r, s);
+    case A_F32: return launch_part<float, false>(h, p, (float)h->r, s);
+    case A_FX64: return launch_part<long long, false>(h, p, h->R, s);
+    case A_F64_XS: return launch_part_xs(h, p, s);
     }
     return fail(HS_EINVAL, "heat: unknown arithmetic");
+}
+
+// The Interior part of a heat_step step, between a pair of timing events on
+// the handle's stream while heat_time_interior is on.
+int timed_interior(hs_heat* h)
+{
+    if (!h->timing) return do_part(h, P_INTERIOR);
+    const size_t i = 2 * h->tev_used;
+    while (h->tev.size() < i + 2) {
+        cudaEvent_t e;
+        HS_TRY_CUDA(cudaEventCreate(&e), "heat_step: timing event");
+        h->tev.push_back(e);
+    }
+    HS_TRY_CUDA(cudaEventRecord(h->tev[i], h->stream), "heat_step: timing event");
+    const int rc = do_part(h, P_INTERIOR);
+    if (rc != HS_OK) return rc;
+    HS_TRY_CUDA(cudaEventRecord(h->tev[i + 1], h->stream), "heat_step: timing event");
+    h->tev_used += 1;
+    return HS_OK;
 }
 
 // Temporal depth when the descriptor leaves it to the library: FP64 is bound
@@ -788,6 +822,19 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             return rc;
         }
     }
+    // A Boundary kernel beside the Interior one pays for its extra API calls
+    // once the Interior kernel takes tens of microseconds (2^22 points and up).
+    const int64_t npts = (int64_t)h->g.nx * h->g.ny * h->g.nz;
+    if (!(h->flags & HS_SCHED_FULL) && h->tdepth == 1 && npts >= kForkMinPoints && h->g.nz >= 3) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "heat_create: side stream");
+            heat_destroy(h);
+            return rc;
+        }
+    }
     *out = h;
     return HS_OK;
 }
@@ -871,15 +918,52 @@ int heat_step(hs_heat_t h, int64_t n_steps)
         int rc;
         if (h->flags & HS_SCHED_FULL) {
             rc = do_part(h, P_FULL);
+        } else if (h->bstream) {
+            // Interior on the handle's stream, Boundary beside it on the side
+            // stream (the two write disjoint planes of the new level and fold
+            // into the step maximum with atomics); the next step starts after both
+            HS_TRY_CUDA(cudaEventRecord(h->ev_fork, h->stream), "heat_step: fork event");
+            rc = timed_interior(h);
+            if (rc != HS_OK) return rc;
+            HS_TRY_CUDA(cudaStreamWaitEvent(h->bstream, h->ev_fork, 0), "heat_step: fork wait");
+            rc = do_part(h, P_BOUNDARY, h->bstream);
+            if (rc != HS_OK) return rc;
+            HS_TRY_CUDA(cudaEventRecord(h->ev_join, h->bstream), "heat_step: join event");
+            HS_TRY_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "heat_step: join wait");
         } else {
             rc = do_part(h, P_BOUNDARY);
-            if (rc == HS_OK) rc = do_part(h, P_INTERIOR);
+            if (rc == HS_OK) rc = timed_interior(h);
         }
         if (rc != HS_OK) return rc;
         h->cur = 1 - h->cur;
         h->steps += 1;
         h->fxseq += 1;
     }
+    return HS_OK;
+}
+
+int heat_time_interior(hs_heat_t h, int enable)
+{
+    if (!h) return fail(HS_EINVAL, "heat_time_interior: NULL handle");
+    h->timing = enable != 0;
+    return HS_OK;
+}
+
+int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches)
+{
+    if (!h) return fail(HS_EINVAL, "heat_interior_time: NULL handle");
+    double total = 0.0;
+    const size_t n = h->tev_used;
+    if (n > 0) HS_TRY_CUDA(cudaEventSynchronize(h->tev[2 * n - 1]), "heat_interior_time: synchronize");
+    for (size_t i = 0; i < n; ++i) {
+        float ms = 0.0f;
+        HS_TRY_CUDA(cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]),
+                    "heat_interior_time: elapsed time");
+        total += ms;
+    }
+    h->tev_used = 0;
+    if (mean_ms) *mean_ms = n ? total / (double)n : 0.0;
+    if (launches) *launches = (int64_t)n;
     return HS_OK;
 }
 
@@ -942,6 +1026,14 @@ int heat_destroy(hs_heat_t h)
         cudaError_t e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "heat_destroy: stream synchronize");
     }
+    if (h->bstream) {
+        cudaError_t e = cudaStreamSynchronize(h->bstream);
+        if (e != cudaSuccess && rc == HS_OK) rc = cuda_fail(e, "heat_destroy: side stream synchronize");
+        (void)cudaStreamDestroy(h->bstream);
+    }
+    for (cudaEvent_t e : h->tev) (void)cudaEventDestroy(e);
+    if (h->ev_fork) (void)cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) (void)cudaEventDestroy(h->ev_join);
     for (int b = 0; b < 2; ++b) dev_free(h->buf[b], h->stream);
     dev_free(h->fx, h->stream);
     dev_free(h->err, h->stream);

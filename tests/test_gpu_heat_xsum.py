@@ -120,3 +120,51 @@ def test_flag_errors(pkg):
     for kw in (dict(dtype="f32", flags=pkg.HS_FP64_PIPE), dict(flags=pkg.HS_FP64_PIPE | pkg.HS_FIXED64)):
         with pytest.raises(pkg.HeatCGError):
             pkg.Heat(4, 4, 4, 0.1, **kw)
+
+
+@pytest.mark.parametrize("dtype,flags", [("f64", 0), ("f64", "HS_FIXED64"), ("f32", 0)])
+def test_side_stream_boundary_equals_full_step(pkg, dtype, flags):
+    """A grid of 2^22 points or more runs each step's Boundary kernel on a side
+    stream beside the Interior kernel; the result equals the one-kernel full
+    step bit for bit (disjoint planes, the same per-step maxima)."""
+    flags = getattr(pkg, flags) if flags else 0
+    nz, ny, nx = 163, 161, 166   # 4,356,478 points, ragged against every tile
+    rng = np.random.default_rng(23)
+    u0 = rng.uniform(-1, 1, size=(nz, ny, nx))
+    out = []
+    for extra in (0, pkg.HS_SCHED_FULL):
+        with pkg.Heat(nx, ny, nz, 0.13, dtype=dtype, flags=flags | extra) as h:
+            h.upload(u0.astype(np.float64 if dtype == "f64" else np.float32))
+            h.step(7)
+            out.append(h.read())
+    assert np.array_equal(out[0], out[1])
+    if dtype == "f64":
+        assert rel_max_err(out[0], oracle.heat_run(u0, 0.13, 7, threads=oracle.max_threads())) <= F64_REL
+
+
+def test_split_entry_points_and_interior_timing(pkg):
+    """heat_boundary + heat_interior + heat_swap per step equal heat_step bit
+    for bit (on a grid where heat_step runs the two kernels side by side); with
+    timing on, heat_step records one Interior duration per step, and reading
+    the record clears it."""
+    nz, ny, nx = 161, 163, 166
+    u0 = np.random.default_rng(29).uniform(-1, 1, size=(nz, ny, nx))
+    with pkg.Heat(nx, ny, nz, 0.12) as a:
+        a.upload(u0)
+        a.time_interior(True)
+        a.step(5)
+        ms, n = a.interior_time()
+        assert n == 5 and ms > 0.0
+        assert a.interior_time() == (0.0, 0)
+        a.time_interior(False)
+        a.step(1)
+        assert a.interior_time() == (0.0, 0)
+        ra = a.read()
+    with pkg.Heat(nx, ny, nz, 0.12) as b:
+        b.upload(u0)
+        for _ in range(6):
+            b.boundary()
+            b.interior()
+            b.swap()
+        rb = b.read()
+    assert np.array_equal(ra, rb)
