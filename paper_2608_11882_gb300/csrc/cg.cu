@@ -396,24 +396,24 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
                     rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, c->grid, c->stream);
                     if (rc != HS_OK) return rc;
                 } else {
-                    (void)launch_dependent(k_cg_spmv_dot<SP_STAGED>, c->grid, kCgBlock, c->stream, c->A,
-                                           (const double*)c->p, c->q, c->partials, c->S);
+                    HS_TRY_CUDA(launch_dependent(k_cg_spmv_dot<SP_STAGED>, c->grid, kCgBlock, c->stream, c->A,
+                                           (const double*)c->p, c->q, c->partials, c->S), "cg: kernel launch");
                 }
                 break;
             case SP_ROWS:
-                (void)launch_dependent(k_cg_spmv_dot<SP_ROWS>, c->grid, kCgBlock, c->stream, c->A,
-                                       (const double*)c->p, c->q, c->partials, c->S);
+                HS_TRY_CUDA(launch_dependent(k_cg_spmv_dot<SP_ROWS>, c->grid, kCgBlock, c->stream, c->A,
+                                       (const double*)c->p, c->q, c->partials, c->S), "cg: kernel launch");
                 break;
             default:
-                (void)launch_dependent(k_cg_spmv_dot<SP_CSR>, c->grid, kCgBlock, c->stream, c->A,
-                                       (const double*)c->p, c->q, c->partials, c->S);
+                HS_TRY_CUDA(launch_dependent(k_cg_spmv_dot<SP_CSR>, c->grid, kCgBlock, c->stream, c->A,
+                                       (const double*)c->p, c->q, c->partials, c->S), "cg: kernel launch");
             }
             HS_CHECK_LAUNCH("cg: spmv+dot kernel");
-            (void)launch_dependent(k_cg_update, c->grid, kCgBlock, c->stream, nn, x, c->r, (const double*)c->p,
-                                   (const double*)c->q, c->partials, c->S);
+            HS_TRY_CUDA(launch_dependent(k_cg_update, c->grid, kCgBlock, c->stream, nn, x, c->r, (const double*)c->p,
+                                   (const double*)c->q, c->partials, c->S), "cg: kernel launch");
             HS_CHECK_LAUNCH("cg: update kernel");
-            (void)launch_dependent(k_cg_pupdate, c->grid, kCgBlock, c->stream, nn, (const double*)c->r, c->p,
-                                   c->S, track);
+            HS_TRY_CUDA(launch_dependent(k_cg_pupdate, c->grid, kCgBlock, c->stream, nn, (const double*)c->r, c->p,
+                                   c->S, track), "cg: kernel launch");
             HS_CHECK_LAUNCH("cg: p update kernel");
         }
         enqueued += todo;

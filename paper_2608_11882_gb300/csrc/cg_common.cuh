@@ -421,7 +421,8 @@ struct CgMixed;   // mixed-precision state (cg_mixed.cu)
 
 // The TMA-staged form of the SP_STAGED SpMV (cg_spmv_tma.cu) for single
 // solves: eligible when nx is even and p, q are 16-byte aligned; the tensor
-// map spans p (spmv_tma_map returns 0 on success).
+// map spans p (spmv_tma_map returns 0 on success).  spmv_tma_launch leaves
+// the launch check and count to its caller.
 bool spmv_tma_eligible(const OpDev& A, const double* p, const double* q, int nblocks);
 int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p);
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,

@@ -271,12 +271,12 @@ int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p)
                             (uint64_t)A.nx, (uint64_t)A.ny, (uint64_t)A.nz, kSpBW, kSpTY + 2);
 }
 
+// The caller checks and counts the launch, as for the other SpMV kernels.
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
                     int nblocks, cudaStream_t stream)
 {
-    (void)launch_dependent(k_cg_spmv_tma, nblocks, kCgBlock, stream, map, A, q, partials, S);
-    HS_CHECK_LAUNCH("cg: spmv+dot kernel (TMA-staged)");
-    return HS_OK;
+    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nblocks, kCgBlock, stream, map, A, q, partials, S);
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "cg: spmv+dot kernel (TMA-staged)");
 }
 
 }  // namespace hcg

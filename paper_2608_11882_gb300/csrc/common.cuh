@@ -78,7 +78,9 @@ inline cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (e != cudaSuccess) (void)cudaGetLastError();   // reported through the return value only
+    return e;
 }
 
 // Sum of v over a block of BLOCK threads, in a fixed order (warp shuffles,

@@ -147,3 +147,28 @@ def test_unaligned_solution_buffer_same_result(pkg, kind):
         x2, i2 = cg.run(b, x=store[1:], rtol=1e-10)
     assert i1["iters"] == i2["iters"]
     assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+
+
+@pytest.mark.parametrize("shape,kind", [((176, 176, 176), "stencil"), ((176, 176, 175), "stencil"),
+                                        ((20, 18, 16), "stencil"), ((12, 10, 14), "csr")])
+def test_launch_count_of_a_solve(pkg, shape, kind):
+    """hs_launch_count counts every kernel a solve launches, once: q = A x0, the
+    start kernel, three kernels per enqueued iteration (iterations go out in
+    chunks of 4, 8, 16, then 32 between reads of the stop flag), the final
+    A x and the residual norm -- whichever SpMV kernel the grid takes (TMA-staged
+    for 176^3, load-staged for nx = 175, row kernel for the small grid, CSR)."""
+    from paper_2608_11882_gb300 import _native
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    op = pkg.Operator.stencil(nx, ny, nz) if kind == "stencil" else csr_op(pkg, nx, ny, nz)
+    b = dev(cg_rhs(n, seed=31))
+    with pkg.CG(op) as cg:
+        c0 = _native.launch_count()
+        _, info = cg.run(b, rtol=1e-8, max_iter=5000)
+        launched = _native.launch_count() - c0
+    assert info["converged"]
+    enq, chunk = 0, 4
+    while enq < info["iters"]:
+        enq += chunk
+        chunk = min(2 * chunk, 32)
+    assert launched == 4 + 3 * enq
