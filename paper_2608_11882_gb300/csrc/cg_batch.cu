@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
 template <int MODE>
 __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, int nsys)
 {
+    grid_dependency_wait();
     int local;
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
     if (s.mode != MODE || *(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, in
         s.q[row] = qv;
         pq = __fma_rn(__ldg(s.p + row), qv, pq);
     }
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(pq, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double tot = sum_partials_n(s.partials, s.nblocks, sh);
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, in
 
 __global__ void __launch_bounds__(kCgBlock) k_cgb_update(const SysDev* sys, int nsys)
 {
+    grid_dependency_wait();
     int local;
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
     if (*(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_update(const SysDev* sys, int 
     const double alpha = s.S->alpha;
     const double rr = cg_update_rows(s.A.n, s.x, s.r, s.p, s.q, alpha, (int64_t)local * kCgBlock + threadIdx.x,
                                      (int64_t)s.nblocks * kCgBlock);
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho_new = sum_partials_n(s.partials, s.nblocks, sh);
@@ -185,6 +189,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_update(const SysDev* sys, int 
 
 __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int nsys)
 {
+    grid_dependency_wait();
     int local;
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
     // the update kernel of this iteration has already counted it
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int
     const double beta = s.S->beta;
     const unsigned pm = cg_pupdate_rows(s.A.n, s.r, s.p, beta, (int64_t)local * kCgBlock + threadIdx.x,
                                         (int64_t)s.nblocks * kCgBlock);
+    allow_dependents();
     if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
 }
 
@@ -343,6 +349,13 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
         kern<<<G, kCgBlock, 0, b->stream>>>(b->d_sys, n);                      \
         HS_CHECK_LAUNCH(what);                                                 \
     } while (0)
+    // the iteration kernels launch as dependent launches: each waits on entry
+    // for the kernel before it, and its launch overlaps that kernel's tail
+#define CGB_LAUNCH_DEP(kern, what)                                                             \
+    do {                                                                                       \
+        HS_TRY_CUDA(launch_dependent(kern, G, kCgBlock, b->stream, b->d_sys, n), "cg batch: kernel launch"); \
+        HS_CHECK_LAUNCH(what);                                                                 \
+    } while (0)
     CGB_LAUNCH(k_cgb_apply_x, "cg batch: A x0 kernel");
     CGB_LAUNCH(k_cgb_start, "cg batch: start kernel");
     int32_t enqueued = 0;
@@ -358,11 +371,11 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
         if (all || enqueued >= max_iter) break;
         const int32_t todo = (max_iter - enqueued < chunk) ? max_iter - enqueued : chunk;
         for (int32_t t = 0; t < todo; ++t) {
-            if (b->has_mode[SP_STAGED]) CGB_LAUNCH(k_cgb_spmv_dot<SP_STAGED>, "cg batch: spmv+dot kernel");
-            if (b->has_mode[SP_ROWS]) CGB_LAUNCH(k_cgb_spmv_dot<SP_ROWS>, "cg batch: spmv+dot kernel");
-            if (b->has_mode[SP_CSR]) CGB_LAUNCH(k_cgb_spmv_dot<SP_CSR>, "cg batch: spmv+dot kernel");
-            CGB_LAUNCH(k_cgb_update, "cg batch: update kernel");
-            CGB_LAUNCH(k_cgb_pupdate, "cg batch: p update kernel");
+            if (b->has_mode[SP_STAGED]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_STAGED>, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_ROWS]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_ROWS>, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_CSR]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_CSR>, "cg batch: spmv+dot kernel");
+            CGB_LAUNCH_DEP(k_cgb_update, "cg batch: update kernel");
+            CGB_LAUNCH_DEP(k_cgb_pupdate, "cg batch: p update kernel");
         }
         enqueued += todo;
         if (chunk < 32) chunk *= 2;
@@ -375,6 +388,7 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
     CGB_LAUNCH(k_cgb_apply_x, "cg batch: A x kernel");
     CGB_LAUNCH(k_cgb_resid, "cg batch: residual kernel");
 #undef CGB_LAUNCH
+#undef CGB_LAUNCH_DEP
     HS_TRY_CUDA(cudaMemcpyAsync(b->h_S, b->d_S, sizeof(CgScalars) * (size_t)n, cudaMemcpyDeviceToHost,
                                 b->stream),
                 "cg_batch_run: scalar readback");

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kCgBlock)
     k_mx_spmv_dot(OpDev32 A, const float* __restrict__ p, float* __restrict__ q, double* partials,
                   MxScalars* S)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->inner_done) return;
     __shared__ double sh[kCgBlock / 32];
     Acc32 pq;
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kCgBlock)
             pq.add(__ldg(p + row), qv);
         }
     }
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(pq.total(), sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double tot = sum_partials(partials, gridDim.x, sh);
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(kCgBlock)
     k_mx_update(int64_t n, float* __restrict__ d, float* __restrict__ r, const float* __restrict__ p,
                 const float* __restrict__ q, double* partials, MxScalars* S)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->inner_done) return;
     __shared__ double sh[kCgBlock / 32];
     const float alpha = (float)S->alpha;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(kCgBlock)
             r[t] = rt;
             rr.add(rt, rt);
         }
+    allow_dependents();
     const double blk = block_sum<kCgBlock>(rr.total(), sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double rho_new = sum_partials(partials, gridDim.x, sh);
@@ -285,6 +289,7 @@ __global__ void __launch_bounds__(kCgBlock)
 __global__ void __launch_bounds__(kCgBlock)
     k_mx_pupdate(int64_t n, const float* __restrict__ r, float* __restrict__ p, MxScalars* S)
 {
+    grid_dependency_wait();
     if (*(volatile int32_t*)&S->inner_done) return;
     const float beta = (float)S->beta;
     const int64_t t0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x, stride = (int64_t)gridDim.x * kCgBlock;
@@ -384,16 +389,24 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
             if (todo > budget_inner) todo = budget_inner;
             if (todo <= 0) break;
             for (int32_t t = 0; t < todo; ++t) {
+                // dependent launches: each kernel's launch overlaps the previous
+                // kernel's final reduction (it waits for that kernel on entry)
                 if (c->A.kind == HS_OP_STENCIL7)
-                    k_mx_spmv_dot<HS_OP_STENCIL7><<<G, kCgBlock, 0, c->stream>>>(m->A32, m->p, m->q,
-                                                                                 m->partials, m->S);
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_dot<HS_OP_STENCIL7>, G, kCgBlock, c->stream, m->A32,
+                                                 (const float*)m->p, m->q, m->partials, m->S),
+                                "cg mixed: kernel launch");
                 else
-                    k_mx_spmv_dot<HS_OP_CSR><<<G, kCgBlock, 0, c->stream>>>(m->A32, m->p, m->q,
-                                                                            m->partials, m->S);
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_dot<HS_OP_CSR>, G, kCgBlock, c->stream, m->A32,
+                                                 (const float*)m->p, m->q, m->partials, m->S),
+                                "cg mixed: kernel launch");
                 HS_CHECK_LAUNCH("cg mixed: spmv+dot kernel");
-                k_mx_update<<<G, kCgBlock, 0, c->stream>>>(n, m->d, m->r, m->p, m->q, m->partials, m->S);
+                HS_TRY_CUDA(launch_dependent(k_mx_update, G, kCgBlock, c->stream, n, m->d, m->r,
+                                             (const float*)m->p, (const float*)m->q, m->partials, m->S),
+                            "cg mixed: kernel launch");
                 HS_CHECK_LAUNCH("cg mixed: update kernel");
-                k_mx_pupdate<<<G, kCgBlock, 0, c->stream>>>(n, m->r, m->p, m->S);
+                HS_TRY_CUDA(launch_dependent(k_mx_pupdate, G, kCgBlock, c->stream, n, (const float*)m->r, m->p,
+                                             m->S),
+                            "cg mixed: kernel launch");
                 HS_CHECK_LAUNCH("cg mixed: p update kernel");
             }
             inner += todo;
