@@ -581,7 +581,9 @@ int pick_kc_stream(const HeatGeom& g, int arith)
     const int tw = 512 / (int)g.elem;                  // tile width: 32 threads x one 16-byte vector
     const int ry = stream_rows_for(arith);
     const int64_t tiles = (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + ry - 1) / ry);
-    // about four waves of 3 blocks of 16 rows per SM (the exact-sum kernel: 4 of 8 rows)
+    // about four waves of 3 blocks of 16 rows per SM; the exact-sum kernel (8 rows,
+    // 5 resident blocks per SM) gets 16 blocks per SM, about 3.4 waves -- measured
+    // ahead of 4 waves of shorter chunks and 2 waves of longer ones
     const int64_t target = (int64_t)kNumSMs * (arith == A_F64_XS ? 4 : 3) * 4;
     const int64_t planes = g.nz > 2 ? g.nz - 2 : 1;
     int64_t chunks = (target + tiles - 1) / tiles;
