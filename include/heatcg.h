@@ -139,8 +139,9 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
  * copies u_old and u_new alike, Algorithm "1-GPU Baseline"; here the spare
  * buffer needs no copy: its boundary layer is zero from creation and the next
  * step writes every interior value of it before any is read.)  u is host memory
- * if src_is_device == 0 (pinned host memory makes the copy asynchronous),
- * device memory otherwise.  Enqueued on the handle's stream. */
+ * if src_is_device == 0 (one strided copy; pinned host memory makes it
+ * asynchronous), device memory otherwise (a re-layout kernel).  Enqueued on
+ * the handle's stream. */
 int heat_upload(hs_heat_t h, const void* u, int src_is_device);
 
 /* Advance n_steps >= 0 steps.  With tdepth 1 each step runs the Boundary
@@ -183,8 +184,9 @@ int heat_time_interior(hs_heat_t h, int enable);
 int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches);
 
 /* Copy the current interior field to dst (nx*ny*nz elements, x fastest):
- * host memory if dst_is_device == 0, device memory otherwise.  Synchronises
- * the handle's stream and reports any asynchronous error. */
+ * host memory if dst_is_device == 0 (one strided copy), device memory
+ * otherwise (a re-layout kernel).  Synchronises the handle's stream and
+ * reports any asynchronous error. */
 int heat_read(hs_heat_t h, void* dst, int dst_is_device);
 
 /* Steps applied since the last heat_upload. */
