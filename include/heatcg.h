@@ -179,7 +179,8 @@ int heat_swap(hs_heat_t h);
  * heat_interior_time waits for the last recorded launch, writes the mean
  * duration in milliseconds of the launches recorded since the previous call
  * (0 if none) and their count, and clears the record.  Either output may be
- * NULL.  The events belong to the handle (freed by heat_destroy). */
+ * NULL.  A record holds up to 8192 launches; later ones go untimed until it
+ * is read.  The events belong to the handle (freed by heat_destroy). */
 int heat_time_interior(hs_heat_t h, int enable);
 int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches);
 

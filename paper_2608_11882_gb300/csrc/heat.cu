@@ -326,6 +326,7 @@ struct hs_heat {
 namespace {
 
 constexpr int64_t kForkMinPoints = (int64_t)1 << 22;
+constexpr size_t kMaxTimedLaunches = 8192;   // event pairs a handle keeps for heat_interior_time
 
 constexpr uint32_t kKnownFlags =
     HS_ALLOW_UNSTABLE | HS_EXACT_ROUNDING | HS_SCHED_FULL | HS_FIXED64 | HS_VARKAPPA | HS_FP64_PIPE;
@@ -540,7 +541,8 @@ int do_part(hs_heat* h, Part p, cudaStream_t s = nullptr)
 // the handle's stream while heat_time_interior is on.
 int timed_interior(hs_heat* h)
 {
-    if (!h->timing) return do_part(h, P_INTERIOR);
+    // past kMaxTimedLaunches unread records the launches go untimed
+    if (!h->timing || h->tev_used >= kMaxTimedLaunches) return do_part(h, P_INTERIOR);
     const size_t i = 2 * h->tev_used;
     while (h->tev.size() < i + 2) {
         cudaEvent_t e;

@@ -29,16 +29,18 @@ namespace hcg {
 int encode_field_map(CUtensorMap* out, void* base, CUtensorMapDataType dt, size_t elem,
                      uint64_t pitch, uint64_t rows, uint64_t planes, uint32_t box_x, uint32_t box_y)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once, under the thread-safe initialisation of a local static
+    // (CG solves on several host threads encode maps concurrently)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                         cudaEnableDefault, &q);
-        if (e != cudaSuccess) return (int)e;
-        if (q != cudaDriverEntryPointSuccess || !fn) return (int)cudaErrorNotSupported;
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                               cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess)
+                   ? (PFN_cuTensorMapEncodeTiled_v12000)fn
+                   : (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
+    if (!encode) return (int)cudaErrorNotSupported;
     const cuuint64_t dims[3] = {pitch, rows, planes};
     const cuuint64_t strides[2] = {pitch * elem, pitch * rows * elem};
     const cuuint32_t box[3] = {box_x, box_y, 1};
