@@ -314,8 +314,8 @@ int cg_run(hs_cg_t c, const void* b, void* x, int host_buffers, double rtol, int
  * iterations (max_iter bounds them) and info->refinements the inner solves.
  * A CSR operator's values are rounded to an FP32 copy the context owns.
  * Refinement converges while cond(A) times 2^-24 is well below one.  Use
- * cg_run and cg_destroy as for cg_create.  (The precision split follows the
- * spec extension of the paper's FP64 CG of Section 7.5.) */
+ * cg_run and cg_destroy as for cg_create.  (The precision split extends the
+ * paper's FP64 CG of Section 7.5.) */
 int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, void* stream);
 
 /* Release a CG context (synchronises its stream). */
