@@ -52,3 +52,11 @@ def test_version_and_error_string_without_gpu():
     desc.flags = nat.HS_FP64_PIPE   # the FP64-pipe arithmetic keeps no per-step state
     assert nat.lib.heat_device_bytes(ctypes.byref(desc), ctypes.byref(size)) == 0
     assert size.value == 2 * 6 * 6 * 16 * 8
+
+
+def test_timing_entry_points_reject_null_handles():
+    from paper_2608_11882_gb300 import _native as nat
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    assert nat.lib.heat_time_interior(None, 1) == nat.HS_EINVAL
+    assert nat.lib.heat_interior_time(None, ctypes.byref(ms), ctypes.byref(n)) == nat.HS_EINVAL
+    assert "NULL handle" in nat.last_error()
