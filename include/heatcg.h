@@ -121,17 +121,36 @@ typedef struct {
                               kernels every step, or 2, 3, 4 = temporal
                               blocking (see heat_step)                     */
     void*    stream;       /* cudaStream_t for all work of this handle        */
+    void*    dev_buf0;     /* optional caller-owned device buffers for the two
+                              time levels (for example torch allocations):
+                              both NULL (the library allocates them) or both
+                              set, distinct, non-overlapping, 256-byte aligned
+                              and each at least heat_buffer_bytes(desc) long */
+    void*    dev_buf1;
 } hs_heat_desc;
 
-/* Create a heat handle (Algorithm "1-GPU Baseline", setup and allocation).
- * Allocates two device buffers of (nz+2) planes x (ny+2) rows x pitch
- * elements; their boundary layer is zero and is never written again, so the
- * Dirichlet data survive every buffer swap.  Both buffers start all zero.
+/* Create a heat handle (Algorithm "1-GPU Baseline", setup and allocation:
+ * the two time levels u_old and u_new).  Uses two device buffers of (nz+2)
+ * planes x (ny+2) rows x pitch elements -- the caller's dev_buf0/dev_buf1 when
+ * given, else its own allocations; it zeroes both (on the handle's stream), so
+ * their boundary layer holds the Dirichlet zeros, which are never written
+ * again and so survive every buffer swap.  Caller-owned buffers stay the
+ * caller's: the handle never frees them, and they must outlive it.
  * Errors: HS_EINVAL (desc NULL, a size < 1, r < 0 or not finite, unknown flag
- * or dtype), HS_EUNSTABLE (r > 1/6 without HS_ALLOW_UNSTABLE), HS_ENOMEM. */
+ * or dtype; caller buffers not both given, equal, overlapping or misaligned),
+ * HS_EUNSTABLE (r > 1/6 without HS_ALLOW_UNSTABLE), HS_ENOMEM. */
 int heat_create(hs_heat_t* out, const hs_heat_desc* desc);
 
-/* Device bytes heat_create would allocate for desc (for admission control). */
+/* Bytes of ONE padded field buffer for desc: (nz+2) (ny+2) pitch elements of
+ * the dtype, pitch = the interior row plus its boundary cells and a 32-byte
+ * lead, rounded up to 128 bytes (the layout the kernels index; Section 6.1's
+ * padded arrays).  The size a caller-owned dev_buf0/dev_buf1 must have. */
+int heat_buffer_bytes(const hs_heat_desc* desc, size_t* bytes);
+
+/* Device bytes heat_create would allocate for desc (for admission control):
+ * the two field buffers unless the caller supplies them, and the per-step
+ * state of the exact-sum and FIXED64 arithmetics (and kappa, dt f for
+ * HS_VARKAPPA). */
 int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
 
 /* Load the interior field u (nx*ny*nz elements of the handle's dtype, x
@@ -184,7 +203,8 @@ int heat_swap(hs_heat_t h);
 int heat_time_interior(hs_heat_t h, int enable);
 int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches);
 
-/* Copy the current interior field to dst (nx*ny*nz elements, x fastest):
+/* Copy the current interior field to dst (Algorithm "1-GPU Baseline", the
+ * device-to-host copy of the result after the time loop; nx*ny*nz elements, x fastest):
  * host memory if dst_is_device == 0 (one strided copy), device memory
  * otherwise (a re-layout kernel).  Synchronises the handle's stream and
  * reports any asynchronous error. */
@@ -197,7 +217,9 @@ int heat_steps_done(hs_heat_t h, int64_t* steps);
  * + Boundary kernels every step, L >= 2 = L steps per pass). */
 int heat_get_tdepth(hs_heat_t h, int32_t* tdepth);
 
-/* Release the handle and its device buffers (synchronises its stream). */
+/* Release the handle (Algorithm "1-GPU Baseline", freeing the device arrays
+ * after the time loop): synchronises its stream and frees what the library
+ * allocated; caller-owned dev_buf0/dev_buf1 are left to the caller. */
 int heat_destroy(hs_heat_t h);
 
 /* ---- batched heat stepping ---------------------------------------------- */
@@ -228,6 +250,17 @@ int heat_batch_run(hs_batch_t b, int use_graph);
 
 /* Synchronise the batch stream; HS_ETIMEOUT if a bounded wait ran out. */
 int heat_batch_wait(hs_batch_t b);
+
+/* The limit, in SM clock cycles, of the bounded step wait of batches created
+ * after this call (0 restores the default of about one second at GB300
+ * clocks).  A wait that runs out makes the run stop early: every block
+ * finishes the item it holds and takes no other, heat_batch_wait returns
+ * HS_ETIMEOUT, and the grids' fields are not valid until they are uploaded
+ * again.  Nothing else is affected: the handles, the batch and the CUDA
+ * context stay usable.  Meant for tests of that error path (a limit of a few
+ * cycles makes a multi-step batch's waits run out).  Errors: HS_EINVAL for a
+ * negative limit. */
+int heat_batch_set_wait_limit(int64_t cycles);
 
 /* Lattice-point updates per run, and blocks of the persistent launch. */
 int heat_batch_info(hs_batch_t b, int64_t* lups, int32_t* blocks);
@@ -274,6 +307,32 @@ typedef struct hs_cg* hs_cg_t;
  * for CSR).  p and y are device arrays of n FP64 values; A's arrays must be
  * device memory (host == 0). */
 int op_apply(const hs_op* A, const void* p, void* y, void* stream);
+
+/* One SpMV of a CG iteration on its own: q = A p fused with the dot product
+ * p.q (Section 7.5; Algorithm "spmv" (b) for CSR), through exactly one launch
+ * of the kernel named by `kernel`, with the block count and work order cg_run
+ * uses for A, so q and p.q are bit for bit what that kernel computes inside a
+ * solve.  p's scale (its largest exponent, which the exact-sum kernels read)
+ * is taken from p first, as the kernels that form p record it during a solve.
+ *   HS_SPMV_AUTO    the kernel cg_run picks for A, p and q;
+ *   HS_SPMV_ROWS    one row per thread in FP64 arithmetic (matrix-free: the
+ *                   sum ((zm + ym) + (xm + xp)) + (yp + zp), then
+ *                   fma(6, p, -sum); CSR: the row loop with FMA);
+ *   HS_SPMV_STAGED  matrix-free only: planes staged in shared memory by
+ *                   loads, the exact-sum arithmetic described at cg_run;
+ *   HS_SPMV_TMA     matrix-free only: the same, planes staged by TMA; needs
+ *                   nx even and p, q 16-byte aligned (else HS_EINVAL).
+ * The staged kernels accept any grid size here (cg_run takes them only from
+ * about 160^3 up).  p and q are device arrays of n FP64 values that must not
+ * overlap; A's arrays must be device memory.  pq (may be NULL) receives p.q.
+ * Allocates a few kilobytes of scratch on the stream, synchronises the stream.
+ * Errors: HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT (a bounded wait of the
+ * TMA-staged kernel ran out). */
+#define HS_SPMV_AUTO   0
+#define HS_SPMV_ROWS   1
+#define HS_SPMV_STAGED 2
+#define HS_SPMV_TMA    3
+int cg_spmv(const hs_op* A, const void* p, void* q, int kernel, double* pq, void* stream);
 
 /* Create a CG context: checks A, takes a device copy of A's arrays when
  * A->host == 1 (otherwise it keeps A's device pointers, which must outlive
@@ -335,7 +394,9 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
                  int32_t max_iter, hs_cg_info* infos);
 int cg_batch_destroy(hs_cg_batch_t b);
 
-/* One-shot form: cg_create + cg_run (device b and x) + cg_destroy. */
+/* One-shot form of the CG solve of Section 7.5 (textbook unpreconditioned
+ * CG, stopping on ||r_k|| / ||b|| <= rtol): cg_create + cg_run (device b and
+ * x) + cg_destroy. */
 int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_iter,
              hs_cg_info* info, void* stream);
 
@@ -367,7 +428,10 @@ int cg_solve_noalloc(const hs_op* A, const void* b, void* x, double rtol, int32_
                      hs_cg_info* info, void* stream);
 
 /* ---- misc ---------------------------------------------------------------- */
-/* Message describing the last error on the calling thread ("" if none). */
+/* Message describing the last error on the calling thread ("" if none).  The
+ * paper judges a run by comparing its result with a CPU reference (Section
+ * 6.1.7) and has no error interface; this string and the HS_E* codes are the
+ * library's own. */
 const char* hs_last_error(void);
 /* Library ABI version (major*10000 + minor*100 + patch). */
 int hs_version(void);

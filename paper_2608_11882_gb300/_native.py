@@ -15,6 +15,7 @@ HS_F64, HS_F32 = 0, 1
 HS_ALLOW_UNSTABLE, HS_EXACT_ROUNDING, HS_SCHED_FULL, HS_FIXED64, HS_VARKAPPA = 0x1, 0x2, 0x4, 0x8, 0x10
 HS_FP64_PIPE = 0x20
 HS_OP_STENCIL7, HS_OP_CSR = 0, 1
+HS_SPMV_AUTO, HS_SPMV_ROWS, HS_SPMV_STAGED, HS_SPMV_TMA = 0, 1, 2, 3
 
 _CODE_NAMES = {HS_EINVAL: "HS_EINVAL", HS_ENOMEM: "HS_ENOMEM", HS_ECUDA: "HS_ECUDA",
                HS_EUNSTABLE: "HS_EUNSTABLE", HS_ENOCONV: "HS_ENOCONV", HS_ETIMEOUT: "HS_ETIMEOUT",
@@ -30,7 +31,8 @@ class HeatCGError(RuntimeError):
 class hs_heat_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("r", ctypes.c_double), ("flags", ctypes.c_uint32), ("dtype", ctypes.c_int32),
-                ("tdepth", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("tdepth", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("dev_buf0", ctypes.c_void_p), ("dev_buf1", ctypes.c_void_p)]
 
 
 class hs_op(ctypes.Structure):
@@ -60,6 +62,7 @@ def _load():
     sig = {
         "heat_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_heat_desc)],
         "heat_device_bytes": [ctypes.POINTER(hs_heat_desc), ctypes.POINTER(ctypes.c_size_t)],
+        "heat_buffer_bytes": [ctypes.POINTER(hs_heat_desc), ctypes.POINTER(ctypes.c_size_t)],
         "heat_upload": [vp, vp, ctypes.c_int],
         "heat_step": [vp, i64],
         "heat_interior": [vp],
@@ -72,11 +75,13 @@ def _load():
         "heat_get_tdepth": [vp, ctypes.POINTER(i32)],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
+        "cg_spmv": [ctypes.POINTER(hs_op), vp, vp, ctypes.c_int, ctypes.POINTER(dbl), vp],
         "heat_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64), i32, vp],
         "heat_batch_run": [vp, ctypes.c_int],
         "heat_batch_wait": [vp],
         "heat_batch_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "heat_batch_destroy": [vp],
+        "heat_batch_set_wait_limit": [i64],
         "cg_create": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), vp],
         "cg_create_mixed": [ctypes.POINTER(vp), ctypes.POINTER(hs_op), ctypes.POINTER(hs_cg_mixed_opts), vp],
         "cg_run": [vp, vp, vp, ctypes.c_int, dbl, i32, ctypes.POINTER(hs_cg_info)],
@@ -126,6 +131,12 @@ def heat_create(desc: hs_heat_desc) -> int:
 def heat_device_bytes(desc: hs_heat_desc) -> int:
     b = ctypes.c_size_t()
     check(lib.heat_device_bytes(ctypes.byref(desc), ctypes.byref(b)), "heat_device_bytes")
+    return b.value
+
+
+def heat_buffer_bytes(desc: hs_heat_desc) -> int:
+    b = ctypes.c_size_t()
+    check(lib.heat_buffer_bytes(ctypes.byref(desc), ctypes.byref(b)), "heat_buffer_bytes")
     return b.value
 
 
@@ -202,12 +213,23 @@ def heat_batch_info(b: int):
     return lups.value, blocks.value
 
 
+def heat_batch_set_wait_limit(cycles: int) -> None:
+    check(lib.heat_batch_set_wait_limit(int(cycles)), "heat_batch_set_wait_limit")
+
+
 def heat_batch_destroy(b: int) -> None:
     check(lib.heat_batch_destroy(b), "heat_batch_destroy")
 
 
 def op_apply(op: hs_op, p_ptr: int, y_ptr: int, stream: int = 0) -> None:
     check(lib.op_apply(ctypes.byref(op), p_ptr, y_ptr, stream), "op_apply")
+
+
+def cg_spmv(op: hs_op, p_ptr: int, q_ptr: int, kernel: int = HS_SPMV_AUTO, stream: int = 0) -> float:
+    """q = A p through one SpMV launch of the named kernel; returns p.q."""
+    pq = ctypes.c_double()
+    check(lib.cg_spmv(ctypes.byref(op), p_ptr, q_ptr, int(kernel), ctypes.byref(pq), stream), "cg_spmv")
+    return pq.value
 
 
 def cg_create(op: hs_op, stream: int = 0) -> int:

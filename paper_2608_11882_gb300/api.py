@@ -47,9 +47,12 @@ class Heat:
     """A resident heat field (heat_create / heat_upload / heat_step / heat_read)."""
 
     def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
-                 stream=None, tdepth=0):
+                 stream=None, tdepth=0, buffers=None):
         """tdepth: steps per pass (0 = the library's default, 1..4), or "auto" for
-        the autotuner's cached or freshly measured choice for this shape."""
+        the autotuner's cached or freshly measured choice for this shape.
+        buffers: optional pair of caller-owned CUDA tensors for the two padded
+        time levels (each at least ``Heat.buffer_bytes(...)`` bytes); the
+        handle keeps references to them while it lives."""
         self.shape = (nz, ny, nx)
         self.dtype_code, self.np_dtype = _DTYPES[dtype]
         if tdepth == "auto":
@@ -60,7 +63,20 @@ class Heat:
         self.stream = _stream_handle(stream)
         desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,
                                    tdepth=tdepth, stream=self.stream)
+        self._buffers = None
+        if buffers is not None:
+            b0, b1 = buffers
+            if not (b0.is_cuda and b1.is_cuda):
+                raise ValueError("caller-owned heat buffers must be CUDA tensors")
+            desc.dev_buf0, desc.dev_buf1 = b0.data_ptr(), b1.data_ptr()
+            self._buffers = (b0, b1)
         self.handle = native.heat_create(desc)
+
+    @staticmethod
+    def buffer_bytes(nx: int, ny: int, nz: int, dtype: str = "f64") -> int:
+        """Bytes of one padded time-level buffer (heat_buffer_bytes)."""
+        desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=0.0, flags=0, dtype=_DTYPES[dtype][0])
+        return native.heat_buffer_bytes(desc)
 
     @property
     def count(self) -> int:
@@ -217,6 +233,18 @@ class Operator:
             raise ValueError("op_apply takes device tensors")
         native.op_apply(self.op, pp, yp, _stream_handle(stream))
         return y
+
+    _SPMV_KERNELS = {"auto": native.HS_SPMV_AUTO, "rows": native.HS_SPMV_ROWS,
+                     "staged": native.HS_SPMV_STAGED, "tma": native.HS_SPMV_TMA}
+
+    def spmv(self, p, q, kernel: str = "auto", stream=None) -> float:
+        """q = A p through one launch of the SpMV kernel a CG iteration runs
+        ("auto": the one cg_run picks; "rows", "staged", "tma"); returns p.q."""
+        pp, pd, _ = _buffer(p, np.float64, self.n)
+        qp, qd, _ = _buffer(q, np.float64, self.n)
+        if not (pd and qd):
+            raise ValueError("cg_spmv takes device tensors")
+        return native.cg_spmv(self.op, pp, qp, self._SPMV_KERNELS[kernel], _stream_handle(stream))
 
 
 class CG:

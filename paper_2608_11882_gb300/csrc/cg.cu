@@ -160,6 +160,18 @@ __global__ void __launch_bounds__(kCgBlock)
     if (track_pmax) cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
 }
 
+// Largest |p| high word into S->pmax[0] (the direction's scale the
+// matrix-free SpMV of iteration 0 reads), for cg_spmv.
+__global__ void __launch_bounds__(kCgBlock)
+    k_cg_pmax(int64_t n, const double* __restrict__ p, CgScalars* S)
+{
+    unsigned pm = 0;
+    for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * kCgBlock)
+        pm = max(pm, xs_abs_hi(p[t]));
+    cg_fold_pmax(pm, S, 0, false);
+}
+
 // ||b - q||^2 into S->rr_true (q = A x).
 __global__ void __launch_bounds__(kCgBlock)
     k_resid_norm(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
@@ -252,6 +264,87 @@ int op_apply(const hs_op* A, const void* p, void* y, void* stream)
     if (A->host) return fail(HS_EINVAL, "op_apply: operator arrays must be device memory");
     if (!p || !y) return fail(HS_EINVAL, "op_apply: NULL vector");
     return launch_apply(to_dev(A), (const double*)p, (double*)y, (cudaStream_t)stream);
+}
+
+int cg_spmv(const hs_op* A, const void* p, void* q, int kernel, double* pq, void* stream)
+{
+    int rc = check_op(A);
+    if (rc != HS_OK) return rc;
+    if (A->host) return fail(HS_EINVAL, "cg_spmv: operator arrays must be device memory");
+    if (!p || !q) return fail(HS_EINVAL, "cg_spmv: NULL vector");
+    if (p == q) return fail(HS_EINVAL, "cg_spmv: p and q must not overlap");
+    const OpDev D = to_dev(A);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int grid = grid_for(D.n);   // the block count cg_run uses for this operator
+    const bool stencil = D.kind == HS_OP_STENCIL7;
+    int mode = 0;
+    bool tma = false;
+    switch (kernel) {
+    case HS_SPMV_AUTO:
+        mode = spmv_mode(D, grid);
+        tma = mode == SP_STAGED && spmv_tma_eligible(D, (const double*)p, (const double*)q, grid);
+        break;
+    case HS_SPMV_ROWS:
+        mode = stencil ? SP_ROWS : SP_CSR;
+        break;
+    case HS_SPMV_STAGED:
+    case HS_SPMV_TMA:
+        if (!stencil) return fail(HS_EINVAL, "cg_spmv: the staged kernels take the matrix-free operator only");
+        mode = SP_STAGED;
+        tma = kernel == HS_SPMV_TMA;
+        if (tma && ((D.nx & 1) || ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15)))
+            return fail(HS_EINVAL, "cg_spmv: the TMA-staged kernel needs an even nx and 16-byte aligned p and q");
+        break;
+    default:
+        return fail(HS_EINVAL, "cg_spmv: unknown kernel %d", kernel);
+    }
+    CUtensorMap pmap;
+    if (tma) {
+        const int e = spmv_tma_map(&pmap, D, (const double*)p);
+        if (e != 0) return cuda_fail((cudaError_t)e, "cg_spmv: TMA tensor map");
+    }
+    // scratch: the reduction partials and the device scalars of one iteration
+    void* scratch = nullptr;
+    const size_t pbytes = sizeof(double) * 2 * (size_t)grid;
+    HS_TRY_CUDA(dev_alloc(&scratch, pbytes + sizeof(CgScalars), s), "cg_spmv: device allocation");
+    double* partials = (double*)scratch;
+    CgScalars* S = (CgScalars*)((char*)scratch + pbytes);
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    init.rho = 1.0;   // alpha = 1 / p.q: unused here
+    cudaError_t e = cudaMemcpyAsync(S, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        // p's scale, exactly as the kernels that form p record it in a solve
+        k_cg_pmax<<<grid, kCgBlock, 0, s>>>(D.n, (const double*)p, S);
+        e = cudaPeekAtLastError();
+        if (e == cudaSuccess) count_launch();
+    }
+    if (e == cudaSuccess) {
+        if (tma) {
+            rc = spmv_tma_launch(pmap, D, (double*)q, partials, S, grid, s);
+        } else {
+            auto kern = mode == SP_STAGED ? k_cg_spmv_dot<SP_STAGED>
+                        : mode == SP_CSR  ? k_cg_spmv_dot<SP_CSR>
+                                          : k_cg_spmv_dot<SP_ROWS>;
+            e = launch_dependent(kern, grid, kCgBlock, s, D, (const double*)p, (double*)q, partials, S);
+            rc = e == cudaSuccess ? HS_OK : cuda_fail(e, "cg_spmv: kernel launch");
+            e = cudaSuccess;
+        }
+        if (rc == HS_OK) count_launch();
+    }
+    CgScalars out;
+    memset(&out, 0, sizeof(out));
+    if (e == cudaSuccess && rc == HS_OK) e = cudaMemcpyAsync(&out, S, sizeof(out), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && rc == HS_OK) e = cudaStreamSynchronize(s);
+    dev_free(scratch, s);
+    if (rc != HS_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cg_spmv");
+    if (out.done == 3) return fail(HS_ETIMEOUT, "cg_spmv: a bounded wait in the TMA-staged SpMV ran out");
+    if (out.done == 4)
+        return fail(HS_ECUDA, "cg_spmv: a bounded wait in the TMA-staged SpMV ran out and its loads in "
+                              "flight did not complete in time; treat the CUDA context as suspect");
+    if (pq) *pq = out.pq;
+    return HS_OK;
 }
 
 int cg_destroy(hs_cg_t c)
@@ -436,6 +529,9 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     const bool converged = (f.done == 1);
     if (f.done == 2) return fail(HS_ECUDA, "cg_run: breakdown, p.q <= 0 (operator not positive definite?)");
     if (f.done == 3) return fail(HS_ETIMEOUT, "cg_run: a bounded wait in the TMA-staged SpMV ran out");
+    if (f.done == 4)
+        return fail(HS_ECUDA, "cg_run: a bounded wait in the TMA-staged SpMV ran out and its loads in "
+                              "flight did not complete in time; treat the CUDA context as suspect");
     if (info) {
         info->iters = f.iters;
         info->relres_recur = f.relres;

@@ -21,7 +21,8 @@ struct CgScalars {
     double relres;     // sqrt(rho)/||b|| at the last check
     double rr_true;    // ||b - A x||^2 at exit
     int32_t done;      // 1: converged (or nothing to do); 2: breakdown (p.q <= 0);
-                       // 3: a bounded wait of the TMA-staged SpMV ran out
+                       // 3: a bounded wait of the TMA-staged SpMV ran out; 4: that,
+                       // and the block's loads in flight did not complete in time
     int32_t iters;
     uint32_t ticket;   // blocks finished in the running reduction
     int32_t zero_rhs;  // ||b|| == 0

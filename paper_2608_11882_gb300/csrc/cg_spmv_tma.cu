@@ -23,7 +23,9 @@
 //
 // Each mbarrier wait is bounded (about a second); one that runs out marks the
 // solve with done = 3 (HS_ETIMEOUT on the host), waits (bounded) for the
-// block's loads in flight and ends the block.
+// block's loads in flight and ends the block.  If that wait runs out as well,
+// loads may still land in shared memory a later block reuses: done = 4, which
+// the host reports as HS_ECUDA with the context to be treated as suspect.
 #include <cuda.h>
 
 #include "cg_common.cuh"
@@ -53,7 +55,8 @@ template <bool CONV>
 __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const OpDev& A,
                                                 double* __restrict__ q, int emax, const SpmvPlan& P,
                                                 int64_t tile, int kb, int ke, long long* stage,
-                                                uint64_t* bars, uint32_t& seq, bool& aborted)
+                                                uint64_t* bars, uint32_t& seq, bool& aborted,
+                                                bool& drained)
 {
     constexpr int V = 2, BW = kSpBW, NST = kSpNst;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -202,7 +205,10 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
         // before the block may end
         const long long t0 = clock64();   // one time budget for the whole drain
         for (int j = issued > NST ? issued - NST : 0; j < issued; ++j)
-            (void)mbar_wait_until(&bars[(seq + j) % NST], ((seq + j) / NST) & 1u, t0, kWaitCycles);
+            if (!mbar_wait_until(&bars[(seq + j) % NST], ((seq + j) / NST) & 1u, t0, kWaitCycles)) {
+                drained = false;   // loads may still be landing: the context is suspect
+                break;
+            }
     }
     seq += (uint32_t)np;
     return pq;
@@ -230,18 +236,19 @@ __global__ void __launch_bounds__(kCgBlock, 4)
     const bool conv = cg_xs_ok(emax);
     const SpmvPlan P = spmv_plan(A, gridDim.x);
     uint32_t seq = 0;
-    bool aborted = false;
+    bool aborted = false, drained = true;
     double pq = 0.0;
     for (int64_t item = blockIdx.x; item < P.items; item += gridDim.x) {
         const int64_t tile = item % P.tiles;
         const int kb = (int)(item / P.tiles) * P.kc;
         const int ke = min(kb + P.kc, A.nz);
-        pq += conv ? spmv_item_tma<true>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted)
-                   : spmv_item_tma<false>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted);
+        pq += conv ? spmv_item_tma<true>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained)
+                   : spmv_item_tma<false>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained);
         if (aborted) break;   // the same in every thread
     }
     if (aborted) {
-        if (tid == 0) atomicExch(reinterpret_cast<int*>(&S->done), 3);
+        // 3: a wait ran out; 4: so did the wait for this block's loads in flight
+        if (tid == 0) atomicMax(reinterpret_cast<int*>(&S->done), drained ? 3 : 4);
         return;
     }
     allow_dependents();

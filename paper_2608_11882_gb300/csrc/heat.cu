@@ -296,6 +296,7 @@ struct hs_heat {
     uint32_t flags;
     cudaStream_t stream;
     void* buf[2];
+    bool owns_buf;     // false: buf[] are the caller's dev_buf0/dev_buf1
     FxState* fx;       // FIXED64 only
     int* err;          // device error word: 1 when a bounded device wait ran out
     int cur;           // buffer holding the current time level
@@ -378,6 +379,21 @@ int check_desc(const hs_heat_desc* d)
 }
 
 size_t elem_size(int dtype) { return dtype == HS_F64 ? sizeof(double) : sizeof(float); }
+
+// Caller-owned time-level buffers: both or neither, distinct, not
+// overlapping, 256-byte aligned (TMA and the 16-byte vector accesses need
+// less; every CUDA allocator gives this).
+int check_user_buffers(const hs_heat_desc* d, size_t bytes)
+{
+    if (!d->dev_buf0 && !d->dev_buf1) return HS_OK;
+    if (!d->dev_buf0 || !d->dev_buf1)
+        return fail(HS_EINVAL, "heat: give both dev_buf0 and dev_buf1, or neither");
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d->dev_buf0), b = reinterpret_cast<uintptr_t>(d->dev_buf1);
+    if ((a | b) & 255) return fail(HS_EINVAL, "heat: dev_buf0 and dev_buf1 must be 256-byte aligned");
+    if ((a < b ? b - a : a - b) < bytes)
+        return fail(HS_EINVAL, "heat: dev_buf0 and dev_buf1 overlap (each needs %zu bytes)", bytes);
+    return HS_OK;
+}
 
 // Plain FP64 runs the exact-sum arithmetic, except where a kernel has only the
 // FP64-pipe form: temporal blocking and the variable-coefficient problem.
@@ -584,9 +600,10 @@ int pick_kc_stream(const HeatGeom& g, int arith)
     const int ry = stream_rows_for(arith);
     const int64_t tiles = (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + ry - 1) / ry);
     // about four waves of 3 blocks of 16 rows per SM; the exact-sum kernel (8 rows,
-    // 5 resident blocks per SM) gets 16 blocks per SM, about 3.4 waves -- measured
-    // ahead of 4 waves of shorter chunks and 2 waves of longer ones
-    const int64_t target = (int64_t)kNumSMs * (arith == A_F64_XS ? 4 : 3) * 4;
+    // 8 resident blocks of 128 threads per SM) gets 64 blocks per SM, about 8
+    // waves of 27-plane chunks at 512^3 -- measured ahead of 4 waves of longer
+    // chunks and 12 waves of shorter ones
+    const int64_t target = (int64_t)kNumSMs * (arith == A_F64_XS ? 16 : 3) * 4;
     const int64_t planes = g.nz > 2 ? g.nz - 2 : 1;
     int64_t chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
@@ -731,13 +748,24 @@ int heat_batch_advance(hs_heat_t h, int64_t steps)
 
 extern "C" {
 
+int heat_buffer_bytes(const hs_heat_desc* desc, size_t* bytes)
+{
+    int rc = check_desc(desc);
+    if (rc != HS_OK) return rc;
+    if (!bytes) return fail(HS_EINVAL, "heat_buffer_bytes: bytes is NULL");
+    const HeatGeom g = make_geom(desc->nx, desc->ny, desc->nz, elem_size(desc->dtype));
+    *bytes = (size_t)g.total * elem_size(desc->dtype);
+    return HS_OK;
+}
+
 int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
 {
     int rc = check_desc(desc);
     if (rc != HS_OK) return rc;
     if (!bytes) return fail(HS_EINVAL, "heat_device_bytes: bytes is NULL");
     const HeatGeom g = make_geom(desc->nx, desc->ny, desc->nz, elem_size(desc->dtype));
-    *bytes = 2 * (size_t)g.total * elem_size(desc->dtype);
+    const bool user_bufs = desc->dev_buf0 || desc->dev_buf1;
+    *bytes = user_bufs ? 0 : 2 * (size_t)g.total * elem_size(desc->dtype);
     const Arith a = pick_arith(desc);
     if (a == A_FX64 || a == A_F64_XS) *bytes += sizeof(FxState);
     if (desc->flags & HS_VARKAPPA) *bytes += 2 * (size_t)g.total * elem_size(desc->dtype);
@@ -769,8 +797,19 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     h->tdepth = desc->tdepth ? desc->tdepth : default_tdepth(h->arith);
     if (h->flags & HS_SCHED_FULL) h->tdepth = 1;
     const size_t bytes = (size_t)h->g.total * h->elem;
+    rc = check_user_buffers(desc, bytes);
+    if (rc != HS_OK) {
+        delete h;
+        return rc;
+    }
+    h->owns_buf = !desc->dev_buf0;
     for (int b = 0; b < 2; ++b) {
-        cudaError_t e = dev_alloc(&h->buf[b], bytes, h->stream);
+        cudaError_t e = cudaSuccess;
+        if (h->owns_buf) {
+            e = dev_alloc(&h->buf[b], bytes, h->stream);
+        } else {
+            h->buf[b] = b == 0 ? desc->dev_buf0 : desc->dev_buf1;
+        }
         if (e != cudaSuccess) {
             h->buf[b] = nullptr;
             rc = cuda_fail(e, "heat_create: device allocation");
@@ -1040,9 +1079,13 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device)
     HS_TRY_CUDA(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
                 "heat_read: error word");
     HS_TRY_CUDA(cudaStreamSynchronize(h->stream), "heat_read: stream synchronize");
+    if (err == 2)
+        return fail(HS_ECUDA, "heat_read: a bounded wait inside a TMA-staged heat kernel ran out and "
+                              "the block's loads in flight did not complete in time; the field is not "
+                              "valid and the CUDA context should be treated as suspect");
     if (err)
-        return fail(HS_ETIMEOUT, "heat_read: a bounded wait inside the temporally blocked kernel "
-                                 "ran out; the field is not valid");
+        return fail(HS_ETIMEOUT, "heat_read: a bounded wait inside a TMA-staged heat kernel ran out; "
+                                 "the field is not valid");
     if (h->arith == A_FX64) {
         FxState st;
         HS_TRY_CUDA(cudaMemcpyAsync(&st, h->fx, sizeof(st), cudaMemcpyDeviceToHost, h->stream),
@@ -1085,7 +1128,8 @@ int heat_destroy(hs_heat_t h)
     for (cudaEvent_t e : h->tev) (void)cudaEventDestroy(e);
     if (h->ev_fork) (void)cudaEventDestroy(h->ev_fork);
     if (h->ev_join) (void)cudaEventDestroy(h->ev_join);
-    for (int b = 0; b < 2; ++b) dev_free(h->buf[b], h->stream);
+    if (h->owns_buf)
+        for (int b = 0; b < 2; ++b) dev_free(h->buf[b], h->stream);
     dev_free(h->fx, h->stream);
     dev_free(h->err, h->stream);
     dev_free(h->kap, h->stream);

@@ -10,7 +10,9 @@
 // and Boundary work of one step of Section 4's update, over the whole grid.
 // Items of step m-1 always come earlier in the order, so they have been taken
 // by running blocks and the wait ends; it is still bounded (about a second of
-// SM clock), after which the kernel records HS_ETIMEOUT and stops.
+// SM clock unless heat_batch_set_wait_limit set another limit before the batch
+// was created), after which the kernel records HS_ETIMEOUT and stops: blocks
+// finish the item they hold and take no further one.
 //
 // Loads use ld.global.cg (L2 only): a block must never see another SM's
 // freshly written plane through its own stale L1 lines.
@@ -21,6 +23,7 @@
 // let step m start; each tile adds its outputs' maximum to slot (m3 + m + 1) % 3,
 // and tile 0 clears slot (m3 + m + 2) % 3, which no unfinished item reads.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -30,7 +33,9 @@
 namespace hcg {
 
 constexpr int kBatchBX = 32, kBatchBY = 8;
-constexpr long long kBatchWaitCycles = 2000000000ll;
+constexpr long long kBatchWaitCycles = 2000000000ll;   // about one second at GB300 clocks
+// Wait limit that batches created from now on get (heat_batch_set_wait_limit).
+static std::atomic<long long> g_batch_wait_cycles{kBatchWaitCycles};
 
 enum BatchKind { K_F64_PIPE = 0, K_F32 = 1, K_F64_XS = 2 };
 
@@ -58,6 +63,7 @@ struct BatchDev {
     unsigned long long* done;     // per grid: tiles completed, all steps
     int* err;
     int64_t items;
+    long long wait_cycles;        // limit of the step wait, in SM clock cycles
     int32_t max_steps;
 };
 
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
             const unsigned long long need = (unsigned long long)m * (unsigned long long)G.tiles;
             const long long t0 = clock64();
             while (*(volatile unsigned long long*)&B.done[gi] < need) {
-                if (clock64() - t0 > kBatchWaitCycles) {
+                if (clock64() - t0 > B.wait_cycles) {
                     atomicExch(B.err, 1);
                     s_abort = 1;
                     break;
@@ -313,6 +319,7 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
     b->dev.done = ctr + 1;
     b->dev.err = (int*)(ctr + 1 + n);
     b->dev.items = items;
+    b->dev.wait_cycles = g_batch_wait_cycles.load();
     b->dev.max_steps = (int32_t)(max_steps > 0 ? max_steps : 1);
     // persistent grid: every block resident at once
     int per_sm = 0;
@@ -413,6 +420,13 @@ int heat_batch_wait(hs_batch_t b)
                 "heat_batch_wait: status");
     HS_TRY_CUDA(cudaStreamSynchronize(b->stream), "heat_batch_wait: synchronize");
     if (err) return fail(HS_ETIMEOUT, "heat_batch_wait: a bounded wait in the batch kernel ran out");
+    return HS_OK;
+}
+
+int heat_batch_set_wait_limit(int64_t cycles)
+{
+    if (cycles < 0) return fail(HS_EINVAL, "heat_batch_set_wait_limit: cycles < 0");
+    g_batch_wait_cycles.store(cycles ? (long long)cycles : kBatchWaitCycles);
     return HS_OK;
 }
 

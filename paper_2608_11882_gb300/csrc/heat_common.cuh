@@ -298,10 +298,13 @@ inline T stream_param(const StreamCall& c)
 int stream_launch(const StreamCall& c);
 // TMA box (elements x rows) the streaming kernel loads for an arithmetic.
 int stream_box(int arith, uint32_t* box_x, uint32_t* box_y);
-// Rows of the streaming kernels' tiles (a tile is 32 threads x rows): 16 for
-// k_heat_stream, kXsRows for the exact-sum FP64 kernel.
+// Rows of the streaming kernels' tiles: 16 for k_heat_stream (a thread per
+// row), kXsRows for the exact-sum FP64 kernel (kXsRowsPerThread rows per
+// thread, a ring of kXsStages staged planes).
 constexpr int kStreamRowsHost = 16;
 constexpr int kXsRows = 8;
+constexpr int kXsRowsPerThread = 2;
+constexpr int kXsStages = 4;
 inline int stream_rows_for(int arith) { return arith == A_F64_XS ? kXsRows : kStreamRowsHost; }
 
 // One launch of a variable-coefficient kernel (heat_vk.cu).

@@ -164,7 +164,10 @@ __global__ void __launch_bounds__(32 * RY)
             const long long t0 = clock64();   // one time budget for the whole drain
             for (int p = drain_from; p <= issued; ++p) {
                 const int i = p - p_first;
-                (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
+                if (!mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles)) {
+                    atomicExch(err, 2);   // loads may still be landing: the context is suspect
+                    break;
+                }
             }
         }
         return;
@@ -174,20 +177,25 @@ __global__ void __launch_bounds__(32 * RY)
 }
 
 // ---- FP64 with the exact neighbour sum (A_F64_XS) -------------------------------------
-// The tile, ring, waits and error handling of k_heat_stream, for FP64 fields
-// in the exact-sum arithmetic (heat_common.cuh).  Once plane k+1 has landed,
-// the block converts it in place to fixed point on the field's scale: every
-// thread its own vector (keeping the raw doubles, the centre values of the next
-// iteration), warps 0 and 1 the halo rows, warp 2 the two halo columns, so each
-// staged value is converted once.  Plane k, converted one iteration earlier,
-// gives the in-plane neighbours.  A point then costs the exact integer sum, one
-// conversion back (on the FP64 pipe for a thread's first point, with integer
-// instructions for its second) and one FP64 fused multiply-add.  Converted slots are written
-// through the generic proxy and refilled later by TMA (the async proxy), so
-// every thread fences the async proxy after its conversion stores, before the
-// block barrier that precedes a refill.  CONV = false is the FP64-pipe update
-// on the raw planes, for fields outside the conversion's exponent range.
-template <int RY, int NST, bool CONV>
+// The ring, waits and error handling of k_heat_stream, for FP64 fields in the
+// exact-sum arithmetic (heat_common.cuh).  A block of 32 x (RY / RT) threads
+// owns a 64 x RY tile; every thread two consecutive x points of RT adjacent
+// rows, so the per-plane work of a thread (its waits, barrier, address and
+// loop arithmetic) is shared by 2 RT points, and the y neighbours between its
+// own rows come from its registers.  Once plane k+1 has landed, the block
+// converts it in place to fixed point on the field's scale: every thread its
+// own vectors (keeping the raw doubles, the centre values of the next
+// iteration), warps 0 and 1 the halo rows, warp 2 the two halo columns, so
+// each staged value is converted once.  Plane k, converted one iteration
+// earlier, gives the neighbours from outside the thread's own values.  A point
+// then costs the exact integer sum, one conversion back (on the FP64 pipe for
+// a thread's first point of a row, with integer instructions for its second)
+// and one FP64 fused multiply-add.  Converted slots are written through the
+// generic proxy and refilled later by TMA (the async proxy), so every thread
+// fences the async proxy after its conversion stores, before the block
+// barrier that precedes a refill.  CONV = false is the FP64-pipe update on the
+// raw planes, for fields outside the conversion's exponent range.
+template <int RY, int RT, int NST, bool CONV>
 __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* __restrict__ dst,
                                                const HeatGeom& g, double r, int kb, int ke, int emax,
                                                long long* stage, uint64_t* bars, int& s_abort,
@@ -196,22 +204,23 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     using S = StreamShape<double>;
     constexpr int V = S::V;
     constexpr int BW = S::BW;
+    constexpr int TY = RY / RT;
     constexpr int ROWS = RY + 2;
     constexpr uint32_t BOX_BYTES = ROWS * BW * (uint32_t)sizeof(double);
     constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(double));
-    static_assert(V == 2 && 2 * RY <= 32 && RY >= 3, "warp 2 converts the 2 RY halo-column values");
+    static_assert(V == 2 && RY % RT == 0 && TY >= 3 && 2 * RY <= 32,
+                  "warps 0, 1 convert the halo rows, warp 2 the 2 RY halo-column values");
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * RY;
-    const int X = x0 + V * tx, Y = y0 + ty;
+    const int X = x0 + V * tx, Y0 = y0 + ty * RT;      // this thread's first point
     const int xs = g.lead + x0 - S::D;
-    const int own = (ty + 1) * BW + S::D + V * tx;
-    const bool row_ok = (Y < g.ny);
-    const int nvalid = row_ok ? min(V, g.nx - X) : 0;
+    const int own = (ty * RT + 1) * BW + S::D + V * tx;  // its first point in a stage (row j: + j BW)
+    const int nx_ok = min(V, g.nx - X);                // points per row inside the box
     const int p_first = kb - 1, p_last = ke;
     const double r2 = CONV ? xs_r2(r, emax) : 0.0;
-    // what this thread converts besides its own vector: a vector of halo row 0
+    // what this thread converts besides its own vectors: a vector of halo row 0
     // (warp 0) or RY+1 (warp 1), or one halo-column value (warp 2)
     int extra = -1;
     if (ty == 0) extra = S::D + V * tx;
@@ -219,17 +228,20 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     else if (ty == 2 && tx < 2 * RY)
         extra = tx < RY ? (tx + 1) * BW + S::D - 1 : (tx - RY + 1) * BW + S::D + 32 * V;
 
-    // converts this thread's part of the staged plane at `pl`; returns its own raw vector
-    auto convert = [&](long long* pl, long long (&q)[V], double (&raw)[V]) {
-        long long b[V];
-        ld_vec(pl + own, b);
+    // converts this thread's part of the staged plane at `pl`; returns its own raw vectors
+    auto convert = [&](long long* pl, long long (&q)[RT][V], double (&raw)[RT][V]) {
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            raw[i] = __longlong_as_double(b[i]);
-            q[i] = CONV ? xs_fix(b[i], emax) : b[i];
+        for (int j = 0; j < RT; ++j) {
+            long long b[V];
+            ld_vec(pl + own + j * BW, b);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                raw[j][i] = __longlong_as_double(b[i]);
+                q[j][i] = CONV ? xs_fix(b[i], emax) : b[i];
+            }
+            if constexpr (CONV) st_vec(pl + own + j * BW, q[j]);
         }
         if constexpr (CONV) {
-            st_vec(pl + own, q);
             if (ty < 2) {
                 long long h[V];
                 ld_vec(pl + extra, h);
@@ -251,15 +263,16 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
             issued = p_first + s;
         }
     }
-    long long below[V], cur[V], above[V];
-    double craw[V], araw[V];
+    long long below[RT][V], cur[RT][V], above[RT][V];
+    double craw[RT][V], araw[RT][V];
     int s_cur = 0, n_cur = 0;
     bool ok = mbar_wait_bounded(&bars[0], 0);
-    {
-        long long b[V];
-        ld_vec(stage + own, b);
 #pragma unroll
-        for (int i = 0; i < V; ++i) below[i] = CONV ? xs_fix(b[i], emax) : b[i];
+    for (int j = 0; j < RT; ++j) {
+        long long b[V];
+        ld_vec(stage + own + j * BW, b);
+#pragma unroll
+        for (int i = 0; i < V; ++i) below[j][i] = CONV ? xs_fix(b[i], emax) : b[i];
     }
     int s_nxt = 1 % NST, n_nxt = 1 / NST;
     ok = ok && mbar_wait_bounded(&bars[s_nxt], (uint32_t)n_nxt & 1u);
@@ -273,7 +286,8 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
     if constexpr (CONV) fence_proxy_async_smem();
     __syncthreads();
 
-    double* out = dst + g.at(X < g.nx ? X : 0, row_ok ? Y : 0, kb);   // only used when nvalid > 0
+    // row j of this thread's points at plane kb; only used for rows inside the box
+    double* out = dst + g.at(X < g.nx ? X : 0, 0, kb) + (int64_t)Y0 * g.pitch;
     if (!s_abort) {
         for (int k = kb; k < ke; ++k) {
             s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
@@ -285,41 +299,53 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
             convert(stage + s_nxt * STAGE, above, araw);
             const long long* pl = stage + s_cur * STAGE + own;
             long long ym[V], yp[V];
-            ld_vec(pl - BW, ym);
-            ld_vec(pl + BW, yp);
-            const long long left = pl[-1], right = pl[V];
-            double v[V];
+            ld_vec(pl - BW, ym);        // the row below the thread's first row
+            ld_vec(pl + RT * BW, yp);   // the row above its last row
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const long long xm = i == 0 ? left : cur[i - 1];
-                const long long xp = i == V - 1 ? right : cur[i + 1];
-                if constexpr (CONV) {
-                    // the first point converts L on the FP64 pipe, the second with
-                    // integer instructions: the same result, the two pipes shared
-                    const long long L = xs_numerator(cur[i], xm, xp, ym[i], yp[i], below[i], above[i]);
-                    v[i] = i == 0 ? xs_apply<true>(craw[i], L, r, r2, emax)
-                                  : xs_apply<false>(craw[i], L, r, r2, emax);
+            for (int j = 0; j < RT; ++j) {
+                const long long left = pl[j * BW - 1], right = pl[j * BW + V];
+                double v[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const long long xm = i == 0 ? left : cur[j][i - 1];
+                    const long long xp = i == V - 1 ? right : cur[j][i + 1];
+                    const long long yl = j == 0 ? ym[i] : cur[j - 1][i];
+                    const long long yh = j == RT - 1 ? yp[i] : cur[j + 1][i];
+                    if constexpr (CONV) {
+                        // the first point converts L on the FP64 pipe, the second with
+                        // integer instructions: the same result, the two pipes shared
+                        const long long L = xs_numerator(cur[j][i], xm, xp, yl, yh, below[j][i], above[j][i]);
+                        v[i] = i == 0 ? xs_apply<true>(craw[j][i], L, r, r2, emax)
+                                      : xs_apply<false>(craw[j][i], L, r, r2, emax);
+                    } else {
+                        auto d = [](long long b) { return __longlong_as_double(b); };
+                        v[i] = Point<double, false>::update(craw[j][i], d(xm), d(xp), d(yl), d(yh),
+                                                            d(below[j][i]), d(above[j][i]), r, 0);
+                    }
+                }
+                const int nvalid = Y0 + j < g.ny ? nx_ok : 0;
+                double* o = out + j * g.pitch;
+                if (nvalid == V) {
+                    st_vec(o, v);
                 } else {
-                    auto d = [](long long b) { return __longlong_as_double(b); };
-                    v[i] = Point<double, false>::update(craw[i], d(xm), d(xp), d(ym[i]), d(yp[i]),
-                                                        d(below[i]), d(above[i]), r, 0);
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (i < nvalid) o[i] = v[i];
+                }
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const unsigned a = i < nvalid ? xs_abs_hi(v[i]) : 0u;
+                    mx = a > mx ? a : mx;
                 }
             }
-            if (nvalid == V) {
-                st_vec(out, v);
-            } else {
 #pragma unroll
-                for (int i = 0; i < V; ++i)
-                    if (i < nvalid) out[i] = v[i];
-            }
+            for (int j = 0; j < RT; ++j)
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const unsigned a = i < nvalid ? xs_abs_hi(v[i]) : 0u;
-                mx = a > mx ? a : mx;
-                below[i] = cur[i];
-                cur[i] = above[i];
-                craw[i] = araw[i];
-            }
+                for (int i = 0; i < V; ++i) {
+                    below[j][i] = cur[j][i];
+                    cur[j][i] = above[j][i];
+                    craw[j][i] = araw[j][i];
+                }
             out += g.plane;
             if constexpr (CONV) fence_proxy_async_smem();
             __syncthreads();
@@ -345,13 +371,18 @@ __device__ __forceinline__ void xs_stream_body(const CUtensorMap* map, double* _
         const long long t0 = clock64();   // one time budget for the whole drain
         for (int p = drain_from; p <= issued; ++p) {
             const int i = p - p_first;
-            (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
+            if (!mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles)) {
+                atomicExch(err, 2);   // loads may still be landing: the context is suspect
+                break;
+            }
         }
     }
 }
 
-template <int RY, int NST>
-__global__ void __launch_bounds__(32 * RY)
+// kXsRows rows per tile, kXsRowsPerThread per thread: 128 threads, 64
+// registers (eight blocks per SM, each with a ring of kXsStages planes).
+template <int RY, int RT, int NST>
+__global__ void __launch_bounds__(32 * (RY / RT), 8)
     k_heat_stream_xs(const __grid_constant__ CUtensorMap map, double* __restrict__ dst, HeatGeom g,
                      double r, int kbeg, int kend, int kc, FxState* fx, int m3, int* err)
 {
@@ -376,12 +407,12 @@ __global__ void __launch_bounds__(32 * RY)
     const int emax = xs_emax(fx, m3);
     unsigned mx = 0;
     if (xs_native(emax, r))
-        xs_stream_body<RY, NST, false>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
+        xs_stream_body<RY, RT, NST, false>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
     else
-        xs_stream_body<RY, NST, true>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
+        xs_stream_body<RY, RT, NST, true>(&map, dst, g, r, kb, ke, emax, stage, bars, s_abort, mx, err);
     if (s_abort) return;   // uniform: every thread passed the barrier that saw it
-    fx_finish<32 * RY>((unsigned long long)mx << 32, fx, m3, 0,
-                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+    fx_finish<32 * (RY / RT)>((unsigned long long)mx << 32, fx, m3, 0,
+                              blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
 template <typename T>
@@ -392,14 +423,13 @@ constexpr int stream_rows()
 
 int stream_launch_xs(const StreamCall& c)
 {
-    constexpr int RY = kXsRows;
-    constexpr int NST = 6;
+    constexpr int RY = kXsRows, RT = kXsRowsPerThread, NST = kXsStages;
     constexpr size_t box_bytes = sizeof(double) * (size_t)(RY + 2) * StreamShape<double>::BW;
     constexpr size_t smem = NST * ((box_bytes + 127) / 128 * 128) + NST * sizeof(uint64_t);
     if (c.box[0] != (uint32_t)StreamShape<double>::BW || c.box[1] != (uint32_t)(RY + 2))
         return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
                     c.box[1], StreamShape<double>::BW, RY + 2);
-    auto kern = k_heat_stream_xs<RY, NST>;
+    auto kern = k_heat_stream_xs<RY, RT, NST>;
     static bool configured = false;
     if (!configured) {
         HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -411,7 +441,7 @@ int stream_launch_xs(const StreamCall& c)
     if (planes <= 0) return HS_OK;
     constexpr int TXW = 32 * StreamShape<double>::V;
     dim3 grid((g.nx + TXW - 1) / TXW, (g.ny + RY - 1) / RY, (planes + c.kc - 1) / c.kc);
-    dim3 block(32, RY, 1);
+    dim3 block(32, RY / RT, 1);
     kern<<<grid, block, smem, c.stream>>>(*c.map, (double*)c.dst, g, c.r, c.kbeg, c.kend, c.kc, c.fx,
                                           c.m3, c.err);
     HS_CHECK_LAUNCH("heat streaming Interior kernel (FP64 exact sum)");

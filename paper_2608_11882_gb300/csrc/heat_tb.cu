@@ -209,7 +209,10 @@ __global__ void __launch_bounds__(32 * RY, 1)
             const long long t0 = clock64();   // one time budget for the whole drain
             for (int p = drain_from; p <= issued; ++p) {
                 const int i = p - q0;
-                (void)mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles);
+                if (!mbar_wait_until(&bars[i % NST], (uint32_t)(i / NST) & 1u, t0, kWaitCycles)) {
+                    atomicExch(err, 2);   // loads may still be landing: the context is suspect
+                    break;
+                }
             }
         }
         return;

@@ -150,3 +150,38 @@ def test_full_size_f64_1000_steps_closed_form(pkg):
     expect = oracle.sine_modes_exact(modes, amps, u0.shape, 0.15, 1000, pts)
     vals = got[pts[:, 0], pts[:, 1], pts[:, 2]]
     assert np.max(np.abs(vals - expect)) <= F64_REL * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_caller_owned_buffers(pkg, dtype):
+    """Torch-allocated time-level buffers passed through hs_heat_desc.dev_buf0/1:
+    the library zeroes them, steps in them (the small workload, against the
+    oracle), and leaves them allocated and usable after the handle is gone."""
+    torch = require_cuda()
+    u0 = heat_u0_single_mode(64, 64, 64)
+    nbytes = pkg.Heat.buffer_bytes(64, 64, 64, dtype)
+    bufs = [torch.full((nbytes,), 7, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    h = pkg.Heat(64, 64, 64, 0.1, dtype=dtype, buffers=bufs)
+    h.upload(np.ascontiguousarray(u0, dtype=h.np_dtype))
+    torch.cuda.synchronize()
+    # the field sits in the caller's buffer 0: padded layout, interior at plane,
+    # row and column 1 (column offset lead = 32 bytes), boundary layer zero
+    elem = 8 if dtype == "f64" else 4
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    lead = 32 // elem
+    pitch = nbytes // elem // (66 * 66)
+    f0 = bufs[0].view(tdt).reshape(66, 66, pitch)
+    assert np.array_equal(f0[1:65, 1:65, lead:lead + 64].cpu().numpy(), u0.astype(h.np_dtype))
+    assert not f0[0].any() and not f0[:, 0].any() and not f0[:, :, lead - 1].any()
+    h.step(100)
+    got = h.read()
+    h.close()
+    ref = oracle.heat_run(u0, 0.1, 100, threads=oracle.max_threads())
+    if dtype == "f64":
+        assert rel_max_err(got, ref) <= F64_REL
+    else:
+        assert np.max(np.abs(got - ref)) <= f32_bound(100, np.max(np.abs(u0)))
+    # after 100 steps (an even count) the current level is buffer 0 again
+    assert np.array_equal(f0[1:65, 1:65, lead:lead + 64].cpu().numpy(), got)
+    bufs[1].zero_()                       # still the caller's, still allocated
+    torch.cuda.synchronize()

@@ -109,3 +109,39 @@ def test_batch_workload_256_grids_subset(pkg):
         assert np.array_equal(heats[i].read(), alone(pkg, specs[i], specs[i]["steps"]))
     for h in heats:
         h.close()
+
+
+def test_bounded_step_wait_runs_out_then_recovers(pkg):
+    """A step wait that runs out (its limit set to a few SM cycles, so a grid's
+    step m+1 cannot wait for step m to finish): the run stops early and
+    heat_batch_wait reports HS_ETIMEOUT; no fault, no endless wait.  With the
+    default limit restored, the same handles re-uploaded give the oracle's
+    result, stepped alone and batched."""
+    from paper_2608_11882_gb300 import _native as nat
+    specs = draw_batch(2, seed=8, edge=(40, 64), steps=(12, 12))
+    for s in specs:
+        s["dtype"] = "f64"
+    heats = make_heats(pkg, specs)
+    try:
+        nat.heat_batch_set_wait_limit(4)
+        b = pkg.HeatBatch(heats, [s["steps"] for s in specs])
+    finally:
+        nat.heat_batch_set_wait_limit(0)
+    with b:
+        b.run(use_graph=False)
+        with pytest.raises(pkg.HeatCGError) as e:
+            b.wait()
+        assert e.value.code == nat.HS_ETIMEOUT
+    # the handles and the context stay usable
+    for s, h in zip(specs, heats):
+        h.upload(s["u0"])
+        h.step(s["steps"])
+        assert rel_max_err(h.read(), oracle.heat_run(s["u0"], s["r"], s["steps"])) <= F64_REL
+        h.upload(s["u0"])
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b2:
+        b2.run(use_graph=True).wait()
+    for s, h in zip(specs, heats):
+        assert rel_max_err(h.read(), oracle.heat_run(s["u0"], s["r"], s["steps"])) <= F64_REL
+        h.close()
+    with pytest.raises(pkg.HeatCGError):
+        nat.heat_batch_set_wait_limit(-1)
