@@ -61,6 +61,36 @@ HEAT_MODES = {
 }
 
 
+# Algorithmic bytes of the other rows (read each input once, write each output once):
+#  * batched heat: 16 B per lattice-point update of an FP64 grid, 8 B of an FP32 grid;
+#  * the paper's variable-coefficient update: u, kappa and dt f read, u' written --
+#    32 B (FP64) / 16 B (FP32) per update; the FP64 form is bound by the FP64 pipe
+#    at 23 operations per update (per axis 4 additions, a multiply and an FMA for
+#    the face differences; 5 to add dt f and the three scaled differences);
+#  * CG per unknown and iteration: SpMV 16 B (read p, write q), x/r update 48 B
+#    (read x, p, r, q; write x, r), p update 24 B (read r, p; write p) = 88 B
+#    matrix-free; CSR adds 12 B per stored entry and 4 B of row pointer per row;
+#  * mixed-precision CG per inner iteration and unknown: FP32 SpMV 8 B (+ 8 B per
+#    entry and 4 B per row for CSR), update 24 B, p update 12 B; per refinement:
+#    FP64 SpMV 16 B (+ 12 B per entry, 4 B per row for CSR), residual 36 B
+#    (read b, A x; write r in FP64 and r, p, d in FP32), correction 20 B.
+VK_FP64_OPS_PER_LUP = 23
+CG_BYTES_PER_ROW = 88
+MIXED_INNER_BYTES_PER_ROW = 44
+MIXED_REFINE_BYTES_PER_ROW = 72
+
+
+def hbm_roofline(kernel, bytes_moved, ms, hbm_gbs, peak_kind, traffic=None, **extra):
+    """Roofline object of an HBM-bound measurement: algorithmic bytes moved in
+    `ms` milliseconds against the measured copy rate."""
+    ach = bytes_moved / (ms * 1e-3) / 1e9
+    out = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+           "frac": ach / hbm_gbs, "traffic": traffic, "peak_kind": peak_kind,
+           "frac_of_nominal": ach / NOMINAL_HBM_GBS, "algorithmic_bytes": bytes_moved}
+    out.update(extra)
+    return out
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -80,7 +110,9 @@ def parse_args():
                     help="default: the timed heat + CG step; precision: the 1024^3 FP32 heat "
                          "and 512^3 mixed-precision CG comparison; serving: the continuous-"
                          "batching request stream (these two: one run, no timing contract)")
-    ap.add_argument("--requests", type=int, default=200, help="serving: requests in the trace")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the trace")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving workload in the default run")
     ap.add_argument("--tdepth", type=int, default=0,
                     help="steps per pass of the timed heat handle (0: library choice)")
     ap.add_argument("--no-side", action="store_true",
@@ -103,6 +135,26 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def host_cores():
@@ -156,7 +208,7 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def paper_problem_side(pkg, stream):
+def paper_problem_side(pkg, stream, hbm_gbs, peak_kind):
     """The paper's variable-coefficient problem at its N = 512 (510^3 interior
     nodes, dt = h^2/(12 kappa_max)), 500 steps, FP64 and FP32.  The paper's
     measured k = 6.4042e-11 s per point-step for OpenMP offload on one H100
@@ -182,17 +234,31 @@ def paper_problem_side(pkg, stream):
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1)
-        out[dtype] = {"glups": float(n) ** 3 * steps / (ms * 1e-3) / 1e9, "ms": ms}
+        lups = float(n) ** 3 * steps
+        out[dtype] = {"glups": lups / (ms * 1e-3) / 1e9, "ms": ms}
+        bpl = 32 if dtype == "f64" else 16
+        hbm = hbm_roofline(f"k_vk_interior<{'double' if dtype == 'f64' else 'float'}> + k_vk_boundary",
+                           lups * bpl, ms, hbm_gbs, peak_kind, bytes_per_lup=bpl)
+        if dtype == "f64":
+            rate = lups * VK_FP64_OPS_PER_LUP / (ms * 1e-3) / 1e12
+            out[dtype]["roofline"] = {"bound": "alu", "kernel": hbm["kernel"], "achieved": rate,
+                                      "peak": FP64_INSTR_PEAK_T, "unit": "T FP64-instr/s",
+                                      "frac": rate / FP64_INSTR_PEAK_T, "traffic": None,
+                                      "fp64_ops_per_lup": VK_FP64_OPS_PER_LUP,
+                                      "hbm_achieved_gbs": hbm["achieved"], "hbm_frac": hbm["frac"]}
+        else:
+            out[dtype]["roofline"] = hbm
         del src
     return out
 
 
-def batching_side(pkg, stream):
+def batching_side(pkg, stream, hbm_gbs, peak_kind):
     """The batching workload: 256 heat grids (edges log-uniform in [16, 128],
     FP64/FP32, r ~ U[0.05, 0.16], steps ~ U{50..500}) in one persistent launch
     replayed from a CUDA graph, against the same grids stepped one handle at a
     time; and 64 CG solves (edges in [32, 128], rtol 1e-8) batched against one
     at a time."""
+    import numpy as np
     import torch
 
     from workloads import cg_batch_specs, heat_batch_specs
@@ -216,8 +282,13 @@ def batching_side(pkg, stream):
         e1.record(stream)
         b.wait()
         ms = e0.elapsed_time(e1)
+        nbytes = sum(int(np.prod(sp["shape"])) * sp["steps"] * (16 if sp["dtype"] == "f64" else 8)
+                     for sp in specs)
         out["heat_256"] = {"lups": b.lups, "ms": ms, "glups": b.lups / (ms * 1e-3) / 1e9,
-                           "blocks": b.blocks, "launches_per_run": 1}
+                           "blocks": b.blocks, "launches_per_run": 1,
+                           "roofline": hbm_roofline("k_heat_batch (persistent, all grids and steps)",
+                                                    nbytes, ms, hbm_gbs, peak_kind,
+                                                    bytes_per_lup="16 (FP64 grids) / 8 (FP32 grids)")}
     e0, e1 = ev(), ev()
     e0.record(stream)
     for s, h in zip(specs, heats):
@@ -313,7 +384,7 @@ def cpu_baseline(args, threads):
     b = cg_rhs(m ** 3, seed=SEED)
     cg_iters = 20
     _, info = oracle.cg_solve(b, 1e-30, cg_iters, shape=(m, m, m), threads=threads)
-    return {"value": glups, "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+    return {"value": glups, "unit": "GLUP/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"heat {n}^3 FP64 r={args.r}, {steps} of {args.heat_steps} steps, timed step "
                       f"loop only; CG matrix-free {m}^3, {cg_iters} iterations",
             "cg_matrix_free_its_per_s": cg_iters / info["loop_seconds"],
@@ -351,6 +422,7 @@ def run_reference(args):
             "config": {"workload": f"heat {n}^3 FP64 r={args.r} (sample: {per} steps per bench step)",
                        "seed": SEED},
             "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": f"{per} heat steps of {n}^3 per bench step"},
             "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -497,6 +569,14 @@ def run_ours(args):
 
     it_mf = [i[0]["iters"] for i in infos]
     it_csr = [i[1]["iters"] for i in infos]
+    nrow = float(m) ** 3
+    cg_roof = {
+        "matrix_free": hbm_roofline("CG matrix-free (SpMV + updates, whole solve)",
+                                    it_mf[-1] * CG_BYTES_PER_ROW * nrow, statistics.median(seg["cg_mf"]),
+                                    hbm_gbs, peak_kind, bytes_per_row_per_iter=CG_BYTES_PER_ROW),
+        "csr": hbm_roofline("CG CSR (SpMV + updates, whole solve)",
+                            it_csr[-1] * (CG_BYTES_PER_ROW * nrow + 12.0 * nnz + 4 * nrow),
+                            statistics.median(seg["cg_csr"]), hbm_gbs, peak_kind)}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -513,10 +593,11 @@ def run_ours(args):
                  "hbm_frac_16B_per_lup": value / world * 16 / hbm_gbs},
         "cg": {"matrix_free": {"iters": it_mf[-1], "its_per_s": it_mf[-1] / (statistics.median(seg["cg_mf"]) * 1e-3),
                                "ms_per_solve": statistics.median(seg["cg_mf"]),
-                               "relres_true": infos[-1][0]["relres_true"]},
+                               "relres_true": infos[-1][0]["relres_true"],
+                               "roofline": cg_roof["matrix_free"]},
                "csr": {"iters": it_csr[-1], "its_per_s": it_csr[-1] / (statistics.median(seg["cg_csr"]) * 1e-3),
                        "ms_per_solve": statistics.median(seg["cg_csr"]),
-                       "relres_true": infos[-1][1]["relres_true"]}},
+                       "relres_true": infos[-1][1]["relres_true"], "roofline": cg_roof["csr"]}},
         "latency_ms": {k: {"p50": pct(v, 0.5), "p99": pct(v, 0.99)} for k, v in seg.items()},
         # (max - min) / median of each segment over the timed steps
         "variability": {k: (max(v) - min(v)) / statistics.median(v) for k, v in seg.items()},
@@ -610,11 +691,11 @@ def run_ours(args):
 
     # ---- batching: 256 uneven heat grids in one persistent launch, 64 CG solves -
     if not args.no_side:
-        line["batching"] = batching_side(pkg, stream)
+        line["batching"] = batching_side(pkg, stream, hbm_gbs, peak_kind)
 
     # ---- the paper's own problem: variable kappa, N = 512, 500 steps ---------------
     if not args.no_side:
-        line["paper_problem"] = paper_problem_side(pkg, stream)
+        line["paper_problem"] = paper_problem_side(pkg, stream, hbm_gbs, peak_kind)
 
     # ---- mixed-precision CG beside the FP64 solves (untimed region) ------------
     if not args.no_side:
@@ -630,10 +711,21 @@ def run_ours(args):
                 e1.record(stream)
                 e1.synchronize()
                 ms = e0.elapsed_time(e1)
+                nrow = float(m) ** 3
+                csr_inner = (8.0 * nnz + 4 * nrow) if kind == "csr" else 0.0
+                csr_ref = (12.0 * nnz + 4 * nrow) if kind == "csr" else 0.0
+                nbytes = (im["iters"] * (MIXED_INNER_BYTES_PER_ROW * nrow + csr_inner)
+                          + (im["refinements"] + 1) * (MIXED_REFINE_BYTES_PER_ROW * nrow + csr_ref))
                 mixed[kind] = {"ms_per_solve": ms, "inner_iters": im["iters"],
                                "refinements": im["refinements"], "relres_true": im["relres_true"],
-                               "speedup_vs_f64": line["cg"][kind]["ms_per_solve"] / ms}
+                               "speedup_vs_f64": line["cg"][kind]["ms_per_solve"] / ms,
+                               "roofline": hbm_roofline(f"mixed CG {kind} (whole solve)", nbytes, ms,
+                                                        hbm_gbs, peak_kind)}
         line["cg"]["mixed_f32_krylov"] = mixed
+
+    # ---- serving: the Poisson request stream, closed loop and one offered load ----
+    if not args.no_side and not args.no_serving:
+        line["serving"] = serving_side(args, loads=(0.7,))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, host_cores())
@@ -707,16 +799,14 @@ def run_precision(args):
     return 0
 
 
-def run_serving(args):
+def serving_side(args, loads=(0.5, 0.7, 0.9)):
     """The serving workload: a seeded Poisson stream of heat (75%) and CG (25%)
     requests, edges log-uniform in [32, 384] per axis, steps log-uniform in
     [10, 2000], FP32/FP64 half each, admitted by free HBM with fields resident.
     Capacity is measured closed-loop (every request arriving at once); the
-    same trace is then replayed at 0.5, 0.7 and 0.9 of that request rate."""
+    same trace is then replayed at the given fractions of that request rate."""
     import torch
 
-    from paper_2608_11882_gb300.build import build
-    build()
     from paper_2608_11882_gb300.serve import GpuBackend, Server, poisson_trace, predict_seconds, summarize
 
     base = poisson_trace(args.requests, rate=1.0, seed=SEED)   # arrivals for rate 1, rescaled below
@@ -745,10 +835,17 @@ def run_serving(args):
             "closed_loop": closed, "capacity_req_per_s": capacity, "loads": {},
             "kbar_s_per_point_step": kbars,
             "predicted_heat_device_s": sum(predict_seconds(q, kbars) for q in base if q.kind == "heat")}
-    for load in (0.5, 0.7, 0.9):
+    for load in loads:
         line["loads"][str(load)] = serve(1.0 / (load * capacity))
     torch.cuda.synchronize()
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serving(args):
+    """--workload serving: the serving workload at offered loads 0.5, 0.7, 0.9."""
+    from paper_2608_11882_gb300.build import build
+    build()
+    print(json.dumps(serving_side(args)), flush=True)
     return 0
 
 

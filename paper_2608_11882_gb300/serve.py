@@ -325,8 +325,21 @@ def poisson_trace(n: int, rate: float, seed: int, edge=(32, 384), steps=(10, 200
                   heat_frac: float = 0.75, f32_frac: float = 0.5, rtol: float = 1e-8):
     """Seeded requests: exponential inter-arrival times of mean 1/rate; heat
     with probability heat_frac; edges log-uniform per axis in `edge`; steps
-    log-uniform in `steps`; FP32/FP64 by f32_frac; u0 ~ U[-1, 1]; b ~ N(0, 1)."""
+    log-uniform in `steps`; FP32/FP64 by f32_frac; u0 ~ U[-1, 1]; b ~ N(0, 1).
+    Payloads are windows, at seeded offsets, of two seeded pools (uniform and
+    normal) a little longer than the largest request, so a trace of thousands
+    of requests holds two pools instead of one array per request."""
     rng = np.random.default_rng([seed, 5])
+    prng = np.random.default_rng([seed, 6])
+    pool_n = edge[1] ** 3 + (1 << 22)
+    upool = prng.uniform(-1.0, 1.0, size=pool_n)
+    npool = prng.standard_normal(pool_n)
+
+    def window(pool, shape):
+        pts = int(np.prod(shape))
+        off = int(rng.integers(0, pool_n - pts + 1))
+        return pool[off:off + pts].reshape(shape)
+
     t = 0.0
     reqs = []
     for rid in range(n):
@@ -336,8 +349,8 @@ def poisson_trace(n: int, rate: float, seed: int, edge=(32, 384), steps=(10, 200
             st = int(round(math.exp(rng.uniform(math.log(steps[0]), math.log(steps[1])))))
             dt = "f32" if rng.uniform() < f32_frac else "f64"
             reqs.append(Request(rid, "heat", shape, dt, float(rng.uniform(0.05, 0.16)), st,
-                                arrival=t, payload=rng.uniform(-1.0, 1.0, size=shape)))
+                                arrival=t, payload=window(upool, shape)))
         else:
             reqs.append(Request(rid, "cg", shape, "f64", rtol=rtol, arrival=t,
-                                payload=rng.standard_normal(int(np.prod(shape)))))
+                                payload=window(npool, (int(np.prod(shape)),))))
     return reqs
