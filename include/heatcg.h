@@ -217,6 +217,14 @@ int heat_steps_done(hs_heat_t h, int64_t* steps);
  * + Boundary kernels every step, L >= 2 = L steps per pass). */
 int heat_get_tdepth(hs_heat_t h, int32_t* tdepth);
 
+/* Planes each block of the one-step Interior kernel takes (the k-chunk of
+ * Section 6.1's k-split, applied within one GPU): planes >= 1 sets it (capped
+ * at the interior's nz - 2), 0 restores the library's choice.  It changes
+ * speed only -- every point is computed the same way -- and does not apply to
+ * temporally blocked passes.  heat_get_kchunk reports the value in use. */
+int heat_set_kchunk(hs_heat_t h, int32_t planes);
+int heat_get_kchunk(hs_heat_t h, int32_t* planes);
+
 /* Release the handle (Algorithm "1-GPU Baseline", freeing the device arrays
  * after the time loop): synchronises its stream and frees what the library
  * allocated; caller-owned dev_buf0/dev_buf1 are left to the caller. */
@@ -230,8 +238,9 @@ int heat_destroy(hs_heat_t h);
  * grid i by steps[i] steps of the update of Section 4, Eq. 4 -- the work of
  * the Interior and Boundary kernels of each step -- with the same per-point
  * arithmetic as heat_step, so the results match running each grid alone bit
- * for bit.  Work items are (step, grid, column tile) taken from a device work
- * counter; a grid's step starts once its previous step is complete, a wait
+ * for bit.  Work items are (step, grid, column tile of 64 x 8, chunk of
+ * planes) taken from a device work counter; each item stages its planes in
+ * shared memory (converted once in the exact-sum FP64 arithmetic); a grid's step starts once its previous step is complete, a wait
  * that is bounded (about a second), after which heat_batch_wait reports
  * HS_ETIMEOUT. */
 typedef struct hs_batch* hs_batch_t;
@@ -241,6 +250,15 @@ typedef struct hs_batch* hs_batch_t;
  * (each grid's own stream is synchronised before a run). */
 int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps, int32_t n,
                       void* stream);
+
+/* heat_batch_create with the planes per work item chosen per grid: kz[i] >= 1
+ * splits each step of grid i into z-chunks of kz[i] planes (each chunk of
+ * each column tile is one item), 0 leaves it to the library (whole columns
+ * for grids of 16 or more column tiles, else chunks of at least 16 planes
+ * so that about 16 items share a step); kz may be NULL (all 0).  The chunking
+ * changes speed only: every point is computed the same way. */
+int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps,
+                            const int32_t* kz, int32_t n, void* stream);
 
 /* Enqueue one run: every grid advances by its steps (asynchronous; the
  * handles' step counters and current buffers are updated at once).  With

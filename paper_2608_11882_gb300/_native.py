@@ -73,6 +73,10 @@ def _load():
         "heat_time_interior": [vp, ctypes.c_int],
         "heat_interior_time": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
         "heat_get_tdepth": [vp, ctypes.POINTER(i32)],
+        "heat_set_kchunk": [vp, i32],
+        "heat_get_kchunk": [vp, ctypes.POINTER(i32)],
+        "heat_batch_create_tiled": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i32), i32, vp],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
         "cg_spmv": [ctypes.POINTER(hs_op), vp, vp, ctypes.c_int, ctypes.POINTER(dbl), vp],
@@ -186,16 +190,31 @@ def heat_get_tdepth(h: int) -> int:
     return t.value
 
 
+def heat_set_kchunk(h: int, planes: int) -> None:
+    check(lib.heat_set_kchunk(h, int(planes)), "heat_set_kchunk")
+
+
+def heat_get_kchunk(h: int) -> int:
+    t = ctypes.c_int32()
+    check(lib.heat_get_kchunk(h, ctypes.byref(t)), "heat_get_kchunk")
+    return t.value
+
+
 def heat_destroy(h: int) -> None:
     check(lib.heat_destroy(h), "heat_destroy")
 
 
-def heat_batch_create(handles, steps, stream: int = 0) -> int:
+def heat_batch_create(handles, steps, stream: int = 0, kz=None) -> int:
+    """kz: planes per work item for each grid (0: the library's choice), or None."""
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*handles)
     st = (ctypes.c_int64 * n)(*[int(s) for s in steps])
     b = ctypes.c_void_p()
-    check(lib.heat_batch_create(ctypes.byref(b), arr, st, n, stream), "heat_batch_create")
+    if kz is None:
+        check(lib.heat_batch_create(ctypes.byref(b), arr, st, n, stream), "heat_batch_create")
+    else:
+        kza = (ctypes.c_int32 * n)(*[int(k) for k in kz])
+        check(lib.heat_batch_create_tiled(ctypes.byref(b), arr, st, kza, n, stream), "heat_batch_create_tiled")
     return b.value
 
 

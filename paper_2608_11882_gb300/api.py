@@ -49,17 +49,22 @@ class Heat:
     def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
                  stream=None, tdepth=0, buffers=None):
         """tdepth: steps per pass (0 = the library's default, 1..4), or "auto" for
-        the autotuner's cached or freshly measured choice for this shape.
+        the autotuner's cached or freshly measured choice for this shape (the
+        depth, and the Interior kernel's planes per block).
         buffers: optional pair of caller-owned CUDA tensors for the two padded
         time levels (each at least ``Heat.buffer_bytes(...)`` bytes); the
         handle keeps references to them while it lives."""
         self.shape = (nz, ny, nx)
         self.dtype_code, self.np_dtype = _DTYPES[dtype]
+        self.dtype = dtype
+        tuned = None
         if tdepth == "auto":
             from .autotune import Tuner
             arith = ("fixed64" if flags & HS_FIXED64 else "f64exact" if flags & HS_EXACT_ROUNDING
                      else "f64pipe" if flags & HS_FP64_PIPE else dtype)
-            tdepth = 1 if flags & (HS_VARKAPPA | HS_SCHED_FULL) else Tuner().best_depth(arith, self.shape)
+            tuned = ({"depth": 1, "kc_factor": 1.0} if flags & (HS_VARKAPPA | HS_SCHED_FULL)
+                     else Tuner().best(arith, self.shape))
+            tdepth = tuned["depth"]
         self.stream = _stream_handle(stream)
         desc = native.hs_heat_desc(nx=nx, ny=ny, nz=nz, r=r, flags=flags, dtype=self.dtype_code,
                                    tdepth=tdepth, stream=self.stream)
@@ -71,6 +76,18 @@ class Heat:
             desc.dev_buf0, desc.dev_buf1 = b0.data_ptr(), b1.data_ptr()
             self._buffers = (b0, b1)
         self.handle = native.heat_create(desc)
+        if tuned is not None and tuned["kc_factor"] != 1.0 and tuned["depth"] == 1:
+            lib_kc = native.heat_get_kchunk(self.handle)
+            native.heat_set_kchunk(self.handle, max(4, int(round(lib_kc * tuned["kc_factor"]))))
+
+    @property
+    def kchunk(self) -> int:
+        """Planes per block of the one-step Interior kernel (heat_get_kchunk)."""
+        return native.heat_get_kchunk(self.handle)
+
+    @kchunk.setter
+    def kchunk(self, planes: int) -> None:
+        native.heat_set_kchunk(self.handle, planes)
 
     @staticmethod
     def buffer_bytes(nx: int, ny: int, nz: int, dtype: str = "f64") -> int:
@@ -151,11 +168,19 @@ class HeatBatch:
     """Several Heat handles advanced together by one persistent launch
     (heat_batch_create / heat_batch_run / heat_batch_wait)."""
 
-    def __init__(self, heats, steps, stream=None):
+    def __init__(self, heats, steps, stream=None, kz=None):
+        """kz: planes per work item, per grid (a list; 0 = the library's choice),
+        "auto" for the autotuner's choice per grid size class, or None."""
         self.heats = list(heats)
         self.steps = [int(s) for s in steps]
         self.stream = _stream_handle(stream)
-        self.handle = native.heat_batch_create([h.handle for h in self.heats], self.steps, self.stream)
+        if kz == "auto":
+            from .autotune import Tuner
+            t = Tuner()
+            kz = [t.best_batch_kz(h.dtype, h.shape) for h in self.heats]
+        self.kz = kz
+        self.handle = native.heat_batch_create([h.handle for h in self.heats], self.steps, self.stream,
+                                               kz=kz)
 
     def run(self, use_graph: bool = True) -> "HeatBatch":
         native.heat_batch_run(self.handle, use_graph)

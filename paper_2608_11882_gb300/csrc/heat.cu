@@ -1105,6 +1105,28 @@ int heat_steps_done(hs_heat_t h, int64_t* steps)
     return HS_OK;
 }
 
+int heat_set_kchunk(hs_heat_t h, int32_t planes)
+{
+    if (!h) return fail(HS_EINVAL, "heat_set_kchunk: NULL handle");
+    if (planes < 0) return fail(HS_EINVAL, "heat_set_kchunk: planes = %d < 0", planes);
+    const int interior = h->g.nz > 2 ? h->g.nz - 2 : 1;
+    if (planes == 0) {
+        h->kchunk = pick_kchunk(h->g);
+        h->kc_stream = pick_kc_stream(h->g, h->arith);
+    } else {
+        h->kchunk = h->kc_stream = planes < interior ? planes : interior;
+    }
+    return HS_OK;
+}
+
+int heat_get_kchunk(hs_heat_t h, int32_t* planes)
+{
+    if (!h || !planes) return fail(HS_EINVAL, "heat_get_kchunk: NULL argument");
+    const bool streaming = !(h->flags & HS_VARKAPPA) && h->arith != A_F64 && h->arith != A_F64_EXACT;
+    *planes = streaming ? h->kc_stream : h->kchunk;
+    return HS_OK;
+}
+
 int heat_get_tdepth(hs_heat_t h, int32_t* tdepth)
 {
     if (!h || !tdepth) return fail(HS_EINVAL, "heat_get_tdepth: NULL argument");

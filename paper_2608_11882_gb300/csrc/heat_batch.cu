@@ -2,9 +2,10 @@
 // counts, FP32 or FP64), every step of every grid, in ONE persistent kernel
 // launch, optionally replayed from a captured CUDA graph.
 //
-// Work items are (step m, grid g, column tile t) in step-major order; a
-// persistent grid of co-resident blocks takes them from an atomic counter.
-// An item of step m of grid g may start once all tiles of step m-1 of grid g
+// Work items are (step m, grid g, column tile, chunk of planes) in step-major
+// order; a persistent grid of co-resident blocks takes them from an atomic
+// counter.
+// An item of step m of grid g may start once all items of step m-1 of grid g
 // have finished (a per-grid completion counter, published with a fence), so
 // each step of a grid reads a complete previous time level -- the Interior
 // and Boundary work of one step of Section 4's update, over the whole grid.
@@ -18,10 +19,10 @@
 // freshly written plane through its own stale L1 lines.
 //
 // Plain FP64 grids run the exact-sum arithmetic of heat_step (heat_common.cuh):
-// every tile of step m reads the field maximum of step m from the grid's slot
-// (m3 + m) % 3, which the tiles of step m-1 completed before the wait above
-// let step m start; each tile adds its outputs' maximum to slot (m3 + m + 1) % 3,
-// and tile 0 clears slot (m3 + m + 2) % 3, which no unfinished item reads.
+// every item of step m reads the field maximum of step m from the grid's slot
+// (m3 + m) % 3, which the items of step m-1 completed before the wait above
+// let step m start; each item adds its outputs' maximum to slot (m3 + m + 1) % 3,
+// and item 0 clears slot (m3 + m + 2) % 3, which no unfinished item reads.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -37,7 +38,9 @@ constexpr long long kBatchWaitCycles = 2000000000ll;   // about one second at GB
 // Wait limit that batches created from now on get (heat_batch_set_wait_limit).
 static std::atomic<long long> g_batch_wait_cycles{kBatchWaitCycles};
 
-enum BatchKind { K_F64_PIPE = 0, K_F32 = 1, K_F64_XS = 2 };
+// K_F64_XS_NATIVE: an exact-sum grid whose field is outside the convertible
+// exponent range this step, stepped on the FP64 pipe (never a grid's kind).
+enum BatchKind { K_F64_PIPE = 0, K_F32 = 1, K_F64_XS = 2, K_F64_XS_NATIVE = 3 };
 
 struct BatchGrid {
     HeatGeom g;
@@ -47,9 +50,10 @@ struct BatchGrid {
     int32_t kind;       // BatchKind
     int32_t cur;        // buffer holding the field when the batch starts
     int32_t m3;         // K_F64_XS: slot of the field when the batch starts
-    int32_t tiles_x;
-    int32_t tiles;      // tiles per step
-    int32_t pad;
+    int32_t tiles_x;    // column tiles per row of tiles
+    int32_t tiles_xy;   // column tiles
+    int32_t kz;         // planes per work item (the last chunk may be shorter)
+    int32_t tiles;      // work items per step: column tiles x z-chunks
     int64_t steps;
 };
 
@@ -60,55 +64,181 @@ struct BatchDev {
     const int32_t* list_grid;     // active grid of each entry
     const int64_t* list_item0;    // first item (within its step) of each entry
     unsigned long long* next;     // work counter
-    unsigned long long* done;     // per grid: tiles completed, all steps
+    unsigned long long* done;     // per grid: items completed, all steps
     int* err;
     int64_t items;
     long long wait_cycles;        // limit of the step wait, in SM clock cycles
     int32_t max_steps;
 };
 
-// One column tile of step m; returns the largest |u| high word of its outputs
-// (exact-sum FP64 only).
-template <typename T, bool XS>
-__device__ __forceinline__ unsigned batch_tile(const BatchGrid& G, int m, int t)
+// One work item of step m -- a column tile and a chunk [kb, ke) of its planes:
+// a block of 32 x 8 threads owns a 64 x 8 tile of the grid's columns and
+// marches up the chunk's planes, every thread two
+// consecutive x points of one row.  Each plane of the tile with its one-point
+// halo is loaded once with coalesced L2 loads two planes ahead of use (kept in
+// registers), converted once (exact-sum FP64: to fixed point on the field's
+// scale; otherwise kept as is) into one of two shared plane buffers; a thread
+// keeps its own values at k-1, k and k+1 in registers, reads the in-plane
+// neighbours from the buffer of plane k, and one block barrier per plane
+// orders the buffers.  Positions past the grid's boundary layer (x > nx,
+// y > ny, possible in the last tiles) are never loaded: they hold zeros and
+// feed no output.  The per-point arithmetic is that of heat_step, so the
+// result matches the grid stepped alone bit for bit.  Returns the largest
+// |u| high word of the outputs (exact-sum FP64 only).
+constexpr int kBatchTW = 64, kBatchBW = 68, kBatchD = 2;   // tile width, buffer row, x offset
+constexpr int kBatchPlane = (kBatchBY + 2) * kBatchBW;     // buffer elements per plane
+static_assert(kBatchBX * 2 == kBatchTW, "two points per thread");
+
+template <typename T>
+__device__ __forceinline__ void st_pair(T* p, const T (&v)[2])
 {
+    if constexpr (sizeof(T) == 8)
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ unsigned batch_tile(const BatchGrid& G, int m, int item, long long* sbuf)
+{
+    constexpr int V = 2, BW = kBatchBW;
+    constexpr bool CONV = KIND == K_F64_XS;
+    // shared values: fixed-point integers (exact-sum FP64), raw bits otherwise
+    using Q = typename std::conditional<CONV, long long, T>::type;
+    Q* buf = reinterpret_cast<Q*>(sbuf);
     const HeatGeom& g = G.g;
-    const int tx = t % G.tiles_x, ty = t / G.tiles_x;
-    const int i = tx * kBatchBX + threadIdx.x;
-    const int j = ty * kBatchBY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return 0u;
-    const int emax = XS ? xs_emax(G.fx, (G.m3 + m) % 3) : 0;
-    unsigned mx = 0;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBatchBX + tx;
+    const int t = item % G.tiles_xy;
+    const int kb = (item / G.tiles_xy) * G.kz, ke = min(kb + G.kz, g.nz);
+    const int x0 = (t % G.tiles_x) * kBatchTW, y0 = (t / G.tiles_x) * kBatchBY;
+    const int X = x0 + V * tx, Y = y0 + ty;
+    const int own = (ty + 1) * BW + kBatchD + V * tx;
+    const int emax = CONV ? xs_emax(G.fx, (G.m3 + m) % 3) : 0;
+    const double r = G.r;
+    const double r2 = CONV ? xs_r2(r, emax) : 0.0;
     const int src_b = (G.cur + m) & 1;
     const T* __restrict__ src = (const T*)G.buf[src_b];
     T* __restrict__ dst = (T*)G.buf[src_b ^ 1];
-    const T r = (T)G.r;
-    const int64_t P = g.plane, Y = g.pitch;
-    int64_t c = g.at(i, j, 0);
-    T below = __ldcg(src + c - P);
-    T cur = __ldcg(src + c);
-    for (int k = 0; k < g.nz; ++k) {
-        const T above = __ldcg(src + c + P);
-        const T xm = __ldcg(src + c - 1), xp = __ldcg(src + c + 1);
-        const T ym = __ldcg(src + c - Y), yp = __ldcg(src + c + Y);
-        T v;
-        if constexpr (XS) {
-            v = xs_point(cur, xm, xp, ym, yp, below, above, r, emax);
-            const unsigned a = xs_abs_hi(v);
-            mx = a > mx ? a : mx;
+    // own points: loaded where they lie in the padded buffer (y <= ny, x <= nx
+    // reach the boundary layer), computed and stored where interior
+    const bool ld0 = Y <= g.ny && X <= g.nx, ld1 = Y <= g.ny && X + 1 <= g.nx;
+    const bool ok0 = Y < g.ny && X < g.nx, ok1 = Y < g.ny && X + 1 < g.nx;
+    const int64_t rowoff = g.at(X, Y, -1);   // plane k adds (k + 1) plane
+    // one halo value per thread for the first 2*64 + 2*8 threads
+    int hidx = -1;
+    int64_t hoff = 0;
+    bool hld = false;
+    if (tid < 2 * kBatchTW) {
+        const int rr = tid < kBatchTW ? 0 : kBatchBY + 1;
+        const int c = tid % kBatchTW;
+        const int hx = x0 + c, hy = rr == 0 ? y0 - 1 : y0 + kBatchBY;
+        hidx = rr * BW + kBatchD + c;
+        hld = hx <= g.nx && hy <= g.ny;
+        hoff = g.at(hx, hy, -1);
+    } else if (tid < 2 * kBatchTW + 2 * kBatchBY) {
+        const int u = tid - 2 * kBatchTW;
+        const int rr = 1 + u % kBatchBY;
+        const bool right = u >= kBatchBY;
+        const int hx = right ? x0 + kBatchTW : x0 - 1, hy = y0 + rr - 1;
+        hidx = rr * BW + (right ? kBatchD + kBatchTW : kBatchD - 1);
+        hld = hx <= g.nx && hy <= g.ny;
+        hoff = g.at(hx, hy, -1);
+    }
+    auto ld_own = [&](int k, T (&o)[V]) {   // k in [-1, nz]: boundary planes included
+        const T* p = src + rowoff + (int64_t)(k + 1) * g.plane;
+        o[0] = ld0 ? __ldcg(p) : T(0);
+        o[1] = ld1 ? __ldcg(p + 1) : T(0);
+    };
+    auto ld_halo = [&](int k) -> T { return hld ? __ldcg(src + hoff + (int64_t)(k + 1) * g.plane) : T(0); };
+    auto fix = [&](T v) -> Q {
+        if constexpr (CONV) return xs_fix(__double_as_longlong(v), emax);
+        else return v;
+    };
+
+    Q below[V], cur[V], above[V];
+    T craw[V], araw[V], nown[V], tt[V];
+    ld_own(kb - 1, tt);
+    below[0] = fix(tt[0]);
+    below[1] = fix(tt[1]);
+    ld_own(kb, tt);
+    craw[0] = tt[0];
+    craw[1] = tt[1];
+    cur[0] = fix(tt[0]);
+    cur[1] = fix(tt[1]);
+    {
+        Q* b0 = buf + (kb & 1) * kBatchPlane;
+        b0[own] = cur[0];
+        b0[own + 1] = cur[1];
+        if (hidx >= 0) b0[hidx] = fix(ld_halo(kb));
+    }
+    ld_own(kb + 1, araw);
+    T h1 = ld_halo(kb + 1), nh = T(0);
+    nown[0] = T(0);
+    nown[1] = T(0);
+    if (kb + 2 <= ke) {
+        ld_own(kb + 2, nown);
+        nh = ld_halo(kb + 2);
+    }
+    above[0] = fix(araw[0]);
+    above[1] = fix(araw[1]);
+    __syncthreads();
+
+    unsigned mx = 0;
+    T* out = dst + rowoff + (int64_t)(kb + 1) * g.plane;   // plane kb
+    for (int k = kb; k < ke; ++k) {
+        Q* bn = buf + ((k + 1) & 1) * kBatchPlane;   // plane k+1, read in the next iteration
+        bn[own] = above[0];
+        bn[own + 1] = above[1];
+        if (hidx >= 0) bn[hidx] = fix(h1);
+        const Q* pc = buf + (k & 1) * kBatchPlane + own;
+        const Q ym0 = pc[-BW], ym1 = pc[1 - BW], yp0 = pc[BW], yp1 = pc[1 + BW];
+        const Q left = pc[-1], right = pc[V];
+        T v[V];
+        if constexpr (CONV) {
+            const long long L0 = xs_numerator(cur[0], left, cur[1], ym0, yp0, below[0], above[0]);
+            const long long L1 = xs_numerator(cur[1], cur[0], right, ym1, yp1, below[1], above[1]);
+            v[0] = xs_apply<true>(craw[0], L0, r, r2, emax);
+            v[1] = xs_apply<false>(craw[1], L1, r, r2, emax);
+            const unsigned a0 = ok0 ? xs_abs_hi(v[0]) : 0u, a1 = ok1 ? xs_abs_hi(v[1]) : 0u;
+            mx = max(mx, max(a0, a1));
         } else {
-            v = Point<T, false>::update(cur, xm, xp, ym, yp, below, above, r, 0);
+            const T rr = (T)r;
+            v[0] = Point<T, false>::update(cur[0], left, cur[1], ym0, yp0, below[0], above[0], rr, 0);
+            v[1] = Point<T, false>::update(cur[1], cur[0], right, ym1, yp1, below[1], above[1], rr, 0);
+            if constexpr (KIND == K_F64_XS_NATIVE) {
+                const unsigned a0 = ok0 ? xs_abs_hi(v[0]) : 0u, a1 = ok1 ? xs_abs_hi(v[1]) : 0u;
+                mx = max(mx, max(a0, a1));
+            }
         }
-        dst[c] = v;
-        below = cur;
-        cur = above;
-        c += P;
+        if (ok1) {
+            st_pair(out, v);
+        } else if (ok0) {
+            out[0] = v[0];
+        }
+        out += g.plane;
+        below[0] = cur[0];
+        below[1] = cur[1];
+        cur[0] = above[0];
+        cur[1] = above[1];
+        craw[0] = araw[0];
+        craw[1] = araw[1];
+        araw[0] = nown[0];
+        araw[1] = nown[1];
+        above[0] = fix(nown[0]);
+        above[1] = fix(nown[1]);
+        h1 = nh;
+        if (k + 3 <= ke) {
+            ld_own(k + 3, nown);
+            nh = ld_halo(k + 3);
+        }
+        __syncthreads();
     }
     return mx;
 }
 
-__global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
+__global__ void __launch_bounds__(kBatchBX* kBatchBY, 4) k_heat_batch(BatchDev B)
 {
+    __shared__ __align__(16) long long sbuf[2 * kBatchPlane];
     __shared__ long long s_item;
     __shared__ int s_abort;
     const int tid = threadIdx.y * kBatchBX + threadIdx.x;
@@ -152,12 +282,15 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
         __syncthreads();
         if (s_abort) break;
         if (G.kind == K_F64_XS) {
-            const unsigned mx = batch_tile<double, true>(G, m, t);
+            // fields outside the convertible exponent range take the FP64 pipe
+            const unsigned mx = xs_native(xs_emax(G.fx, (G.m3 + m) % 3), G.r)
+                                    ? batch_tile<double, K_F64_XS_NATIVE>(G, m, t, sbuf)
+                                    : batch_tile<double, K_F64_XS>(G, m, t, sbuf);
             fx_finish<kBatchBX * kBatchBY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
         } else if (G.kind == K_F64_PIPE) {
-            batch_tile<double, false>(G, m, t);
+            batch_tile<double, K_F64_PIPE>(G, m, t, sbuf);
         } else {
-            batch_tile<float, false>(G, m, t);
+            batch_tile<float, K_F32>(G, m, t, sbuf);
         }
         __threadfence();
         __syncthreads();
@@ -168,6 +301,24 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY) k_heat_batch(BatchDev B)
 }  // namespace hcg
 
 using namespace hcg;
+
+namespace {
+
+// Planes per work item when the caller leaves it to the library: a grid with
+// few column tiles splits each step into z-chunks of at least 16 planes, so
+// that about 16 items share a step and the chain of its steps (each waits for
+// the one before) does not hang on one block marching the whole column.
+int batch_default_kz(const HeatGeom& g, int tiles_xy)
+{
+    const int want = 16;
+    if (tiles_xy >= want) return g.nz;
+    const int chunks = (want + tiles_xy - 1) / tiles_xy;
+    int kz = (g.nz + chunks - 1) / chunks;
+    if (kz < 16) kz = 16;
+    return kz < g.nz ? kz : g.nz;
+}
+
+}  // namespace
 
 struct hs_batch {
     cudaStream_t stream;
@@ -203,6 +354,12 @@ int heat_batch_destroy(hs_batch_t b)
 int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps, int32_t n,
                       void* stream)
 {
+    return heat_batch_create_tiled(out, grids, steps, nullptr, n, stream);
+}
+
+int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps,
+                            const int32_t* kz, int32_t n, void* stream)
+{
     if (!out) return fail(HS_EINVAL, "heat_batch_create: out is NULL");
     *out = nullptr;
     if (!grids || !steps || n < 1) return fail(HS_EINVAL, "heat_batch_create: no grids");
@@ -229,9 +386,11 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
         G.fx = v.fx;
         G.cur = 0;   // cur and m3 are set at each run
         G.m3 = 0;
-        G.pad = 0;
-        G.tiles_x = (v.g.nx + kBatchBX - 1) / kBatchBX;
-        G.tiles = G.tiles_x * ((v.g.ny + kBatchBY - 1) / kBatchBY);
+        G.tiles_x = (v.g.nx + kBatchTW - 1) / kBatchTW;
+        G.tiles_xy = G.tiles_x * ((v.g.ny + kBatchBY - 1) / kBatchBY);
+        if (kz && kz[i] < 0) return fail(HS_EINVAL, "heat_batch_create: kz[%d] < 0", i);
+        G.kz = (kz && kz[i]) ? std::min(kz[i], v.g.nz) : batch_default_kz(v.g, G.tiles_xy);
+        G.tiles = G.tiles_xy * ((v.g.nz + G.kz - 1) / G.kz);
         G.steps = steps[i];
         if (steps[i] > max_steps) max_steps = steps[i];
         lups += (int64_t)v.g.nx * v.g.ny * v.g.nz * steps[i];

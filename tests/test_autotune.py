@@ -1,6 +1,7 @@
-"""The temporal-depth autotuner: picks the fastest measured depth, caches it
-by GPU, arithmetic and size class, and reuses the cache (CPU, fake timer)."""
-from paper_2608_11882_gb300.autotune import Tuner, key, size_class
+"""The autotuner: picks the fastest measured (depth, planes per block) for a
+single grid and the fastest planes per batched work item, caches them by GPU,
+arithmetic and size class, and reuses the cache (CPU, fake timers)."""
+from paper_2608_11882_gb300.autotune import CANDIDATES, Tuner, batch_kz_for, key, size_class
 
 
 def test_size_class_rounds_edges_up_to_powers_of_two():
@@ -10,16 +11,36 @@ def test_size_class_rounds_edges_up_to_powers_of_two():
 
 def test_picks_fastest_and_caches(tmp_path):
     calls = []
+    table = {(1, 1.0): 3.0, (1, 0.5): 2.5, (1, 2.0): 4.0, (2, 1.0): 1.0, (3, 1.0): 2.0, (4, 1.0): 5.0}
 
-    def timer(arith, shape, d):
-        calls.append(d)
-        return {1: 3.0, 2: 1.0, 3: 2.0, 4: 5.0}[d]
+    def timer(arith, shape, d, f):
+        calls.append((d, f))
+        return table[(d, f)]
 
     t = Tuner(tmp_path / "c.json", timer=timer, gpu_name="fake")
-    assert t.best_depth("f32", (100, 100, 100)) == 2
-    assert sorted(calls) == [1, 2, 3, 4]
+    assert t.best("f32", (100, 100, 100)) == {"depth": 2, "kc_factor": 1.0}
+    assert sorted(calls) == sorted(CANDIDATES)
     t2 = Tuner(tmp_path / "c.json", timer=lambda *a: 1 / 0, gpu_name="fake")
     assert t2.best_depth("f32", (120, 90, 100)) == 2          # same size class, from the file
-    assert t2.cache["fake|f32|128x128x128"]["seconds_per_step"]["4"] == 5.0
+    assert t2.cache["fake|f32|128x128x128"]["seconds_per_step"]["4x1.0"] == 5.0
     calls.clear()
-    assert t.best_depth("f32", (100, 100, 100), retune=True) == 2 and len(calls) == 4
+    assert t.best_depth("f32", (100, 100, 100), retune=True) == 2 and len(calls) == len(CANDIDATES)
+    table[(1, 0.5)] = 0.5
+    assert t.best("f64", (100, 100, 100)) == {"depth": 1, "kc_factor": 0.5}
+
+
+def test_batch_kz_picks_fastest_and_caches(tmp_path):
+    seen = []
+
+    def bt(arith, shape, kz):
+        seen.append(kz)
+        return {0: 3.0, 40: 2.0, 32: 1.5, 16: 1.0}[kz]
+
+    t = Tuner(tmp_path / "c.json", batch_timer=bt, gpu_name="fake")
+    # nz = 40: whole columns (40) and chunks of 64 coincide; 32 and 16 are distinct
+    assert t.best_batch_kz("f64", (40, 20, 30)) == 16
+    assert sorted(seen) == [0, 16, 32, 40]
+    t2 = Tuner(tmp_path / "c.json", batch_timer=lambda *a: 1 / 0, gpu_name="fake")
+    assert t2.best_batch_kz("f64", (60, 30, 17)) == 16   # same class (64x32x32), cached choice
+    assert batch_kz_for((40, 1, 1), -1) == 40 and batch_kz_for((40, 1, 1), 64) == 40
+    assert batch_kz_for((40, 1, 1), 0) == 0

@@ -145,3 +145,30 @@ def test_bounded_step_wait_runs_out_then_recovers(pkg):
         h.close()
     with pytest.raises(pkg.HeatCGError):
         nat.heat_batch_set_wait_limit(-1)
+
+
+@pytest.mark.parametrize("kz", [1, 3, 16, 0])
+def test_z_chunked_items_equal_alone_bitwise(pkg, kz):
+    """Work items split into z-chunks of kz planes (1 = one plane per item;
+    0 = the library's choice, which splits grids of few column tiles): the
+    same bits as each grid stepped alone."""
+    specs = draw_batch(8, seed=9, edge=(5, 70), steps=(2, 25))
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs], kz=[kz] * len(specs)) as b:
+        b.run(use_graph=True).wait()
+    for s, h in zip(specs, heats):
+        assert np.array_equal(h.read(), alone(pkg, s, s["steps"]))
+        h.close()
+
+
+def test_tuned_batch_equals_alone(pkg, tmp_path, monkeypatch):
+    from paper_2608_11882_gb300 import autotune
+    monkeypatch.setattr(autotune, "_DEFAULT_CACHE", tmp_path / "tune.json")
+    specs = draw_batch(4, seed=10, edge=(16, 48), steps=(5, 20))
+    heats = make_heats(pkg, specs)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs], kz="auto") as b:
+        assert len(b.kz) == 4
+        b.run().wait()
+    for s, h in zip(specs, heats):
+        assert np.array_equal(h.read(), alone(pkg, s, s["steps"]))
+        h.close()
