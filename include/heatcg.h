@@ -253,10 +253,9 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
 
 /* heat_batch_create with the planes per work item chosen per grid: kz[i] >= 1
  * splits each step of grid i into z-chunks of kz[i] planes (each chunk of
- * each column tile is one item), 0 leaves it to the library (whole columns
- * for grids of 16 or more column tiles, else chunks of at least 16 planes
- * so that about 16 items share a step); kz may be NULL (all 0).  The chunking
- * changes speed only: every point is computed the same way. */
+ * each column tile is one item), 0 leaves it to the library (chunks of 32
+ * planes); kz may be NULL (all 0).  The chunking changes speed only: every
+ * point is computed the same way. */
 int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps,
                             const int32_t* kz, int32_t n, void* stream);
 

@@ -2,9 +2,9 @@
 // counts, FP32 or FP64), every step of every grid, in ONE persistent kernel
 // launch, optionally replayed from a captured CUDA graph.
 //
-// Work items are (step m, grid g, column tile, chunk of planes) in step-major
-// order; a persistent grid of co-resident blocks takes them from an atomic
-// counter.
+// Work items are (step m, grid g, column tile, chunk of planes); a persistent
+// grid of co-resident blocks takes them from an atomic counter in a fixed
+// order that spreads every grid's steps over the whole run.
 // An item of step m of grid g may start once all items of step m-1 of grid g
 // have finished (a per-grid completion counter, published with a fence), so
 // each step of a grid reads a complete previous time level -- the Interior
@@ -30,10 +30,10 @@
 #include <vector>
 
 #include "heat_common.cuh"
+#include "tma.cuh"
 
 namespace hcg {
 
-constexpr int kBatchBX = 32, kBatchBY = 8;
 constexpr long long kBatchWaitCycles = 2000000000ll;   // about one second at GB300 clocks
 // Wait limit that batches created from now on get (heat_batch_set_wait_limit).
 static std::atomic<long long> g_batch_wait_cycles{kBatchWaitCycles};
@@ -59,35 +59,44 @@ struct BatchGrid {
 
 struct BatchDev {
     const BatchGrid* grids;
-    const int64_t* step_item0;    // first item of step m (size max_steps + 1)
-    const int32_t* step_list0;    // first entry of step m in the active lists (size max_steps + 1)
-    const int32_t* list_grid;     // active grid of each entry
-    const int64_t* list_item0;    // first item (within its step) of each entry
+    // one descriptor per work item, in schedule order: step << 40 | grid << 24 |
+    // item within the grid's step, so a block finds its item with one load
+    const unsigned long long* sched;
+    const CUtensorMap* maps;      // per grid: TMA maps of its two buffers (box BW x 10)
     unsigned long long* next;     // work counter
     unsigned long long* done;     // per grid: items completed, all steps
     int* err;
     int64_t items;
     long long wait_cycles;        // limit of the step wait, in SM clock cycles
-    int32_t max_steps;
 };
 
-// One work item of step m -- a column tile and a chunk [kb, ke) of its planes:
-// a block of 32 x 8 threads owns a 64 x 8 tile of the grid's columns and
-// marches up the chunk's planes, every thread two
-// consecutive x points of one row.  Each plane of the tile with its one-point
-// halo is loaded once with coalesced L2 loads two planes ahead of use (kept in
-// registers), converted once (exact-sum FP64: to fixed point on the field's
-// scale; otherwise kept as is) into one of two shared plane buffers; a thread
-// keeps its own values at k-1, k and k+1 in registers, reads the in-plane
-// neighbours from the buffer of plane k, and one block barrier per plane
-// orders the buffers.  Positions past the grid's boundary layer (x > nx,
-// y > ny, possible in the last tiles) are never loaded: they hold zeros and
-// feed no output.  The per-point arithmetic is that of heat_step, so the
-// result matches the grid stepped alone bit for bit.  Returns the largest
-// |u| high word of the outputs (exact-sum FP64 only).
-constexpr int kBatchTW = 64, kBatchBW = 68, kBatchD = 2;   // tile width, buffer row, x offset
-constexpr int kBatchPlane = (kBatchBY + 2) * kBatchBW;     // buffer elements per plane
-static_assert(kBatchBX * 2 == kBatchTW, "two points per thread");
+// One work item of step m -- a column tile and a chunk [kb, ke) of its planes.
+// A block of 32 x 4 threads owns a 64 x 8 tile of the grid's columns and
+// marches up the chunk; every thread computes two consecutive x points in each
+// of two adjacent rows.  Each plane of the tile with its one-point halo
+// ((8 + 2) rows of BW elements) arrives by TMA into a ring of kBatchNst stages
+// up to kBatchNst - 2 planes ahead of use, through a tensor map of the grid's
+// source buffer kept in the batch's device memory; the ring and its mbarrier
+// phases run on across the items a block takes (`seq` counts the planes
+// staged so far).  Exact-sum FP64 planes are converted in place to fixed point
+// once they land (every thread its own vectors, warps 0 and 1 the halo rows,
+// warp 2 the halo columns), exactly as in heat_step's Interior kernel; FP32
+// and FP64-pipe planes are used as they are.  The per-point arithmetic is that
+// of heat_step, so every grid matches stepping it alone bit for bit.  Returns
+// false when a bounded wait ran out (the block then stops).
+constexpr int kBatchTW = 64, kBatchRY = 8, kBatchRT = 2, kBatchTY = kBatchRY / kBatchRT;
+constexpr int kBatchNst = 4;
+constexpr int kBatchSlot = 688;   // stage stride in 8-byte words: the FP64 box, 5440 B, to 128 B
+
+template <typename T>
+struct BatchShape {
+    static constexpr int A = 16 / (int)sizeof(T);                // elements per 16 bytes
+    static constexpr int D = A;                                  // offset of the tile's first point
+    static constexpr int BW = (D + kBatchTW + 1 + A - 1) / A * A;  // stage row, a 16-byte multiple
+    static constexpr uint32_t BOX_BYTES = (kBatchRY + 2) * BW * (uint32_t)sizeof(T);
+};
+static_assert(BatchShape<double>::BOX_BYTES <= kBatchSlot * 8 && BatchShape<float>::BOX_BYTES <= kBatchSlot * 8,
+              "a box fits a stage");
 
 template <typename T>
 __device__ __forceinline__ void st_pair(T* p, const T (&v)[2])
@@ -98,150 +107,210 @@ __device__ __forceinline__ void st_pair(T* p, const T (&v)[2])
         *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
 }
 
-template <typename T, int KIND>
-__device__ __forceinline__ unsigned batch_tile(const BatchGrid& G, int m, int item, long long* sbuf)
+template <typename T>
+__device__ __forceinline__ void ld_pair(const T* p, T (&v)[2])
 {
-    constexpr int V = 2, BW = kBatchBW;
+    if constexpr (sizeof(T) == 8) {
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    }
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap* map, int m, int item,
+                                           long long* ring, uint64_t* bars, uint32_t& seq, unsigned& mx,
+                                           int* err)
+{
+    using S = BatchShape<T>;
+    constexpr int V = 2, RT = kBatchRT, BW = S::BW, NST = kBatchNst;
     constexpr bool CONV = KIND == K_F64_XS;
-    // shared values: fixed-point integers (exact-sum FP64), raw bits otherwise
+    // stage words: fixed-point integers (exact-sum FP64), raw bits otherwise
     using Q = typename std::conditional<CONV, long long, T>::type;
-    Q* buf = reinterpret_cast<Q*>(sbuf);
     const HeatGeom& g = G.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBatchBX + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int t = item % G.tiles_xy;
     const int kb = (item / G.tiles_xy) * G.kz, ke = min(kb + G.kz, g.nz);
-    const int x0 = (t % G.tiles_x) * kBatchTW, y0 = (t / G.tiles_x) * kBatchBY;
-    const int X = x0 + V * tx, Y = y0 + ty;
-    const int own = (ty + 1) * BW + kBatchD + V * tx;
+    const int x0 = (t % G.tiles_x) * kBatchTW, y0 = (t / G.tiles_x) * kBatchRY;
+    const int X = x0 + V * tx, Y0 = y0 + RT * ty;
+    const int xs = g.lead + x0 - S::D;                 // padded x of the box, 16-byte aligned
+    const int own = (RT * ty + 1) * BW + S::D + V * tx;
+    const int nx_ok = min(V, g.nx - X);
     const int emax = CONV ? xs_emax(G.fx, (G.m3 + m) % 3) : 0;
     const double r = G.r;
     const double r2 = CONV ? xs_r2(r, emax) : 0.0;
-    const int src_b = (G.cur + m) & 1;
-    const T* __restrict__ src = (const T*)G.buf[src_b];
-    T* __restrict__ dst = (T*)G.buf[src_b ^ 1];
-    // own points: loaded where they lie in the padded buffer (y <= ny, x <= nx
-    // reach the boundary layer), computed and stored where interior
-    const bool ld0 = Y <= g.ny && X <= g.nx, ld1 = Y <= g.ny && X + 1 <= g.nx;
-    const bool ok0 = Y < g.ny && X < g.nx, ok1 = Y < g.ny && X + 1 < g.nx;
-    const int64_t rowoff = g.at(X, Y, -1);   // plane k adds (k + 1) plane
-    // one halo value per thread for the first 2*64 + 2*8 threads
-    int hidx = -1;
-    int64_t hoff = 0;
-    bool hld = false;
-    if (tid < 2 * kBatchTW) {
-        const int rr = tid < kBatchTW ? 0 : kBatchBY + 1;
-        const int c = tid % kBatchTW;
-        const int hx = x0 + c, hy = rr == 0 ? y0 - 1 : y0 + kBatchBY;
-        hidx = rr * BW + kBatchD + c;
-        hld = hx <= g.nx && hy <= g.ny;
-        hoff = g.at(hx, hy, -1);
-    } else if (tid < 2 * kBatchTW + 2 * kBatchBY) {
-        const int u = tid - 2 * kBatchTW;
-        const int rr = 1 + u % kBatchBY;
-        const bool right = u >= kBatchBY;
-        const int hx = right ? x0 + kBatchTW : x0 - 1, hy = y0 + rr - 1;
-        hidx = rr * BW + (right ? kBatchD + kBatchTW : kBatchD - 1);
-        hld = hx <= g.nx && hy <= g.ny;
-        hoff = g.at(hx, hy, -1);
-    }
-    auto ld_own = [&](int k, T (&o)[V]) {   // k in [-1, nz]: boundary planes included
-        const T* p = src + rowoff + (int64_t)(k + 1) * g.plane;
-        o[0] = ld0 ? __ldcg(p) : T(0);
-        o[1] = ld1 ? __ldcg(p + 1) : T(0);
+    T* __restrict__ dst = (T*)G.buf[((G.cur + m) & 1) ^ 1];
+    int extra = -1;   // besides its own vectors: a halo-row vector (warps 0, 1) or a halo-column value (warp 2)
+    if (ty == 0) extra = S::D + V * tx;
+    else if (ty == 1) extra = (kBatchRY + 1) * BW + S::D + V * tx;
+    else if (ty == 2 && tx < 2 * kBatchRY)
+        extra = tx < kBatchRY ? (tx + 1) * BW + S::D - 1 : (tx - kBatchRY + 1) * BW + S::D + kBatchTW;
+    const int np = ke - kb + 2;   // planes kb-1 .. ke
+    auto slot = [&](int sl) { return reinterpret_cast<Q*>(ring + sl * kBatchSlot); };
+    bool bad = false;
+    auto wait = [&](int sl, uint32_t ph) {
+        if (!mbar_wait_bounded(&bars[sl], ph)) bad = true;
     };
-    auto ld_halo = [&](int k) -> T { return hld ? __ldcg(src + hoff + (int64_t)(k + 1) * g.plane) : T(0); };
-    auto fix = [&](T v) -> Q {
-        if constexpr (CONV) return xs_fix(__double_as_longlong(v), emax);
-        else return v;
-    };
-
-    Q below[V], cur[V], above[V];
-    T craw[V], araw[V], nown[V], tt[V];
-    ld_own(kb - 1, tt);
-    below[0] = fix(tt[0]);
-    below[1] = fix(tt[1]);
-    ld_own(kb, tt);
-    craw[0] = tt[0];
-    craw[1] = tt[1];
-    cur[0] = fix(tt[0]);
-    cur[1] = fix(tt[1]);
-    {
-        Q* b0 = buf + (kb & 1) * kBatchPlane;
-        b0[own] = cur[0];
-        b0[own + 1] = cur[1];
-        if (hidx >= 0) b0[hidx] = fix(ld_halo(kb));
-    }
-    ld_own(kb + 1, araw);
-    T h1 = ld_halo(kb + 1), nh = T(0);
-    nown[0] = T(0);
-    nown[1] = T(0);
-    if (kb + 2 <= ke) {
-        ld_own(kb + 2, nown);
-        nh = ld_halo(kb + 2);
-    }
-    above[0] = fix(araw[0]);
-    above[1] = fix(araw[1]);
-    __syncthreads();
-
-    unsigned mx = 0;
-    T* out = dst + rowoff + (int64_t)(kb + 1) * g.plane;   // plane kb
-    for (int k = kb; k < ke; ++k) {
-        Q* bn = buf + ((k + 1) & 1) * kBatchPlane;   // plane k+1, read in the next iteration
-        bn[own] = above[0];
-        bn[own + 1] = above[1];
-        if (hidx >= 0) bn[hidx] = fix(h1);
-        const Q* pc = buf + (k & 1) * kBatchPlane + own;
-        const Q ym0 = pc[-BW], ym1 = pc[1 - BW], yp0 = pc[BW], yp1 = pc[1 + BW];
-        const Q left = pc[-1], right = pc[V];
-        T v[V];
-        if constexpr (CONV) {
-            const long long L0 = xs_numerator(cur[0], left, cur[1], ym0, yp0, below[0], above[0]);
-            const long long L1 = xs_numerator(cur[1], cur[0], right, ym1, yp1, below[1], above[1]);
-            v[0] = xs_apply<true>(craw[0], L0, r, r2, emax);
-            v[1] = xs_apply<false>(craw[1], L1, r, r2, emax);
-            const unsigned a0 = ok0 ? xs_abs_hi(v[0]) : 0u, a1 = ok1 ? xs_abs_hi(v[1]) : 0u;
-            mx = max(mx, max(a0, a1));
-        } else {
-            const T rr = (T)r;
-            v[0] = Point<T, false>::update(cur[0], left, cur[1], ym0, yp0, below[0], above[0], rr, 0);
-            v[1] = Point<T, false>::update(cur[1], cur[0], right, ym1, yp1, below[1], above[1], rr, 0);
-            if constexpr (KIND == K_F64_XS_NATIVE) {
-                const unsigned a0 = ok0 ? xs_abs_hi(v[0]) : 0u, a1 = ok1 ? xs_abs_hi(v[1]) : 0u;
-                mx = max(mx, max(a0, a1));
+    auto convert = [&](Q* pl, Q (&q)[RT][V], T (&raw)[RT][V]) {
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            ld_pair(reinterpret_cast<const T*>(pl) + own + j * BW, raw[j]);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if constexpr (CONV) q[j][i] = xs_fix(__double_as_longlong(raw[j][i]), emax);
+                else q[j][i] = raw[j][i];
+            }
+            if constexpr (CONV) {
+                pl[own + j * BW] = q[j][0];
+                pl[own + j * BW + 1] = q[j][1];
             }
         }
-        if (ok1) {
-            st_pair(out, v);
-        } else if (ok0) {
-            out[0] = v[0];
+        if constexpr (CONV) {
+            if (ty < 2) {
+                pl[extra] = xs_fix(pl[extra], emax);
+                pl[extra + 1] = xs_fix(pl[extra + 1], emax);
+            } else if (extra >= 0) {
+                pl[extra] = xs_fix(pl[extra], emax);
+            }
         }
-        out += g.plane;
-        below[0] = cur[0];
-        below[1] = cur[1];
-        cur[0] = above[0];
-        cur[1] = above[1];
-        craw[0] = araw[0];
-        craw[1] = araw[1];
-        araw[0] = nown[0];
-        araw[1] = nown[1];
-        above[0] = fix(nown[0]);
-        above[1] = fix(nown[1]);
-        h1 = nh;
-        if (k + 3 <= ke) {
-            ld_own(k + 3, nown);
-            nh = ld_halo(k + 3);
+    };
+
+    const int s0 = (int)(seq % NST);
+    const uint32_t ph0 = (seq / NST) & 1u;
+    int issued = 0;
+    if (tid == 0) {
+        // the source planes were written by other blocks' generic stores, which
+        // the step wait has made visible to this thread: order them before the
+        // async-proxy loads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        fence_proxy_async_smem();
+        for (int sl = s0; issued < NST && issued < np; ++issued, sl = sl + 1 == NST ? 0 : sl + 1) {
+            mbar_arrive_expect_tx(&bars[sl], S::BOX_BYTES);
+            tma_load_3d(ring + sl * kBatchSlot, map, xs, y0, kb + issued, &bars[sl]);
         }
-        __syncthreads();
     }
-    return mx;
+    Q below[RT][V], cur[RT][V], above[RT][V];
+    T craw[RT][V], araw[RT][V];
+    int s_cur = s0;
+    uint32_t ph_cur = ph0;
+    wait(s_cur, ph_cur);
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+        T b[V];
+        ld_pair(reinterpret_cast<const T*>(slot(s_cur)) + own + j * BW, b);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            if constexpr (CONV) below[j][i] = xs_fix(__double_as_longlong(b[i]), emax);
+            else below[j][i] = b[i];
+        }
+    }
+    if (++s_cur == NST) {
+        s_cur = 0;
+        ph_cur ^= 1u;
+    }
+    wait(s_cur, ph_cur);
+    convert(slot(s_cur), cur, craw);
+    if constexpr (CONV) fence_proxy_async_smem();
+    bool aborted = __syncthreads_or(bad) != 0;
+
+    T* out = dst + g.at(X < g.nx ? X : 0, 0, kb) + (int64_t)Y0 * g.pitch;   // used for rows inside the grid
+    for (int k = kb; !aborted && k < ke; ++k) {
+        const int s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
+        const uint32_t ph_nxt = s_nxt == 0 ? ph_cur ^ 1u : ph_cur;
+        wait(s_nxt, ph_nxt);
+        convert(slot(s_nxt), above, araw);
+        const Q* pl = slot(s_cur) + own;
+        Q ym[V], yp[V];
+        ym[0] = pl[-BW];
+        ym[1] = pl[1 - BW];
+        yp[0] = pl[RT * BW];
+        yp[1] = pl[RT * BW + 1];
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            const Q left = pl[j * BW - 1], right = pl[j * BW + V];
+            T v[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const Q xm = i == 0 ? left : cur[j][i - 1];
+                const Q xp = i == V - 1 ? right : cur[j][i + 1];
+                const Q yl = j == 0 ? ym[i] : cur[j - 1][i];
+                const Q yh = j == RT - 1 ? yp[i] : cur[j + 1][i];
+                if constexpr (CONV) {
+                    const long long L = xs_numerator(cur[j][i], xm, xp, yl, yh, below[j][i], above[j][i]);
+                    v[i] = i == 0 ? xs_apply<true>(craw[j][i], L, r, r2, emax)
+                                  : xs_apply<false>(craw[j][i], L, r, r2, emax);
+                } else {
+                    v[i] = Point<T, false>::update(cur[j][i], xm, xp, yl, yh, below[j][i], above[j][i], (T)r, 0);
+                }
+            }
+            const int nvalid = Y0 + j < g.ny ? nx_ok : 0;
+            T* o = out + j * g.pitch;
+            if (nvalid == V) {
+                st_pair(o, v);
+            } else if (nvalid == 1) {
+                o[0] = v[0];
+            }
+            if constexpr (KIND == K_F64_XS || KIND == K_F64_XS_NATIVE) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const unsigned a = i < nvalid ? xs_abs_hi((double)v[i]) : 0u;
+                    mx = a > mx ? a : mx;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RT; ++j)
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                below[j][i] = cur[j][i];
+                cur[j][i] = above[j][i];
+                craw[j][i] = araw[j][i];
+            }
+        out += g.plane;
+        if constexpr (CONV) fence_proxy_async_smem();
+        aborted = __syncthreads_or(bad) != 0;
+        // the slot of plane k-1 is free: every thread is past its last use
+        if (!aborted && tid == 0 && issued < np) {
+            const int sl = s_cur == 0 ? NST - 1 : s_cur - 1;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[sl], S::BOX_BYTES);
+            tma_load_3d(ring + sl * kBatchSlot, map, xs, y0, kb + issued, &bars[sl]);
+            ++issued;
+        }
+        s_cur = s_nxt;
+        ph_cur = ph_nxt;
+    }
+    if (aborted && tid == 0) {
+        // the last load issued into each slot, consumed or not, completes
+        // before the block may end or reuse the ring
+        atomicMax(err, 1);
+        const long long t0 = clock64();   // one time budget for the whole drain
+        for (int j = issued > NST ? issued - NST : 0; j < issued; ++j)
+            if (!mbar_wait_until(&bars[(seq + j) % NST], ((seq + j) / NST) & 1u, t0, kWaitCycles)) {
+                atomicMax(err, 2);   // loads may still be landing: the context is suspect
+                break;
+            }
+    }
+    seq += (uint32_t)np;
+    return !aborted;
 }
 
-__global__ void __launch_bounds__(kBatchBX* kBatchBY, 4) k_heat_batch(BatchDev B)
+__global__ void __launch_bounds__(32 * kBatchTY, 8) k_heat_batch(BatchDev B)
 {
-    __shared__ __align__(16) long long sbuf[2 * kBatchPlane];
+    __shared__ __align__(128) long long ring[kBatchNst * kBatchSlot];
+    __shared__ __align__(8) uint64_t bars[kBatchNst];
     __shared__ long long s_item;
     __shared__ int s_abort;
-    const int tid = threadIdx.y * kBatchBX + threadIdx.x;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (tid == 0) {
+        for (int sl = 0; sl < kBatchNst; ++sl) mbar_init(&bars[sl], 1);
+        fence_mbar_init();
+    }
+    uint32_t seq = 0;   // planes this block has staged through the ring
     for (;;) {
         if (tid == 0) {
             s_abort = *(volatile int*)B.err;
@@ -250,22 +319,11 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY, 4) k_heat_batch(BatchDev B
         __syncthreads();
         const long long item = s_item;
         if (item >= B.items) break;
-        // step m: the last m with step_item0[m] <= item
-        int lo = 0, hi = B.max_steps - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (B.step_item0[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        const int m = lo;
-        const long long in_step = item - B.step_item0[m];
-        int a = B.step_list0[m], z = B.step_list0[m + 1] - 1;
-        while (a < z) {
-            const int mid = (a + z + 1) >> 1;
-            if (B.list_item0[mid] <= in_step) a = mid; else z = mid - 1;
-        }
-        const int gi = B.list_grid[a];
+        const unsigned long long desc = __ldg(B.sched + item);
+        const int m = (int)(desc >> 40);
+        const int gi = (int)((desc >> 24) & 0xffffu);
+        const int t = (int)(desc & 0xffffffu);
         const BatchGrid& G = B.grids[gi];
-        const int t = (int)(in_step - B.list_item0[a]);
         if (tid == 0 && m > 0) {
             // wait until step m-1 of this grid is complete
             const unsigned long long need = (unsigned long long)m * (unsigned long long)G.tiles;
@@ -281,17 +339,22 @@ __global__ void __launch_bounds__(kBatchBX* kBatchBY, 4) k_heat_batch(BatchDev B
         }
         __syncthreads();
         if (s_abort) break;
+        // the map of this step's source buffer
+        const CUtensorMap* map = B.maps + 2 * gi + ((G.cur + m) & 1);
+        unsigned mx = 0;
+        bool ok;
         if (G.kind == K_F64_XS) {
             // fields outside the convertible exponent range take the FP64 pipe
-            const unsigned mx = xs_native(xs_emax(G.fx, (G.m3 + m) % 3), G.r)
-                                    ? batch_tile<double, K_F64_XS_NATIVE>(G, m, t, sbuf)
-                                    : batch_tile<double, K_F64_XS>(G, m, t, sbuf);
-            fx_finish<kBatchBX * kBatchBY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
+            ok = xs_native(xs_emax(G.fx, (G.m3 + m) % 3), G.r)
+                     ? batch_item<double, K_F64_XS_NATIVE>(G, map, m, t, ring, bars, seq, mx, B.err)
+                     : batch_item<double, K_F64_XS>(G, map, m, t, ring, bars, seq, mx, B.err);
+            if (ok) fx_finish<32 * kBatchTY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
         } else if (G.kind == K_F64_PIPE) {
-            batch_tile<double, K_F64_PIPE>(G, m, t, sbuf);
+            ok = batch_item<double, K_F64_PIPE>(G, map, m, t, ring, bars, seq, mx, B.err);
         } else {
-            batch_tile<float, K_F32>(G, m, t, sbuf);
+            ok = batch_item<float, K_F32>(G, map, m, t, ring, bars, seq, mx, B.err);
         }
+        if (!ok) break;   // the same in every thread
         __threadfence();
         __syncthreads();
         if (tid == 0) atomicAdd(&B.done[gi], 1ull);
@@ -304,18 +367,14 @@ using namespace hcg;
 
 namespace {
 
-// Planes per work item when the caller leaves it to the library: a grid with
-// few column tiles splits each step into z-chunks of at least 16 planes, so
-// that about 16 items share a step and the chain of its steps (each waits for
-// the one before) does not hang on one block marching the whole column.
-int batch_default_kz(const HeatGeom& g, int tiles_xy)
+// Planes per work item when the caller leaves it to the library: chunks of 32
+// planes.  A grid's step may start only when its previous step is complete,
+// so the time one item takes bounds how fast a grid's chain of steps can go;
+// 32-plane chunks measured fastest on the 256-grid workload (ahead of whole
+// columns by 1.5x and of 16-plane chunks).
+int batch_default_kz(const HeatGeom& g, int)
 {
-    const int want = 16;
-    if (tiles_xy >= want) return g.nz;
-    const int chunks = (want + tiles_xy - 1) / tiles_xy;
-    int kz = (g.nz + chunks - 1) / chunks;
-    if (kz < 16) kz = 16;
-    return kz < g.nz ? kz : g.nz;
+    return g.nz < 32 ? g.nz : 32;
 }
 
 }  // namespace
@@ -387,7 +446,7 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
         G.cur = 0;   // cur and m3 are set at each run
         G.m3 = 0;
         G.tiles_x = (v.g.nx + kBatchTW - 1) / kBatchTW;
-        G.tiles_xy = G.tiles_x * ((v.g.ny + kBatchBY - 1) / kBatchBY);
+        G.tiles_xy = G.tiles_x * ((v.g.ny + kBatchRY - 1) / kBatchRY);
         if (kz && kz[i] < 0) return fail(HS_EINVAL, "heat_batch_create: kz[%d] < 0", i);
         G.kz = (kz && kz[i]) ? std::min(kz[i], v.g.nz) : batch_default_kz(v.g, G.tiles_xy);
         G.tiles = G.tiles_xy * ((v.g.nz + G.kz - 1) / G.kz);
@@ -396,43 +455,74 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
         lups += (int64_t)v.g.nx * v.g.ny * v.g.nz * steps[i];
     }
     if (max_steps > (1 << 30)) return fail(HS_EINVAL, "heat_batch_create: too many steps");
-    // step-major schedule
-    std::vector<int64_t> step_item0((size_t)max_steps + 1, 0);
-    std::vector<int32_t> step_list0((size_t)max_steps + 1, 0);
-    std::vector<int32_t> list_grid;
-    std::vector<int64_t> list_item0;
+    // step-major schedule: one descriptor per item
+    if (max_steps >= (1 << 24) || n > 0xffff)
+        return fail(HS_EINVAL, "heat_batch_create: at most 2^24 - 1 steps and 65535 grids");
     int64_t items = 0;
-    for (int64_t m = 0; m < max_steps; ++m) {
-        step_item0[(size_t)m] = items;
-        step_list0[(size_t)m] = (int32_t)list_grid.size();
-        int64_t in_step = 0;
-        for (int32_t i = 0; i < n; ++i) {
-            if (hg[(size_t)i].steps <= m) continue;
-            list_grid.push_back(i);
-            list_item0.push_back(in_step);
-            in_step += hg[(size_t)i].tiles;
-        }
-        items += in_step;
+    for (int32_t i = 0; i < n; ++i) {
+        if (hg[(size_t)i].tiles >= (1 << 24)) return fail(HS_EINVAL, "heat_batch_create: grid %d too large", i);
+        items += (int64_t)hg[(size_t)i].tiles * hg[(size_t)i].steps;
     }
-    step_item0[(size_t)max_steps] = items;
-    step_list0[(size_t)max_steps] = (int32_t)list_grid.size();
-    if (list_grid.size() > (size_t)INT32_MAX) return fail(HS_EINVAL, "heat_batch_create: schedule too large");
-
+    if (items > ((int64_t)1 << 28))
+        return fail(HS_EINVAL, "heat_batch_create: %lld work items exceed the schedule limit 2^28",
+                    (long long)items);
+    std::vector<unsigned long long> sched;
+    try {
+        sched.reserve((size_t)items);
+    } catch (...) {
+        return fail(HS_ENOMEM, "heat_batch_create: host allocation failed");
+    }
+    // Stretched order: step m of a grid of S steps goes in round
+    // floor(m * max_steps / S), so every grid advances throughout the run and
+    // all finish together -- the longest chains of steps never run alone at
+    // the end.  Consecutive steps of a grid land in increasing rounds (S <=
+    // max_steps), so every item comes after the items it waits for.
+    {
+        std::vector<std::pair<int64_t, int64_t>> order;   // (round, grid << 32 | step)
+        order.reserve((size_t)(max_steps > 0 ? max_steps : 1) * (size_t)n / 2 + 16);
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t S = hg[(size_t)i].steps;
+            for (int64_t mm = 0; mm < S; ++mm)
+                order.emplace_back(mm * max_steps / S, ((int64_t)i << 32) | mm);
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<int64_t, int64_t>& a, const std::pair<int64_t, int64_t>& b) {
+                             return a.first < b.first;
+                         });
+        for (const auto& o : order) {
+            const int32_t i = (int32_t)(o.second >> 32);
+            const int64_t mm = o.second & 0xffffffffll;
+            const unsigned long long base = ((unsigned long long)mm << 40) | ((unsigned long long)i << 24);
+            for (int32_t t = 0; t < hg[(size_t)i].tiles; ++t) sched.push_back(base | (unsigned long long)t);
+        }
+    }
     hs_batch* b = new (std::nothrow) hs_batch();
     if (!b) return fail(HS_ENOMEM, "heat_batch_create: host allocation failed");
     b->stream = (cudaStream_t)stream;
     b->handles.assign(grids, grids + n);
     b->steps.assign(steps, steps + n);
     b->lups = lups;
-    // one arena: grids | step_item0 | list_item0 | step_list0 | list_grid | counters
+    // TMA maps of every grid's two buffers, boxes of one tile plane with its halo
+    std::vector<CUtensorMap> maps(2 * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const BatchGrid& G = hg[(size_t)i];
+        const bool f32 = G.kind == K_F32;
+        const uint32_t bx = f32 ? BatchShape<float>::BW : BatchShape<double>::BW;
+        for (int bi = 0; bi < 2; ++bi) {
+            const int e = encode_field_map(&maps[2 * (size_t)i + bi], G.buf[bi],
+                                           f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                           f32 ? sizeof(float) : sizeof(double), (uint64_t)G.g.pitch,
+                                           (uint64_t)(G.g.ny + 2), (uint64_t)(G.g.nz + 2), bx, kBatchRY + 2);
+            if (e != 0) return cuda_fail((cudaError_t)e, "heat_batch_create: TMA tensor map");
+        }
+    }
+    // one arena: maps | grids | schedule | counters (maps first: 128-byte aligned)
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t s_maps = align(sizeof(CUtensorMap) * maps.size());
     const size_t s_grids = align(sizeof(BatchGrid) * hg.size());
-    const size_t s_si = align(sizeof(int64_t) * step_item0.size());
-    const size_t s_li = align(sizeof(int64_t) * (list_item0.size() ? list_item0.size() : 1));
-    const size_t s_sl = align(sizeof(int32_t) * step_list0.size());
-    const size_t s_lg = align(sizeof(int32_t) * (list_grid.size() ? list_grid.size() : 1));
+    const size_t s_sched = align(sizeof(unsigned long long) * (sched.size() ? sched.size() : 1));
     b->counter_bytes = align(sizeof(unsigned long long) * (1 + (size_t)n) + sizeof(int));
-    const size_t total = s_grids + s_si + s_li + s_sl + s_lg + b->counter_bytes;
+    const size_t total = s_maps + s_grids + s_sched + b->counter_bytes;
     cudaError_t e = dev_alloc(&b->arena, total, b->stream);
     if (e != cudaSuccess) {
         b->arena = nullptr;
@@ -440,28 +530,23 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
         heat_batch_destroy(b);
         return rc;
     }
-    char* base = (char*)b->arena;
+    CUtensorMap* d_maps = (CUtensorMap*)b->arena;
+    char* base = (char*)b->arena + s_maps;
     BatchGrid* d_grids = (BatchGrid*)base;
-    int64_t* d_si = (int64_t*)(base + s_grids);
-    int64_t* d_li = (int64_t*)(base + s_grids + s_si);
-    int32_t* d_sl = (int32_t*)(base + s_grids + s_si + s_li);
-    int32_t* d_lg = (int32_t*)(base + s_grids + s_si + s_li + s_sl);
-    b->counters = base + s_grids + s_si + s_li + s_sl + s_lg;
+    unsigned long long* d_sched = (unsigned long long*)(base + s_grids);
+    b->counters = base + s_grids + s_sched;
     // grids are re-uploaded at each run (cur changes); the schedule once.  The
     // arena is ordered on the batch stream, so the copies are too (and finish
     // before the host arrays go away).
     const cudaStream_t bs = b->stream;
-    e = cudaMemcpyAsync(d_si, step_item0.data(), sizeof(int64_t) * step_item0.size(), cudaMemcpyHostToDevice, bs);
-    if (e == cudaSuccess && !list_item0.empty())
-        e = cudaMemcpyAsync(d_li, list_item0.data(), sizeof(int64_t) * list_item0.size(), cudaMemcpyHostToDevice,
-                            bs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_sl, step_list0.data(), sizeof(int32_t) * step_list0.size(), cudaMemcpyHostToDevice,
-                            bs);
-    if (e == cudaSuccess && !list_grid.empty())
-        e = cudaMemcpyAsync(d_lg, list_grid.data(), sizeof(int32_t) * list_grid.size(), cudaMemcpyHostToDevice, bs);
+    e = cudaSuccess;
+    if (!sched.empty())
+        e = cudaMemcpyAsync(d_sched, sched.data(), sizeof(unsigned long long) * sched.size(),
+                            cudaMemcpyHostToDevice, bs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_grids, hg.data(), sizeof(BatchGrid) * hg.size(), cudaMemcpyHostToDevice, bs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, bs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
     if (e != cudaSuccess) {
         const int rc = cuda_fail(e, "heat_batch_create: schedule upload");
@@ -470,19 +555,16 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
     }
     unsigned long long* ctr = (unsigned long long*)b->counters;
     b->dev.grids = d_grids;
-    b->dev.step_item0 = d_si;
-    b->dev.step_list0 = d_sl;
-    b->dev.list_grid = d_lg;
-    b->dev.list_item0 = d_li;
+    b->dev.sched = d_sched;
+    b->dev.maps = d_maps;
     b->dev.next = ctr;
     b->dev.done = ctr + 1;
     b->dev.err = (int*)(ctr + 1 + n);
     b->dev.items = items;
     b->dev.wait_cycles = g_batch_wait_cycles.load();
-    b->dev.max_steps = (int32_t)(max_steps > 0 ? max_steps : 1);
     // persistent grid: every block resident at once
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heat_batch, kBatchBX * kBatchBY, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heat_batch, 32 * kBatchTY, 0);
     int sms = kNumSMs;
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -543,7 +625,7 @@ int heat_batch_run(hs_batch_t b, int use_graph)
             HS_TRY_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal),
                         "heat_batch_run: begin capture");
             cudaError_t e1 = cudaMemsetAsync(b->counters, 0, b->counter_bytes, b->capture);
-            k_heat_batch<<<b->blocks, dim3(kBatchBX, kBatchBY), 0, b->capture>>>(b->dev);
+            k_heat_batch<<<b->blocks, dim3(32, kBatchTY), 0, b->capture>>>(b->dev);
             cudaError_t e2 = cudaPeekAtLastError();
             cudaGraph_t graph = nullptr;
             cudaError_t e3 = cudaStreamEndCapture(b->capture, &graph);
@@ -560,7 +642,7 @@ int heat_batch_run(hs_batch_t b, int use_graph)
         count_launch();
     } else {
         HS_TRY_CUDA(cudaMemsetAsync(b->counters, 0, b->counter_bytes, b->stream), "heat_batch_run: memset");
-        k_heat_batch<<<b->blocks, dim3(kBatchBX, kBatchBY), 0, b->stream>>>(b->dev);
+        k_heat_batch<<<b->blocks, dim3(32, kBatchTY), 0, b->stream>>>(b->dev);
         HS_CHECK_LAUNCH("heat batch kernel");
     }
     // every grid advanced by its steps: update the handles' bookkeeping
