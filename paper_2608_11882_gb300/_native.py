@@ -76,7 +76,7 @@ def _load():
         "heat_set_kchunk": [vp, i32],
         "heat_get_kchunk": [vp, ctypes.POINTER(i32)],
         "heat_batch_create_tiled": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
-                                    ctypes.POINTER(i32), i32, vp],
+                                    ctypes.POINTER(i32), ctypes.POINTER(i32), i32, vp],
         "heat_destroy": [vp],
         "op_apply": [ctypes.POINTER(hs_op), vp, vp, vp],
         "cg_spmv": [ctypes.POINTER(hs_op), vp, vp, ctypes.c_int, ctypes.POINTER(dbl), vp],
@@ -204,17 +204,20 @@ def heat_destroy(h: int) -> None:
     check(lib.heat_destroy(h), "heat_destroy")
 
 
-def heat_batch_create(handles, steps, stream: int = 0, kz=None) -> int:
-    """kz: planes per work item for each grid (0: the library's choice), or None."""
+def heat_batch_create(handles, steps, stream: int = 0, kz=None, tile_w=None) -> int:
+    """kz: planes per work item for each grid, tile_w: column-tile width (64 or
+    32) for each grid (0 or None: the library's choice)."""
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*handles)
     st = (ctypes.c_int64 * n)(*[int(s) for s in steps])
     b = ctypes.c_void_p()
-    if kz is None:
+    if kz is None and tile_w is None:
         check(lib.heat_batch_create(ctypes.byref(b), arr, st, n, stream), "heat_batch_create")
     else:
-        kza = (ctypes.c_int32 * n)(*[int(k) for k in kz])
-        check(lib.heat_batch_create_tiled(ctypes.byref(b), arr, st, kza, n, stream), "heat_batch_create_tiled")
+        kza = None if kz is None else (ctypes.c_int32 * n)(*[int(k) for k in kz])
+        twa = None if tile_w is None else (ctypes.c_int32 * n)(*[int(w) for w in tile_w])
+        check(lib.heat_batch_create_tiled(ctypes.byref(b), arr, st, kza, twa, n, stream),
+              "heat_batch_create_tiled")
     return b.value
 
 

@@ -168,19 +168,22 @@ class HeatBatch:
     """Several Heat handles advanced together by one persistent launch
     (heat_batch_create / heat_batch_run / heat_batch_wait)."""
 
-    def __init__(self, heats, steps, stream=None, kz=None):
-        """kz: planes per work item, per grid (a list; 0 = the library's choice),
-        "auto" for the autotuner's choice per grid size class, or None."""
+    def __init__(self, heats, steps, stream=None, kz=None, tile_w=None):
+        """kz: planes per work item and tile_w: column-tile width (64 or 32),
+        each a list with one value per grid (0 = the library's choice) or None;
+        kz="auto" takes both from the autotuner, per grid size class."""
         self.heats = list(heats)
         self.steps = [int(s) for s in steps]
         self.stream = _stream_handle(stream)
         if kz == "auto":
             from .autotune import Tuner
             t = Tuner()
-            kz = [t.best_batch_kz(h.dtype, h.shape) for h in self.heats]
-        self.kz = kz
+            picks = [t.best_batch(h.dtype, h.shape) for h in self.heats]
+            kz = [p["kz"] for p in picks]
+            tile_w = [p["tile_w"] for p in picks]
+        self.kz, self.tile_w = kz, tile_w
         self.handle = native.heat_batch_create([h.handle for h in self.heats], self.steps, self.stream,
-                                               kz=kz)
+                                               kz=kz, tile_w=tile_w)
 
     def run(self, use_graph: bool = True) -> "HeatBatch":
         native.heat_batch_run(self.handle, use_graph)

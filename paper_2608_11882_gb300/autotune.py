@@ -4,8 +4,8 @@ For a single grid it chooses the temporal depth (steps per pass over HBM: 1 =
 the Interior + Boundary kernels every step, 2..4 = the temporally blocked
 kernel) together with the Interior kernel's planes per block (the library's
 choice, half of it or twice it); for a grid inside a batch it chooses the
-planes per work item of the persistent batched kernel (whole columns, or
-z-chunks of 64, 32 or 16 planes, or the library's choice).  Each candidate is
+planes per work item and the column tile (64 x 8 or 32 x 16) of the
+persistent batched kernel (or the library's choice of both).  Each candidate is
 timed on the actual device on a short sample of steps of a grid of the same
 shape and arithmetic; the fastest is cached in a JSON file keyed by GPU name,
 arithmetic and size class, so later grids of that kind start from the cached
@@ -26,8 +26,9 @@ DEPTHS = (1, 2, 3, 4)
 # (depth, factor on the library's planes per Interior block); depth >= 2 passes
 # choose their own chunking
 CANDIDATES = ((1, 1.0), (1, 0.5), (1, 2.0), (2, 1.0), (3, 1.0), (4, 1.0))
-# planes per batched work item: 0 = the library's choice, -1 = whole columns
-BATCH_KZ = (0, -1, 64, 32, 16)
+# (planes per batched work item, column-tile width): 0 = the library's choice,
+# -1 = whole columns
+BATCH_CANDIDATES = ((0, 0), (32, 64), (16, 64), (-1, 64), (32, 32), (16, 32), (-1, 32))
 _DEFAULT_CACHE = Path(os.environ.get("HEATCG_TUNE_CACHE", Path.home() / ".cache" / "heatcg_tune.json"))
 _lock = threading.Lock()
 
@@ -50,8 +51,9 @@ def batch_kz_for(shape, choice: int) -> int:
 class Tuner:
     def __init__(self, cache_path: Path | str | None = None, timer=None, batch_timer=None,
                  gpu_name: str | None = None):
-        """timer(arith, shape, depth, kc_factor) and batch_timer(arith, shape, kz)
-        return seconds per step (defaults: CUDA-event timings on the device)."""
+        """timer(arith, shape, depth, kc_factor) and batch_timer(arith, shape, kz,
+        tile_w) return seconds per step (defaults: CUDA-event timings on the
+        device)."""
         self.path = Path(cache_path) if cache_path else _DEFAULT_CACHE
         self.timer = timer
         self.batch_timer = batch_timer
@@ -99,24 +101,28 @@ class Tuner:
     def best_depth(self, arith: str, shape, retune: bool = False) -> int:
         return self.best(arith, shape, retune)["depth"]
 
-    def best_batch_kz(self, arith: str, shape, retune: bool = False) -> int:
-        """Planes per work item (heat_batch_create_tiled's kz: 0 = the
-        library's choice) for a grid of this arithmetic ("f64" or "f32") and
-        shape inside a batch, timing every candidate if none is cached."""
+    def best_batch(self, arith: str, shape, retune: bool = False) -> dict:
+        """{"kz": planes per work item, "tile_w": column-tile width} for a grid of
+        this arithmetic ("f64" or "f32") and shape inside a batch (the
+        arguments of heat_batch_create_tiled; 0 = the library's choice), timing
+        every candidate if none is cached."""
         k = "batch|" + key(self.gpu, arith, shape)
-        if not retune and k in self.cache:
-            return batch_kz_for(shape, int(self.cache[k]["kz"]))
+        hit = self.cache.get(k)
+        if not retune and hit and "tile_w" in hit:
+            return {"kz": batch_kz_for(shape, int(hit["kz"])), "tile_w": int(hit["tile_w"])}
         timer = self.batch_timer or _gpu_batch_timer
-        cands = []
-        for c in BATCH_KZ:
-            kz = batch_kz_for(shape, c)
-            if c == 0 or kz not in [batch_kz_for(shape, x) for x in cands if x != 0]:
-                cands.append(c)
-        times = {c: float(timer(arith, shape, batch_kz_for(shape, c))) for c in cands}
-        best = min(times, key=times.get)
-        self.cache[k] = {"kz": best, "seconds_per_step": {str(c): t for c, t in times.items()}}
+        cands, seen = [], set()
+        for c, w in BATCH_CANDIDATES:
+            real = (batch_kz_for(shape, c), w)
+            if (c, w) == (0, 0) or real not in seen:
+                cands.append((c, w))
+                seen.add(real)
+        times = {cw: float(timer(arith, shape, batch_kz_for(shape, cw[0]), cw[1])) for cw in cands}
+        c, w = min(times, key=times.get)
+        self.cache[k] = {"kz": c, "tile_w": w,
+                         "seconds_per_step": {f"{a}x{b}": t for (a, b), t in times.items()}}
         self._save()
-        return batch_kz_for(shape, best)
+        return {"kz": batch_kz_for(shape, c), "tile_w": w}
 
 
 def _flags(pkg, arith):
@@ -149,9 +155,10 @@ def _gpu_timer(arith: str, shape, depth: int, kc_factor: float = 1.0, steps: int
         return e0.elapsed_time(e1) * 1e-3 / steps
 
 
-def _gpu_batch_timer(arith: str, shape, kz: int, copies: int = 8, steps: int = 32) -> float:
+def _gpu_batch_timer(arith: str, shape, kz: int, tile_w: int, copies: int = 8, steps: int = 32) -> float:
     """Seconds per step of a batch of `copies` grids of this shape advanced
-    together by heat_batch (planes per work item kz; 0 = the library's)."""
+    together by heat_batch (planes per work item kz, column-tile width tile_w;
+    0 = the library's choice)."""
     import numpy as np
     import torch
 
@@ -164,7 +171,7 @@ def _gpu_batch_timer(arith: str, shape, kz: int, copies: int = 8, steps: int = 3
         for h in heats:
             h.upload(u0.astype(h.np_dtype))
         s = torch.cuda.current_stream()
-        with pkg.HeatBatch(heats, [steps] * copies, stream=s, kz=[kz] * copies) as b:
+        with pkg.HeatBatch(heats, [steps] * copies, stream=s, kz=[kz] * copies, tile_w=[tile_w] * copies) as b:
             b.run(use_graph=False).wait()   # warm-up
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)

@@ -54,6 +54,8 @@ struct BatchGrid {
     int32_t tiles_xy;   // column tiles
     int32_t kz;         // planes per work item (the last chunk may be shorter)
     int32_t tiles;      // work items per step: column tiles x z-chunks
+    int32_t tw;         // tile width: 64 (64 x 8 tiles) or 32 (32 x 16)
+    int32_t pad;
     int64_t steps;
 };
 
@@ -84,19 +86,23 @@ struct BatchDev {
 // and FP64-pipe planes are used as they are.  The per-point arithmetic is that
 // of heat_step, so every grid matches stepping it alone bit for bit.  Returns
 // false when a bounded wait ran out (the block then stops).
-constexpr int kBatchTW = 64, kBatchRY = 8, kBatchRT = 2, kBatchTY = kBatchRY / kBatchRT;
+// Tiles are TW x TY columns: 64 x 8 (a warp per two rows of 64 points) or,
+// for narrow grids, 32 x 16 (half a warp per two rows of 32 points).
+constexpr int kBatchRT = 2, kBatchTY = 4;   // rows per thread, warps per block
 constexpr int kBatchNst = 4;
-constexpr int kBatchSlot = 688;   // stage stride in 8-byte words: the FP64 box, 5440 B, to 128 B
+constexpr int kBatchSlot = 688;   // stage stride in 8-byte words: the largest box, 5440 B, to 128 B
 
-template <typename T>
+template <typename T, int TW>
 struct BatchShape {
+    static constexpr int TY = TW == 64 ? 8 : 16;                 // tile rows
+    static constexpr int LPR = TW / 2;                           // lanes per tile row
     static constexpr int A = 16 / (int)sizeof(T);                // elements per 16 bytes
     static constexpr int D = A;                                  // offset of the tile's first point
-    static constexpr int BW = (D + kBatchTW + 1 + A - 1) / A * A;  // stage row, a 16-byte multiple
-    static constexpr uint32_t BOX_BYTES = (kBatchRY + 2) * BW * (uint32_t)sizeof(T);
+    static constexpr int BW = (D + TW + 1 + A - 1) / A * A;      // stage row, a 16-byte multiple
+    static constexpr uint32_t BOX_BYTES = (TY + 2) * BW * (uint32_t)sizeof(T);
+    static_assert(TY == kBatchTY * (32 / LPR) * kBatchRT, "the block covers the tile");
+    static_assert(BOX_BYTES <= kBatchSlot * 8, "a box fits a stage");
 };
-static_assert(BatchShape<double>::BOX_BYTES <= kBatchSlot * 8 && BatchShape<float>::BOX_BYTES <= kBatchSlot * 8,
-              "a box fits a stage");
 
 template <typename T>
 __device__ __forceinline__ void st_pair(T* p, const T (&v)[2])
@@ -121,13 +127,13 @@ __device__ __forceinline__ void ld_pair(const T* p, T (&v)[2])
     }
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, int TW>
 __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap* map, int m, int item,
                                            long long* ring, uint64_t* bars, uint32_t& seq, unsigned& mx,
                                            int* err)
 {
-    using S = BatchShape<T>;
-    constexpr int V = 2, RT = kBatchRT, BW = S::BW, NST = kBatchNst;
+    using S = BatchShape<T, TW>;
+    constexpr int V = 2, RT = kBatchRT, BW = S::BW, NST = kBatchNst, TY = S::TY, LPR = S::LPR;
     constexpr bool CONV = KIND == K_F64_XS;
     // stage words: fixed-point integers (exact-sum FP64), raw bits otherwise
     using Q = typename std::conditional<CONV, long long, T>::type;
@@ -135,20 +141,28 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int t = item % G.tiles_xy;
     const int kb = (item / G.tiles_xy) * G.kz, ke = min(kb + G.kz, g.nz);
-    const int x0 = (t % G.tiles_x) * kBatchTW, y0 = (t / G.tiles_x) * kBatchRY;
-    const int X = x0 + V * tx, Y0 = y0 + RT * ty;
+    const int x0 = (t % G.tiles_x) * TW, y0 = (t / G.tiles_x) * TY;
+    const int lx = tx % LPR, row0 = (ty * (32 / LPR) + tx / LPR) * RT;   // this thread's first row in the tile
+    const int X = x0 + V * lx, Y0 = y0 + row0;
     const int xs = g.lead + x0 - S::D;                 // padded x of the box, 16-byte aligned
-    const int own = (RT * ty + 1) * BW + S::D + V * tx;
+    const int own = (row0 + 1) * BW + S::D + V * lx;
     const int nx_ok = min(V, g.nx - X);
     const int emax = CONV ? xs_emax(G.fx, (G.m3 + m) % 3) : 0;
     const double r = G.r;
     const double r2 = CONV ? xs_r2(r, emax) : 0.0;
     T* __restrict__ dst = (T*)G.buf[((G.cur + m) & 1) ^ 1];
-    int extra = -1;   // besides its own vectors: a halo-row vector (warps 0, 1) or a halo-column value (warp 2)
-    if (ty == 0) extra = S::D + V * tx;
-    else if (ty == 1) extra = (kBatchRY + 1) * BW + S::D + V * tx;
-    else if (ty == 2 && tx < 2 * kBatchRY)
-        extra = tx < kBatchRY ? (tx + 1) * BW + S::D - 1 : (tx - kBatchRY + 1) * BW + S::D + kBatchTW;
+    // besides its own vectors: a halo-row vector (64-wide tiles: warps 0 and 1;
+    // 32-wide: warp 0, half a warp per row) or a halo-column value (the next warp)
+    int extra = -1;
+    bool xvec = false;
+    constexpr int HCW = TW == 64 ? 2 : 1;   // the warp that converts the halo columns
+    if (ty < HCW) {
+        const int hrow = TW == 64 ? (ty == 0 ? 0 : TY + 1) : (tx < LPR ? 0 : TY + 1);
+        extra = hrow * BW + S::D + V * lx;
+        xvec = true;
+    } else if (ty == HCW && tx < 2 * TY) {
+        extra = tx < TY ? (tx + 1) * BW + S::D - 1 : (tx - TY + 1) * BW + S::D + TW;
+    }
     const int np = ke - kb + 2;   // planes kb-1 .. ke
     auto slot = [&](int sl) { return reinterpret_cast<Q*>(ring + sl * kBatchSlot); };
     bool bad = false;
@@ -170,7 +184,7 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
             }
         }
         if constexpr (CONV) {
-            if (ty < 2) {
+            if (xvec) {
                 pl[extra] = xs_fix(pl[extra], emax);
                 pl[extra + 1] = xs_fix(pl[extra + 1], emax);
             } else if (extra >= 0) {
@@ -299,6 +313,19 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
     return !aborted;
 }
 
+template <int TW>
+__device__ __forceinline__ bool batch_dispatch(const BatchGrid& G, const CUtensorMap* map, int m, int t,
+                                               long long* ring, uint64_t* bars, uint32_t& seq, unsigned& mx,
+                                               int* err)
+{
+    if (G.kind == K_F64_XS)   // fields outside the convertible exponent range take the FP64 pipe
+        return xs_native(xs_emax(G.fx, (G.m3 + m) % 3), G.r)
+                   ? batch_item<double, K_F64_XS_NATIVE, TW>(G, map, m, t, ring, bars, seq, mx, err)
+                   : batch_item<double, K_F64_XS, TW>(G, map, m, t, ring, bars, seq, mx, err);
+    if (G.kind == K_F64_PIPE) return batch_item<double, K_F64_PIPE, TW>(G, map, m, t, ring, bars, seq, mx, err);
+    return batch_item<float, K_F32, TW>(G, map, m, t, ring, bars, seq, mx, err);
+}
+
 __global__ void __launch_bounds__(32 * kBatchTY, 8) k_heat_batch(BatchDev B)
 {
     __shared__ __align__(128) long long ring[kBatchNst * kBatchSlot];
@@ -342,18 +369,10 @@ __global__ void __launch_bounds__(32 * kBatchTY, 8) k_heat_batch(BatchDev B)
         // the map of this step's source buffer
         const CUtensorMap* map = B.maps + 2 * gi + ((G.cur + m) & 1);
         unsigned mx = 0;
-        bool ok;
-        if (G.kind == K_F64_XS) {
-            // fields outside the convertible exponent range take the FP64 pipe
-            ok = xs_native(xs_emax(G.fx, (G.m3 + m) % 3), G.r)
-                     ? batch_item<double, K_F64_XS_NATIVE>(G, map, m, t, ring, bars, seq, mx, B.err)
-                     : batch_item<double, K_F64_XS>(G, map, m, t, ring, bars, seq, mx, B.err);
-            if (ok) fx_finish<32 * kBatchTY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
-        } else if (G.kind == K_F64_PIPE) {
-            ok = batch_item<double, K_F64_PIPE>(G, map, m, t, ring, bars, seq, mx, B.err);
-        } else {
-            ok = batch_item<float, K_F32>(G, map, m, t, ring, bars, seq, mx, B.err);
-        }
+        const bool ok = G.tw == 64 ? batch_dispatch<64>(G, map, m, t, ring, bars, seq, mx, B.err)
+                                   : batch_dispatch<32>(G, map, m, t, ring, bars, seq, mx, B.err);
+        if (ok && G.kind == K_F64_XS)
+            fx_finish<32 * kBatchTY>((unsigned long long)mx << 32, G.fx, (G.m3 + m) % 3, 0, t == 0);
         if (!ok) break;   // the same in every thread
         __threadfence();
         __syncthreads();
@@ -375,6 +394,16 @@ namespace {
 int batch_default_kz(const HeatGeom& g, int)
 {
     return g.nz < 32 ? g.nz : 32;
+}
+
+// Tile width when the caller leaves it to the library: the one that stages
+// fewer values per plane (tiles with their halo rows and columns), so narrow
+// grids do not leave half of every warp idle.
+int batch_default_tw(const HeatGeom& g)
+{
+    const int64_t c64 = (int64_t)((g.nx + 63) / 64) * ((g.ny + 7) / 8) * 68 * 10;
+    const int64_t c32 = (int64_t)((g.nx + 31) / 32) * ((g.ny + 15) / 16) * 36 * 18;
+    return c32 < c64 ? 32 : 64;
 }
 
 }  // namespace
@@ -413,11 +442,11 @@ int heat_batch_destroy(hs_batch_t b)
 int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps, int32_t n,
                       void* stream)
 {
-    return heat_batch_create_tiled(out, grids, steps, nullptr, n, stream);
+    return heat_batch_create_tiled(out, grids, steps, nullptr, nullptr, n, stream);
 }
 
 int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64_t* steps,
-                            const int32_t* kz, int32_t n, void* stream)
+                            const int32_t* kz, const int32_t* tw, int32_t n, void* stream)
 {
     if (!out) return fail(HS_EINVAL, "heat_batch_create: out is NULL");
     *out = nullptr;
@@ -445,8 +474,12 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
         G.fx = v.fx;
         G.cur = 0;   // cur and m3 are set at each run
         G.m3 = 0;
-        G.tiles_x = (v.g.nx + kBatchTW - 1) / kBatchTW;
-        G.tiles_xy = G.tiles_x * ((v.g.ny + kBatchRY - 1) / kBatchRY);
+        if (tw && tw[i] != 0 && tw[i] != 32 && tw[i] != 64)
+            return fail(HS_EINVAL, "heat_batch_create: tile width %d of grid %d is not 0, 32 or 64", tw[i], i);
+        G.tw = (tw && tw[i]) ? tw[i] : batch_default_tw(v.g);
+        G.pad = 0;
+        G.tiles_x = (v.g.nx + G.tw - 1) / G.tw;
+        G.tiles_xy = G.tiles_x * ((v.g.ny + (G.tw == 64 ? 8 : 16) - 1) / (G.tw == 64 ? 8 : 16));
         if (kz && kz[i] < 0) return fail(HS_EINVAL, "heat_batch_create: kz[%d] < 0", i);
         G.kz = (kz && kz[i]) ? std::min(kz[i], v.g.nz) : batch_default_kz(v.g, G.tiles_xy);
         G.tiles = G.tiles_xy * ((v.g.nz + G.kz - 1) / G.kz);
@@ -507,12 +540,14 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
     for (int32_t i = 0; i < n; ++i) {
         const BatchGrid& G = hg[(size_t)i];
         const bool f32 = G.kind == K_F32;
-        const uint32_t bx = f32 ? BatchShape<float>::BW : BatchShape<double>::BW;
+        const uint32_t bx = G.tw == 64 ? (f32 ? BatchShape<float, 64>::BW : BatchShape<double, 64>::BW)
+                                       : (f32 ? BatchShape<float, 32>::BW : BatchShape<double, 32>::BW);
+        const uint32_t by = (G.tw == 64 ? BatchShape<double, 64>::TY : BatchShape<double, 32>::TY) + 2;
         for (int bi = 0; bi < 2; ++bi) {
             const int e = encode_field_map(&maps[2 * (size_t)i + bi], G.buf[bi],
                                            f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                                            f32 ? sizeof(float) : sizeof(double), (uint64_t)G.g.pitch,
-                                           (uint64_t)(G.g.ny + 2), (uint64_t)(G.g.nz + 2), bx, kBatchRY + 2);
+                                           (uint64_t)(G.g.ny + 2), (uint64_t)(G.g.nz + 2), bx, by);
             if (e != 0) return cuda_fail((cudaError_t)e, "heat_batch_create: TMA tensor map");
         }
     }

@@ -29,18 +29,19 @@ def test_picks_fastest_and_caches(tmp_path):
     assert t.best("f64", (100, 100, 100)) == {"depth": 1, "kc_factor": 0.5}
 
 
-def test_batch_kz_picks_fastest_and_caches(tmp_path):
+def test_batch_choice_picks_fastest_and_caches(tmp_path):
     seen = []
 
-    def bt(arith, shape, kz):
-        seen.append(kz)
-        return {0: 3.0, 40: 2.0, 32: 1.5, 16: 1.0}[kz]
+    def bt(arith, shape, kz, w):
+        seen.append((kz, w))
+        return {(0, 0): 3.0, (40, 64): 2.0, (32, 64): 1.5, (16, 64): 1.2,
+                (40, 32): 2.5, (32, 32): 1.4, (16, 32): 1.0}[(kz, w)]
 
     t = Tuner(tmp_path / "c.json", batch_timer=bt, gpu_name="fake")
-    # nz = 40: whole columns (40) and chunks of 64 coincide; 32 and 16 are distinct
-    assert t.best_batch_kz("f64", (40, 20, 30)) == 16
-    assert sorted(seen) == [0, 16, 32, 40]
+    # nz = 40: whole columns (40) and chunks of 32 or 16, each with both tile widths
+    assert t.best_batch("f64", (40, 20, 30)) == {"kz": 16, "tile_w": 32}
+    assert sorted(seen) == sorted([(0, 0), (32, 64), (16, 64), (40, 64), (32, 32), (16, 32), (40, 32)])
     t2 = Tuner(tmp_path / "c.json", batch_timer=lambda *a: 1 / 0, gpu_name="fake")
-    assert t2.best_batch_kz("f64", (60, 30, 17)) == 16   # same class (64x32x32), cached choice
+    assert t2.best_batch("f64", (60, 30, 17)) == {"kz": 16, "tile_w": 32}   # same class, cached
     assert batch_kz_for((40, 1, 1), -1) == 40 and batch_kz_for((40, 1, 1), 64) == 40
     assert batch_kz_for((40, 1, 1), 0) == 0

@@ -27,8 +27,8 @@ def test_tuner_on_a_real_handle_caches_and_keeps_results(pkg, tmp_path, monkeypa
     choice = t.best("f32", shape)
     assert choice["depth"] in autotune.DEPTHS and cache.exists()
     assert autotune.Tuner().best("f32", shape) == choice          # from the file
-    kz = t.best_batch_kz("f64", shape)
-    assert 0 <= kz <= nz
+    pick = t.best_batch("f64", shape)
+    assert 0 <= pick["kz"] <= nz and pick["tile_w"] in (0, 32, 64)
     with pkg.Heat(nx, ny, nz, 0.12, dtype="f32", tdepth="auto") as h:
         tuned = h.upload(u0.astype(np.float32)).step(30).read()
     with pkg.Heat(nx, ny, nz, 0.12, dtype="f32", tdepth=1) as h:

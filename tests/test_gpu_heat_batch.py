@@ -147,14 +147,15 @@ def test_bounded_step_wait_runs_out_then_recovers(pkg):
         nat.heat_batch_set_wait_limit(-1)
 
 
-@pytest.mark.parametrize("kz", [1, 3, 16, 0])
-def test_z_chunked_items_equal_alone_bitwise(pkg, kz):
+@pytest.mark.parametrize("kz,tw", [(1, 64), (3, 32), (16, 64), (16, 32), (0, 0), (0, 32)])
+def test_z_chunked_items_equal_alone_bitwise(pkg, kz, tw):
     """Work items split into z-chunks of kz planes (1 = one plane per item;
-    0 = the library's choice, which splits grids of few column tiles): the
-    same bits as each grid stepped alone."""
+    0 = the library's choice) over 64 x 8 or 32 x 16 column tiles (0: the
+    library's choice per grid): the same bits as each grid stepped alone."""
     specs = draw_batch(8, seed=9, edge=(5, 70), steps=(2, 25))
     heats = make_heats(pkg, specs)
-    with pkg.HeatBatch(heats, [s["steps"] for s in specs], kz=[kz] * len(specs)) as b:
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs], kz=[kz] * len(specs),
+                       tile_w=[tw] * len(specs)) as b:
         b.run(use_graph=True).wait()
     for s, h in zip(specs, heats):
         assert np.array_equal(h.read(), alone(pkg, s, s["steps"]))
