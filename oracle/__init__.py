@@ -67,7 +67,10 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(str(build()))
+        # ORACLE_LIB names another build of these sources: the mutation tests
+        # point it at copies with a planted mistake to show the pins catch it
+        override = os.environ.get("ORACLE_LIB")
+        lib = ctypes.CDLL(override if override else str(build()))
         dp = ctypes.c_void_p
         lib.oracle_heat_run.argtypes = [ctypes.c_int32] * 3 + [ctypes.c_double, ctypes.c_int64,
                                                                 dp, dp, ctypes.c_int32]
