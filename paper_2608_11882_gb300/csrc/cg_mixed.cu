@@ -9,7 +9,8 @@
 //
 // The CG of each inner solve is the textbook one of Section 7.5.  Its dot
 // products accumulate in FP64 across the grid; each thread adds at most 8
-// FP32 products before promoting them to its FP64 sum, so the long sums --
+// FP32 products (4 in the vectorised kernels) before promoting them to its
+// FP64 sum, so the long sums --
 // the part whose stability needs FP64 -- stay FP64 while the FP64 pipe (about
 // 1/64 of FP32 issue on this GPU) sees one add per 8 elements.  alpha, beta
 // and the residual norms are FP64 device scalars.  Refinement converges while
@@ -20,6 +21,7 @@
 #include <new>
 
 #include "cg_common.cuh"
+#include "tma.cuh"
 
 namespace hcg {
 
@@ -33,7 +35,9 @@ struct MxScalars {
     double rtol, inner_rtol;
     double inner_stop;    // the inner solve ends once r'.r' <= inner_stop
     int32_t outer_done;   // 1: ||b - A x|| / ||b|| <= rtol (or b = 0)
-    int32_t inner_done;   // 1: inner solve finished; 2: breakdown
+    int32_t inner_done;   // 1: inner solve finished; 2: breakdown; 3: a bounded wait of the
+                          // TMA-staged SpMV ran out; 4: that, and its loads in flight did not
+                          // complete in time
     int32_t iters;        // inner iterations, all solves
     uint32_t ticket;
     int32_t zero_rhs;
@@ -65,11 +69,16 @@ struct hcg::CgMixed {
     MxScalars* S_host;   // host mirror
     double inner_rtol;
     int32_t max_inner;
+    bool tma;            // the matrix-free SpMV stages p by TMA (nx a multiple of 4)
+    CUtensorMap pmap;    // TMA map of p (unpadded nx x ny x nz floats)
 };
 
 namespace hcg {
 
-// FP64 sum of FP32 products, promoted every 8 terms.
+// FP64 sum of FP32 products: add() promotes every 8 terms (one product at a
+// time), add4() sums four products in FP32 and promotes them at once -- one
+// conversion and one FP64 add per four products, with no per-product branch
+// that the compiler could turn into a conversion per product.
 struct Acc32 {
     double hi = 0.0;
     float lo = 0.0f;
@@ -82,6 +91,12 @@ struct Acc32 {
             lo = 0.0f;
             n = 0;
         }
+    }
+    __device__ __forceinline__ void add4(float a0, float b0, float a1, float b1, float a2, float b2, float a3,
+                                         float b3)
+    {
+        const float s = __fmaf_rn(a3, b3, __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0))));
+        hi += (double)s;
     }
     __device__ __forceinline__ double total() const { return hi + (double)lo; }
 };
@@ -194,27 +209,216 @@ __global__ void __launch_bounds__(kCgBlock)
             int64_t c = (int64_t)kb * sxy + (int64_t)j * nx + i;
             float below = kb > 0 ? __ldg(p + c - sxy) : 0.0f;
             float cur = __ldg(p + c);
-            for (int k = kb; k < ke; ++k) {
-                const float above = k < nz - 1 ? __ldg(p + c + sxy) : 0.0f;
-                const float ym = j > 0 ? __ldg(p + c - nx) : 0.0f;
-                const float xm = i > 0 ? __ldg(p + c - 1) : 0.0f;
-                const float xp = i < nx - 1 ? __ldg(p + c + 1) : 0.0f;
-                const float yp = j < ny - 1 ? __ldg(p + c + nx) : 0.0f;
-                const float sum = ((below + ym) + (xm + xp)) + (yp + above);
-                const float qv = __fmaf_rn(6.0f, cur, -sum);
-                q[c] = qv;
-                pq.add(cur, qv);
-                below = cur;
-                cur = above;
-                c += sxy;
+            // planes in groups of four: the four products are promoted together
+            for (int k4 = kb; k4 < ke; k4 += 4) {
+                float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f}, qs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k4 + u;
+                    if (k < ke) {
+                        const float above = k < nz - 1 ? __ldg(p + c + sxy) : 0.0f;
+                        const float ym = j > 0 ? __ldg(p + c - nx) : 0.0f;
+                        const float xm = i > 0 ? __ldg(p + c - 1) : 0.0f;
+                        const float xp = i < nx - 1 ? __ldg(p + c + 1) : 0.0f;
+                        const float yp = j < ny - 1 ? __ldg(p + c + nx) : 0.0f;
+                        const float sum = ((below + ym) + (xm + xp)) + (yp + above);
+                        const float qv = __fmaf_rn(6.0f, cur, -sum);
+                        q[c] = qv;
+                        pv[u] = cur;
+                        qs[u] = qv;
+                        below = cur;
+                        cur = above;
+                        c += sxy;
+                    }
+                }
+                pq.add4(pv[0], qs[0], pv[1], qs[1], pv[2], qs[2], pv[3], qs[3]);
             }
         }
     } else {
-        for (int64_t row = row0; row < A.n; row += stride) {
-            const float qv = apply32_csr(A, p, row);
-            q[row] = qv;
-            pq.add(__ldg(p + row), qv);
+        // rows row0, row0 + stride, ... in groups of four: the four products are promoted together
+        for (int64_t row4 = row0; row4 < A.n; row4 += 4 * stride) {
+            float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f}, qs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t row = row4 + u * stride;
+                if (row < A.n) {
+                    const float qv = apply32_csr(A, p, row);
+                    q[row] = qv;
+                    pv[u] = __ldg(p + row);
+                    qs[u] = qv;
+                }
+            }
+            pq.add4(pv[0], qs[0], pv[1], qs[1], pv[2], qs[2], pv[3], qs[3]);
         }
+    }
+    allow_dependents();
+    const double blk = block_sum<kCgBlock>(pq.total(), sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double tot = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->pq = tot;
+        if (!(tot > 0.0))
+            S->inner_done = 2;
+        else
+            S->alpha = S->rho / tot;
+    }
+}
+
+// The matrix-free FP32 SpMV with the planes of p staged by TMA: a block of 256
+// threads (8 warps) owns a tile of 128 x 8 points of the grid -- every lane
+// four consecutive x points of one row, one 16-byte vector -- and a chunk of
+// z-planes at a time, work items (tile, chunk) taken in a fixed order.  Each
+// plane of the tile with its one-point halo is one TMA box of (8 + 2) rows of
+// 136 floats starting 16 bytes left of the tile, over the unpadded vector, so
+// boxes that reach past the grid read zeros (the Dirichlet boundary).  Boxes
+// land in a ring of kMxNst stages up to kMxNst - 2 planes ahead of use; a
+// thread keeps its values at k-1, k and k+1 in registers and reads the rest
+// from the stage of plane k.  q = fma(6, p, -(((zm + ym) + (xm + xp)) + (yp +
+// zp))) point by point, as in the column kernel, so q is the same bit for bit.
+// Every mbarrier wait is bounded; one that runs out stops the inner solve
+// (inner_done 3) after the block's loads in flight have landed (4 if they do
+// not in time).
+constexpr int kMxTW = 128, kMxTY = 8, kMxD = 4, kMxBW = 136, kMxNst = 6;
+constexpr uint32_t kMxBoxBytes = (kMxTY + 2) * kMxBW * sizeof(float);
+constexpr int kMxStage = (int)((kMxBoxBytes + 127) / 128 * 128 / sizeof(float));
+static_assert(kMxBW * sizeof(float) % 16 == 0 && kMxD * sizeof(float) == 16, "TMA box geometry");
+static_assert(kMxTY * 32 == kCgBlock, "one warp per tile row");
+
+struct MxPlan {
+    int64_t tiles, items;
+    int tiles_x, kc;
+};
+
+__host__ __device__ inline MxPlan mx_plan(const OpDev32& A, int nblocks)
+{
+    MxPlan P;
+    P.tiles_x = (A.nx + kMxTW - 1) / kMxTW;
+    P.tiles = (int64_t)P.tiles_x * ((A.ny + kMxTY - 1) / kMxTY);
+    int64_t chunks = ((int64_t)nblocks + P.tiles - 1) / P.tiles;
+    const int64_t maxc = A.nz / 4 > 1 ? A.nz / 4 : 1;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    P.kc = (int)((A.nz + chunks - 1) / chunks);
+    chunks = (A.nz + P.kc - 1) / P.kc;
+    P.items = P.tiles * chunks;
+    return P;
+}
+
+__global__ void __launch_bounds__(kCgBlock)
+    k_mx_spmv_tma(const __grid_constant__ CUtensorMap map, OpDev32 A, float* __restrict__ q,
+                  double* partials, MxScalars* S)
+{
+    __shared__ __align__(128) float stage[kMxNst * kMxStage];
+    __shared__ __align__(8) uint64_t bars[kMxNst];
+    __shared__ double sh[kCgBlock / 32];
+    __shared__ int32_t s_done;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    grid_dependency_wait();   // p, the scalars and the stop flag come from the kernels before
+    if (tid == 0) {
+        s_done = *(volatile int32_t*)&S->inner_done;
+        for (int sl = 0; sl < kMxNst; ++sl) mbar_init(&bars[sl], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_done) return;
+    const MxPlan P = mx_plan(A, gridDim.x);
+    const int nx = A.nx, ny = A.ny;
+    const int64_t sxy = (int64_t)nx * ny;
+    uint32_t seq = 0;   // planes staged so far: plane j of the block sits in slot j % NST
+    bool bad = false, aborted = false, drained = true;
+    int issued = 0, np = 0;
+    Acc32 pq;
+    for (int64_t item = blockIdx.x; item < P.items && !aborted; item += gridDim.x) {
+        const int64_t tile = item % P.tiles;
+        const int kb = (int)(item / P.tiles) * P.kc, ke = min(kb + P.kc, A.nz);
+        const int x0 = (int)(tile % P.tiles_x) * kMxTW, y0 = (int)(tile / P.tiles_x) * kMxTY;
+        const int X = x0 + 4 * tx, Y = y0 + ty;
+        const int own = (ty + 1) * kMxBW + kMxD + 4 * tx;
+        const int nvalid = Y < ny ? min(4, nx - X) : 0;   // nx % 4 == 0: 4 or none
+        np = ke - kb + 2;                                // planes kb-1 .. ke
+        issued = 0;
+        auto wait = [&](int j) {
+            const uint32_t g = seq + (uint32_t)j;
+            if (!mbar_wait_bounded(&bars[g % kMxNst], (g / kMxNst) & 1u)) bad = true;
+        };
+        if (tid == 0) {
+            for (; issued < kMxNst && issued < np; ++issued) {
+                const int sl = (int)((seq + issued) % kMxNst);
+                mbar_arrive_expect_tx(&bars[sl], kMxBoxBytes);
+                tma_load_3d(stage + sl * kMxStage, &map, x0 - kMxD, y0 - 1, kb - 1 + issued, &bars[sl]);
+            }
+        }
+        auto ld4 = [&](int j, float (&o)[4]) {
+            const float4 v = *reinterpret_cast<const float4*>(stage + ((seq + j) % kMxNst) * kMxStage + own);
+            o[0] = v.x;
+            o[1] = v.y;
+            o[2] = v.z;
+            o[3] = v.w;
+        };
+        float below[4], cur[4], above[4];
+        wait(0);
+        ld4(0, below);
+        wait(1);
+        ld4(1, cur);
+        float* dst = q + (int64_t)kb * sxy + (int64_t)(Y < ny ? Y : 0) * nx + (X < nx ? X : 0);
+        for (int k = kb; k < ke; ++k) {
+            const int j = k - kb + 1;   // plane k is plane j of the item
+            wait(j + 1);
+            ld4(j + 1, above);
+            const float* pc = stage + ((seq + j) % kMxNst) * kMxStage + own;
+            const float4 ymv = *reinterpret_cast<const float4*>(pc - kMxBW);
+            const float4 ypv = *reinterpret_cast<const float4*>(pc + kMxBW);
+            const float ym[4] = {ymv.x, ymv.y, ymv.z, ymv.w}, yp[4] = {ypv.x, ypv.y, ypv.z, ypv.w};
+            const float left = pc[-1], right = pc[4];
+            float qv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float xm = i == 0 ? left : cur[i - 1];
+                const float xp = i == 3 ? right : cur[i + 1];
+                const float sum = ((below[i] + ym[i]) + (xm + xp)) + (yp[i] + above[i]);
+                qv[i] = __fmaf_rn(6.0f, cur[i], -sum);
+            }
+            if (nvalid == 4) {
+                *reinterpret_cast<float4*>(dst) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+                pq.add4(cur[0], qv[0], cur[1], qv[1], cur[2], qv[2], cur[3], qv[3]);
+            }
+            dst += sxy;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                below[i] = cur[i];
+                cur[i] = above[i];
+            }
+            if (__syncthreads_or(bad)) {
+                aborted = true;
+                break;
+            }
+            // the slot of plane k-1 is free: every thread is past its last use
+            if (tid == 0 && issued < np) {
+                const int sl = (int)((seq + issued) % kMxNst);
+                mbar_arrive_expect_tx(&bars[sl], kMxBoxBytes);
+                tma_load_3d(stage + sl * kMxStage, &map, x0 - kMxD, y0 - 1, kb - 1 + issued, &bars[sl]);
+                ++issued;
+            }
+        }
+        if (!aborted) aborted = __syncthreads_or(bad) != 0;
+        if (aborted) break;
+        seq += (uint32_t)np;
+    }
+    if (aborted) {
+        if (tid == 0) {
+            // the last load issued into each slot, consumed or not, completes before the block ends
+            const long long t0 = clock64();
+            for (int j = issued > kMxNst ? issued - kMxNst : 0; j < issued; ++j) {
+                const uint32_t g = seq + (uint32_t)j;
+                if (!mbar_wait_until(&bars[g % kMxNst], (g / kMxNst) & 1u, t0, kWaitCycles)) {
+                    drained = false;
+                    break;
+                }
+            }
+            atomicMax(reinterpret_cast<int*>(&S->inner_done), drained ? 3 : 4);
+        }
+        return;
     }
     allow_dependents();
     const double blk = block_sum<kCgBlock>(pq.total(), sh);
@@ -258,10 +462,7 @@ __global__ void __launch_bounds__(kCgBlock)
         rv.w = __fmaf_rn(-alpha, qv.w, rv.w);
         reinterpret_cast<float4*>(d)[t] = dv;
         reinterpret_cast<float4*>(r)[t] = rv;
-        rr.add(rv.x, rv.x);
-        rr.add(rv.y, rv.y);
-        rr.add(rv.z, rv.z);
-        rr.add(rv.w, rv.w);
+        rr.add4(rv.x, rv.x, rv.y, rv.y, rv.z, rv.z, rv.w, rv.w);
     }
     if (t0 == 0)
         for (int64_t t = n4 << 2; t < n; ++t) {
@@ -391,7 +592,11 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
             for (int32_t t = 0; t < todo; ++t) {
                 // dependent launches: each kernel's launch overlaps the previous
                 // kernel's final reduction (it waits for that kernel on entry)
-                if (c->A.kind == HS_OP_STENCIL7)
+                if (m->tma)
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->pmap, m->A32, m->q,
+                                                 m->partials, m->S),
+                                "cg mixed: kernel launch");
+                else if (c->A.kind == HS_OP_STENCIL7)
                     HS_TRY_CUDA(launch_dependent(k_mx_spmv_dot<HS_OP_STENCIL7>, G, kCgBlock, c->stream, m->A32,
                                                  (const float*)m->p, m->q, m->partials, m->S),
                                 "cg mixed: kernel launch");
@@ -421,6 +626,11 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
             breakdown = true;
             break;
         }
+        if (m->S_host->inner_done == 3)
+            return fail(HS_ETIMEOUT, "cg_run: a bounded wait in the TMA-staged FP32 SpMV ran out");
+        if (m->S_host->inner_done == 4)
+            return fail(HS_ECUDA, "cg_run: a bounded wait in the TMA-staged FP32 SpMV ran out and its loads "
+                                  "in flight did not complete in time; treat the CUDA context as suspect");
         k_mx_correct<<<G, kCgBlock, 0, c->stream>>>(n, x, m->d);   // x += d (FP64)
         HS_CHECK_LAUNCH("cg mixed: correction kernel");
         ++outer;
@@ -518,6 +728,15 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
     m->A32.rowptr = c->A.rowptr;
     m->A32.col = c->A.col;
     m->A32.val = m->val32;
+    // the FP32 matrix-free SpMV stages p by TMA when rows are a 16-byte multiple
+    m->tma = false;
+    if (m->A32.kind == HS_OP_STENCIL7 && m->A32.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(m->p) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(m->q) & 15) == 0) {
+        const int e2 = encode_field_map(&m->pmap, m->p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float),
+                                        (uint64_t)m->A32.nx, (uint64_t)m->A32.ny, (uint64_t)m->A32.nz, kMxBW,
+                                        kMxTY + 2);
+        m->tma = e2 == 0;
+    }
     *out = c;
     return HS_OK;
 }

@@ -41,7 +41,8 @@ def true_relres(x, b, shape):
 
 @pytest.mark.parametrize("kind", ["stencil", "csr"])
 @pytest.mark.parametrize("shape,rtol", [((24, 24, 24), 1e-10), ((9, 17, 33), 1e-12),
-                                        ((40, 31, 22), 1e-8), ((2, 2, 2), 1e-10)])
+                                        ((40, 31, 22), 1e-8), ((2, 2, 2), 1e-10),
+                                        ((37, 21, 132), 1e-10), ((5, 3, 4), 1e-10)])
 def test_mixed_meets_rtol_in_fp64(pkg, kind, shape, rtol):
     nz, ny, nx = shape
     b = cg_rhs(nx * ny * nz, seed=31)
