@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kCgBlock)
     }
 }
 
-// q = A p fused with p.q; the last block forms alpha = rho / p.q.  MODE is
-// the operator's SpmvMode.
+// q = A p fused with p.q, one row per thread (MODE SP_ROWS or SP_CSR); the
+// last block forms alpha = rho / p.q.
 template <int MODE>
 __global__ void __launch_bounds__(kCgBlock)
     k_cg_spmv_dot(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
@@ -90,20 +90,41 @@ __global__ void __launch_bounds__(kCgBlock)
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     double pq = 0.0;
-    if (MODE == SP_STAGED) {
-        pq = spmv_stencil_blocks(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
-    } else {
-        for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
-             row += (int64_t)gridDim.x * kCgBlock) {
-            const double qv = MODE == SP_CSR ? apply_csr_row(A, p, row) : apply_stencil_row(A, p, row);
-            q[row] = qv;
-            pq = __fma_rn(__ldg(p + row), qv, pq);
-        }
+    for (int64_t row = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; row < A.n;
+         row += (int64_t)gridDim.x * kCgBlock) {
+        const double qv = MODE == SP_CSR ? apply_csr_row(A, p, row) : apply_stencil_row(A, p, row);
+        q[row] = qv;
+        pq = __fma_rn(__ldg(p + row), qv, pq);
     }
     allow_dependents();
     const double blk = block_sum<kCgBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double tot = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->pq = tot;
+        if (!(tot > 0.0)) {
+            S->done = 2;   // breakdown: A is not positive definite on p
+        } else {
+            S->alpha = S->rho / tot;
+        }
+    }
+}
+
+// The matrix-free SpMV staged by loads (SP_STAGED), fused with p.q: blocks of
+// kSpBlock threads, as many as the other kernels of the solve use.
+__global__ void __launch_bounds__(kSpBlock, kSpMinBlocks)
+    k_cg_spmv_staged(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
+                     CgScalars* S)
+{
+    grid_dependency_wait();
+    if (*(volatile int32_t*)&S->done) return;
+    __shared__ double sh[kSpBlock / 32];
+    const double pq = spmv_stencil_blocks(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
+    allow_dependents();
+    const double blk = block_sum<kSpBlock>(pq, sh);
+    if (!arrive_last(blk, partials, &S->ticket)) return;
+    const double tot = sum_partials_nt<kSpBlock>(partials, gridDim.x, sh);
     if (threadIdx.x == 0) {
         S->ticket = 0;
         S->pq = tot;
@@ -323,10 +344,13 @@ int cg_spmv(const hs_op* A, const void* p, void* q, int kernel, double* pq, void
         if (tma) {
             rc = spmv_tma_launch(pmap, D, (double*)q, partials, S, grid, s);
         } else {
-            auto kern = mode == SP_STAGED ? k_cg_spmv_dot<SP_STAGED>
-                        : mode == SP_CSR  ? k_cg_spmv_dot<SP_CSR>
-                                          : k_cg_spmv_dot<SP_ROWS>;
-            e = launch_dependent(kern, grid, kCgBlock, s, D, (const double*)p, (double*)q, partials, S);
+            if (mode == SP_STAGED) {
+                e = launch_dependent(k_cg_spmv_staged, grid, kSpBlock, s, D, (const double*)p, (double*)q,
+                                     partials, S);
+            } else {
+                auto kern = mode == SP_CSR ? k_cg_spmv_dot<SP_CSR> : k_cg_spmv_dot<SP_ROWS>;
+                e = launch_dependent(kern, grid, kCgBlock, s, D, (const double*)p, (double*)q, partials, S);
+            }
             rc = e == cudaSuccess ? HS_OK : cuda_fail(e, "cg_spmv: kernel launch");
             e = cudaSuccess;
         }
@@ -489,7 +513,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
                     rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, c->grid, c->stream);
                     if (rc != HS_OK) return rc;
                 } else {
-                    HS_TRY_CUDA(launch_dependent(k_cg_spmv_dot<SP_STAGED>, c->grid, kCgBlock, c->stream, c->A,
+                    HS_TRY_CUDA(launch_dependent(k_cg_spmv_staged, c->grid, kSpBlock, c->stream, c->A,
                                            (const double*)c->p, c->q, c->partials, c->S), "cg: kernel launch");
                 }
                 break;

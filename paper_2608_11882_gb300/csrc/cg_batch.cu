@@ -124,20 +124,21 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
     }
 }
 
-// One kernel per SpmvMode, so each has its own register budget; blocks of
-// the other modes' systems return at once.
-template <int MODE>
-__global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, int nsys)
+// One kernel per SpmvMode, so each has its own register budget (and, for the
+// staged mode, block size); blocks of the other modes' systems return at once.
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_cgb_spmv_dot(const SysDev* sys, int nsys)
 {
     grid_dependency_wait();
     int local;
     const SysDev& s = sys[sys_of_block(sys, nsys, &local)];
     if (s.mode != MODE || *(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
-    __shared__ double sh[kCgBlock / 32];
+    __shared__ double sh[NT / 32];
     double pq = 0.0;
-    // as k_cg_spmv_dot: the same rows per thread and per-row arithmetic, so the same results
-    const int64_t row0 = (int64_t)local * kCgBlock + threadIdx.x;
-    const int64_t stride = (int64_t)s.nblocks * kCgBlock;
+    // as k_cg_spmv_dot / k_cg_spmv_staged: the same points per thread and the
+    // same arithmetic, so the same results
+    const int64_t row0 = (int64_t)local * NT + threadIdx.x;
+    const int64_t stride = (int64_t)s.nblocks * NT;
     if (MODE == SP_STAGED) {
         pq = spmv_stencil_blocks(s.A, s.p, s.q, cg_pemax(s.S), local, s.nblocks);
     } else for (int64_t row = row0; row < s.A.n; row += stride) {
@@ -146,9 +147,9 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_spmv_dot(const SysDev* sys, in
         pq = __fma_rn(__ldg(s.p + row), qv, pq);
     }
     allow_dependents();
-    const double blk = block_sum<kCgBlock>(pq, sh);
+    const double blk = block_sum<NT>(pq, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
-    const double tot = sum_partials_n(s.partials, s.nblocks, sh);
+    const double tot = sum_partials_nt<NT>(s.partials, s.nblocks, sh);
     if (threadIdx.x == 0) {
         CgScalars* S = s.S;
         S->ticket = 0;
@@ -371,9 +372,14 @@ int cg_batch_run(hs_cg_batch_t b, const void* const* bs, void* const* xs, double
         if (all || enqueued >= max_iter) break;
         const int32_t todo = (max_iter - enqueued < chunk) ? max_iter - enqueued : chunk;
         for (int32_t t = 0; t < todo; ++t) {
-            if (b->has_mode[SP_STAGED]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_STAGED>, "cg batch: spmv+dot kernel");
-            if (b->has_mode[SP_ROWS]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_ROWS>, "cg batch: spmv+dot kernel");
-            if (b->has_mode[SP_CSR]) CGB_LAUNCH_DEP(k_cgb_spmv_dot<SP_CSR>, "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_STAGED]) {
+                HS_TRY_CUDA(launch_dependent(k_cgb_spmv_dot<SP_STAGED, kSpBlock, kSpMinBlocks>, G, kSpBlock, b->stream, b->d_sys,
+                                             n),
+                            "cg batch: kernel launch");
+                HS_CHECK_LAUNCH("cg batch: spmv+dot kernel");
+            }
+            if (b->has_mode[SP_ROWS]) CGB_LAUNCH_DEP((k_cgb_spmv_dot<SP_ROWS, kCgBlock, 1>), "cg batch: spmv+dot kernel");
+            if (b->has_mode[SP_CSR]) CGB_LAUNCH_DEP((k_cgb_spmv_dot<SP_CSR, kCgBlock, 1>), "cg batch: spmv+dot kernel");
             CGB_LAUNCH_DEP(k_cgb_update, "cg batch: update kernel");
             CGB_LAUNCH_DEP(k_cgb_pupdate, "cg batch: p update kernel");
         }

@@ -118,21 +118,37 @@ __device__ __forceinline__ int cg_pemax(const CgScalars* S)
 __device__ __forceinline__ bool cg_xs_ok(int emax) { return emax >= kXsEmaxLo && emax <= kXsEmaxHi; }
 
 // ---- matrix-free SpMV staged through shared memory ---------------------------------
-// A block of kCgBlock = 256 threads (8 warps) owns a tile of 64 x 8 points of
+// A block of kSpBlock = 128 threads (4 warps) owns a tile of 64 x 8 points of
 // the grid and a chunk of z-planes, and marches up the chunk: every thread two
-// consecutive x points of one row.  Each z-plane of the tile, with a one-point
-// halo, is loaded once with coalesced loads (a plane ahead of its use),
-// converted once to fixed point (exact-sum form) and written to one of two
-// shared plane buffers; a thread keeps its own values at k-1, k and k+1 in
-// registers, reads the in-plane neighbours from the buffer of plane k, and
-// one block barrier per plane orders the buffers.  Points outside the grid
-// are staged as zeros (the Dirichlet boundary).  Work items (tile, chunk) are
-// taken by the system's `nblocks` blocks in a fixed order, so a block's partial
-// p.q -- and the whole reduction -- repeats bit for bit wherever the same
-// operator runs with the same block count (a batch uses its systems' own).
+// consecutive x points in each of two adjacent rows, so its per-plane work
+// (barrier, addresses, loop) is shared by four points and the y neighbours
+// between its own rows come from its registers.  Each z-plane of the tile,
+// with a one-point halo, is loaded once with coalesced loads (two planes
+// ahead of its use), converted once to fixed point (exact-sum form) and
+// written to one of two shared plane buffers; a thread keeps its own values
+// at k-1, k and k+1 in registers, reads the other neighbours from the buffer
+// of plane k, and one block barrier per plane orders the buffers.  Points
+// outside the grid are staged as zeros (the Dirichlet boundary).  Work items
+// (tile, chunk) are taken by the system's `nblocks` blocks in a fixed order,
+// and each thread adds its p.q products in a fixed order (row by row, x
+// ascending), so a block's partial p.q -- and the whole reduction -- repeats
+// bit for bit wherever the same operator runs with the same block count (a
+// batch uses its systems' own).
 constexpr int kSpTW = 64, kSpTY = 8, kSpBW = 68, kSpD = 2;   // tile width/rows, buffer row, x offset
 constexpr int kSpPlane = (kSpTY + 2) * kSpBW;                // buffer elements per plane
-static_assert(kSpTY * 32 == kCgBlock, "one warp per tile row");
+constexpr int kSpBlock = 128, kSpRT = 2;                     // threads of a staged block, rows per thread
+constexpr int kSpMinBlocks = 5;   // load-staged blocks per SM (102 registers): measured fastest
+static_assert(kSpTY == (kSpBlock / 32) * kSpRT, "four warps of two rows each cover the tile");
+
+// Sum of partials[0..m) in a fixed order by a whole block of NT threads;
+// valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double sum_partials_nt(const double* partials, int m, double* sh)
+{
+    double v = 0.0;
+    for (int t = threadIdx.x; t < m; t += NT) v += __ldcg(partials + t);
+    return block_sum<NT>(v, sh);
+}
 
 struct SpmvPlan {
     int64_t tiles, items;
@@ -157,142 +173,182 @@ __host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A, int nblocks)
     return P;
 }
 
+// q for one thread's 2 x 2 points of a plane from their values B (below), C
+// (at), A (above), the row below the first row and above the last, and the x
+// neighbours beyond the pairs: the exact-sum form (fixed-point values; point
+// 0 of a row converted back on the FP64 pipe, point 1 with integers, the same
+// double either way) or the FP64 pipe on raw bits.
+template <bool CONV>
+__device__ __forceinline__ void spmv_points(const long long (&B)[2][2], const long long (&C)[2][2],
+                                            const long long (&A)[2][2], const long long (&ym)[2],
+                                            const long long (&yp)[2], const long long (&left)[2],
+                                            const long long (&right)[2], int emax, double (&qv)[2][2])
+{
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const long long xm = i == 0 ? left[j] : C[j][0];
+            const long long xp = i == 1 ? right[j] : C[j][1];
+            const long long yl = j == 0 ? ym[i] : C[0][i];
+            const long long yh = j == 1 ? yp[i] : C[1][i];
+            if constexpr (CONV) {
+                const long long L = 6 * C[j][i] - (((B[j][i] + yl) + (xm + xp)) + (yh + A[j][i]));
+                qv[j][i] = i == 0 ? xs_unfix_dp(L, emax) : xs_unfix(L, emax);
+            } else {
+                auto d = [](long long b) { return __longlong_as_double(b); };
+                const double sv = ((d(B[j][i]) + d(yl)) + (d(xm) + d(xp))) + (d(yh) + d(A[j][i]));
+                qv[j][i] = __fma_rn(6.0, d(C[j][i]), -sv);
+            }
+        }
+}
+
 // One work item: q = A p on the tile's planes [kb, ke), returning this
 // thread's share of p.q.  CONV: the exact-sum form (emax = p's largest
-// exponent field; odd warps convert the row sums on the FP64 pipe, even warps
-// with integers); otherwise the FP64-pipe row of apply_stencil_row.
+// exponent field); otherwise FP64 arithmetic on raw values.
 template <bool CONV>
 __device__ __forceinline__ double spmv_item(const OpDev& A, const double* __restrict__ p,
                                             double* __restrict__ q, int emax, const SpmvPlan& P,
                                             int64_t tile, int kb, int ke, long long* buf)
 {
-    constexpr int V = 2, BW = kSpBW;
+    constexpr int V = 2, RT = kSpRT, BW = kSpBW;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int64_t sxy = (int64_t)nx * ny;
     const int x0 = (int)(tile % P.tiles_x) * kSpTW, y0 = (int)(tile / P.tiles_x) * kSpTY;
-    const int X = x0 + V * tx, Y = y0 + ty;
-    const int own = (ty + 1) * BW + kSpD + V * tx;
-    const bool ok0 = Y < ny && X < nx, ok1 = Y < ny && X + 1 < nx;
-    // a 16-byte pair: X is even, so the pair is aligned when nx is even and
-    // both vectors start 16-byte aligned
-    const bool vec = ok1 && (nx & 1) == 0 &&
-                     (((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0);
-    const int64_t rowoff = (int64_t)Y * nx + X;
-    // one halo value per thread for the first 2*64 + 2*8 threads
-    int hidx = -1, hx = -1, hy = -1;
-    if (tid < 2 * kSpTW) {
-        const int r = tid < kSpTW ? 0 : kSpTY + 1;
-        const int c = tid % kSpTW;
-        hidx = r * BW + kSpD + c;
-        hx = x0 + c;
-        hy = r == 0 ? y0 - 1 : y0 + kSpTY;
-    } else if (tid < 2 * kSpTW + 2 * kSpTY) {
-        const int t = tid - 2 * kSpTW;
-        const int r = 1 + t % kSpTY;
-        const bool right = t >= kSpTY;
-        hidx = r * BW + (right ? kSpD + kSpTW : kSpD - 1);
-        hx = right ? x0 + kSpTW : x0 - 1;
-        hy = y0 + r - 1;
+    const int X = x0 + V * tx, Y0 = y0 + RT * ty;
+    const int own = (RT * ty + 1) * BW + kSpD + V * tx;   // row j: + j BW
+    bool ok[RT][V], vec[RT];
+    int64_t rowoff[RT];
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+        ok[j][0] = Y0 + j < ny && X < nx;
+        ok[j][1] = Y0 + j < ny && X + 1 < nx;
+        // a 16-byte pair: X is even, so the pair is aligned when nx is even and
+        // both vectors start 16-byte aligned
+        vec[j] = ok[j][1] && (nx & 1) == 0 &&
+                 (((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0);
+        rowoff[j] = (int64_t)(Y0 + j) * nx + X;
     }
-    const bool hok = hidx >= 0 && hx >= 0 && hx < nx && hy >= 0 && hy < ny;
-    const int64_t hoff = (int64_t)hy * nx + hx;
+    // halo: every thread one value of halo row 0 (threads 0..63) or 9 (64..127),
+    // threads 0..15 also one value of the halo columns
+    const int hc = tid % kSpTW;
+    const int hidx = (tid < kSpTW ? 0 : kSpTY + 1) * BW + kSpD + hc;
+    const int hy = tid < kSpTW ? y0 - 1 : y0 + kSpTY;
+    const bool hok = x0 + hc < nx && hy >= 0 && hy < ny;
+    const int64_t hoff = (int64_t)hy * nx + x0 + hc;
+    int hidx2 = -1;
+    bool hok2 = false;
+    int64_t hoff2 = 0;
+    if (tid < 2 * kSpTY) {
+        const int rr = 1 + tid % kSpTY;
+        const bool rgt = tid >= kSpTY;
+        const int hx2 = rgt ? x0 + kSpTW : x0 - 1, hy2 = y0 + rr - 1;
+        hidx2 = rr * BW + (rgt ? kSpD + kSpTW : kSpD - 1);
+        hok2 = hx2 >= 0 && hx2 < nx && hy2 < ny;
+        hoff2 = (int64_t)hy2 * nx + hx2;
+    }
     const long long* pb = reinterpret_cast<const long long*>(p);
-    auto ld_own = [&](int k, long long (&o)[V]) {
-        o[0] = 0;
-        o[1] = 0;
-        if (k < 0 || k >= nz) return;
-        const long long* src = pb + (int64_t)k * sxy + rowoff;
-        if (vec) {
-            const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(src));
-            o[0] = v.x;
-            o[1] = v.y;
-        } else {
-            if (ok0) o[0] = __ldg(src);
-            if (ok1) o[1] = __ldg(src + 1);
+    auto ld_own = [&](int k, long long (&o)[RT][V]) {
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            o[j][0] = 0;
+            o[j][1] = 0;
+            if (k < 0 || k >= nz) continue;
+            const long long* src = pb + (int64_t)k * sxy + rowoff[j];
+            if (vec[j]) {
+                const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(src));
+                o[j][0] = v.x;
+                o[j][1] = v.y;
+            } else {
+                if (ok[j][0]) o[j][0] = __ldg(src);
+                if (ok[j][1]) o[j][1] = __ldg(src + 1);
+            }
         }
     };
-    auto ld_halo = [&](int k) -> long long {
-        return (hok && k >= 0 && k < nz) ? __ldg(pb + (int64_t)k * sxy + hoff) : 0;
+    auto ld_halo = [&](int k, bool okh, int64_t off) -> long long {
+        return (okh && k >= 0 && k < nz) ? __ldg(pb + (int64_t)k * sxy + off) : 0;
     };
     auto fix = [&](long long b) -> long long { return CONV ? xs_fix(b, emax) : b; };
-    const bool dp = (ty & 1) != 0;
+    auto put = [&](long long* bp, const long long (&v)[RT][V], long long h, long long h2) {
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            bp[own + j * BW] = v[j][0];
+            bp[own + j * BW + 1] = v[j][1];
+        }
+        bp[hidx] = fix(h);
+        if (hidx2 >= 0) bp[hidx2] = fix(h2);
+    };
 
-    long long below[V], cur[V], above[V], nown[V], t[V];
-    double craw[V], araw[V];
+    long long below[RT][V], cur[RT][V], above[RT][V], nown[RT][V], t[RT][V];
+    double craw[RT][V], araw[RT][V];
     ld_own(kb - 1, t);
-    below[0] = fix(t[0]);
-    below[1] = fix(t[1]);
+#pragma unroll
+    for (int j = 0; j < RT; ++j)
+#pragma unroll
+        for (int i = 0; i < V; ++i) below[j][i] = fix(t[j][i]);
     ld_own(kb, t);
-    craw[0] = __longlong_as_double(t[0]);
-    craw[1] = __longlong_as_double(t[1]);
-    cur[0] = fix(t[0]);
-    cur[1] = fix(t[1]);
-    {
-        long long* b0 = buf + (kb & 1) * kSpPlane;
-        b0[own] = cur[0];
-        b0[own + 1] = cur[1];
-        if (hidx >= 0) b0[hidx] = fix(ld_halo(kb));
-    }
+#pragma unroll
+    for (int j = 0; j < RT; ++j)
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            craw[j][i] = __longlong_as_double(t[j][i]);
+            cur[j][i] = fix(t[j][i]);
+        }
+    put(buf + (kb & 1) * kSpPlane, cur, ld_halo(kb, hok, hoff), ld_halo(kb, hok2, hoff2));
     ld_own(kb + 1, t);
-    araw[0] = __longlong_as_double(t[0]);
-    araw[1] = __longlong_as_double(t[1]);
-    above[0] = fix(t[0]);
-    above[1] = fix(t[1]);
-    long long h1 = ld_halo(kb + 1), nh = 0;
-    nown[0] = 0;
-    nown[1] = 0;
+#pragma unroll
+    for (int j = 0; j < RT; ++j)
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            araw[j][i] = __longlong_as_double(t[j][i]);
+            above[j][i] = fix(t[j][i]);
+        }
+    long long h1 = ld_halo(kb + 1, hok, hoff), h1b = ld_halo(kb + 1, hok2, hoff2), nh = 0, nhb = 0;
+    ld_own(kb + 2 <= ke ? kb + 2 : nz, nown);   // plane nz reads as zeros
     if (kb + 2 <= ke) {
-        ld_own(kb + 2, nown);
-        nh = ld_halo(kb + 2);
+        nh = ld_halo(kb + 2, hok, hoff);
+        nhb = ld_halo(kb + 2, hok2, hoff2);
     }
     __syncthreads();
 
     double pq = 0.0;
     for (int k = kb; k < ke; ++k) {
-        long long* bn = buf + ((k + 1) & 1) * kSpPlane;   // plane k+1: published for the next iteration
-        bn[own] = above[0];
-        bn[own + 1] = above[1];
-        if (hidx >= 0) bn[hidx] = fix(h1);
+        put(buf + ((k + 1) & 1) * kSpPlane, above, h1, h1b);   // plane k+1: read in the next iteration
         const long long* pc = buf + (k & 1) * kSpPlane + own;
-        const long long ym0 = pc[-BW], ym1 = pc[1 - BW], yp0 = pc[BW], yp1 = pc[1 + BW];
-        const long long left = pc[-1], right = pc[V];
-        double qv[V];
-        if constexpr (CONV) {
-            const long long L0 = 6 * cur[0] - (((below[0] + ym0) + (left + cur[1])) + (yp0 + above[0]));
-            const long long L1 = 6 * cur[1] - (((below[1] + ym1) + (cur[0] + right)) + (yp1 + above[1]));
-            qv[0] = dp ? xs_unfix_dp(L0, emax) : xs_unfix(L0, emax);
-            qv[1] = dp ? xs_unfix_dp(L1, emax) : xs_unfix(L1, emax);
-        } else {
-            auto d = [](long long b) { return __longlong_as_double(b); };
-            const double s0 = ((d(below[0]) + d(ym0)) + (d(left) + d(cur[1]))) + (d(yp0) + d(above[0]));
-            const double s1 = ((d(below[1]) + d(ym1)) + (d(cur[0]) + d(right))) + (d(yp1) + d(above[1]));
-            qv[0] = __fma_rn(6.0, d(cur[0]), -s0);
-            qv[1] = __fma_rn(6.0, d(cur[1]), -s1);
+        const long long ym[V] = {pc[-BW], pc[1 - BW]}, yp[V] = {pc[RT * BW], pc[RT * BW + 1]};
+        const long long left[RT] = {pc[-1], pc[BW - 1]}, right[RT] = {pc[V], pc[BW + V]};
+        double qv[RT][V];
+        spmv_points<CONV>(below, cur, above, ym, yp, left, right, emax, qv);
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            double* dst = q + (int64_t)k * sxy + rowoff[j];
+            if (vec[j]) {
+                *reinterpret_cast<double2*>(dst) = make_double2(qv[j][0], qv[j][1]);
+            } else {
+                if (ok[j][0]) dst[0] = qv[j][0];
+                if (ok[j][1]) dst[1] = qv[j][1];
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (ok[j][i]) pq = __fma_rn(craw[j][i], qv[j][i], pq);
         }
-        double* dst = q + (int64_t)k * sxy + rowoff;
-        if (vec) {
-            *reinterpret_cast<double2*>(dst) = make_double2(qv[0], qv[1]);
-        } else {
-            if (ok0) dst[0] = qv[0];
-            if (ok1) dst[1] = qv[1];
-        }
-        if (ok0) pq = __fma_rn(craw[0], qv[0], pq);
-        if (ok1) pq = __fma_rn(craw[1], qv[1], pq);
-        below[0] = cur[0];
-        below[1] = cur[1];
-        cur[0] = above[0];
-        cur[1] = above[1];
-        craw[0] = araw[0];
-        craw[1] = araw[1];
-        araw[0] = __longlong_as_double(nown[0]);
-        araw[1] = __longlong_as_double(nown[1]);
-        above[0] = fix(nown[0]);
-        above[1] = fix(nown[1]);
+#pragma unroll
+        for (int j = 0; j < RT; ++j)
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                below[j][i] = cur[j][i];
+                cur[j][i] = above[j][i];
+                craw[j][i] = araw[j][i];
+                araw[j][i] = __longlong_as_double(nown[j][i]);
+                above[j][i] = fix(nown[j][i]);
+            }
         h1 = nh;
+        h1b = nhb;
         if (k + 3 <= ke) {
             ld_own(k + 3, nown);
-            nh = ld_halo(k + 3);
+            nh = ld_halo(k + 3, hok, hoff);
+            nhb = ld_halo(k + 3, hok2, hoff2);
         }
         __syncthreads();
     }

@@ -3,22 +3,23 @@
 // q = 6p - sum of the six face neighbours, Dirichlet zeros outside the box).
 //
 // The same work as the staged kernel of cg_common.cuh, in the same order and
-// with the same arithmetic: a block of 256 threads owns a 64 x 8 tile of one
-// z-chunk at a time, every thread two consecutive x points of one row, work
-// items (tile, chunk) taken in the order spmv_plan gives.  q and every
+// with the same arithmetic: a block of 128 threads owns a 64 x 8 tile of one
+// z-chunk at a time, every thread two consecutive x points in each of two
+// adjacent rows, work items (tile, chunk) taken in the order spmv_plan gives.  q and every
 // thread's share of p.q therefore come out bit for bit as there, so a single
 // solve (this kernel) and a batched solve (the staged kernel) still agree.
 //
 // What differs is how p arrives: each plane of the tile with its one-point
 // halo is one 3-D tiled TMA box, (8 + 2) rows of 68 doubles starting 16 bytes
-// left of the tile, loaded into a ring of kSpNst stages up to kSpNst - 2
-// planes ahead of use.  The tensor map spans the unpadded nx x ny x nz vector,
+// left of the tile, loaded into a ring of kSpNst = 4 stages up to 2 planes
+// ahead of use (six blocks of 128 threads per SM, 85 registers: measured
+// ahead of eight blocks at 64 registers).  The tensor map spans the unpadded nx x ny x nz vector,
 // so boxes that reach past the box of the grid (the planes -1 and nz, the rows
 // -1 and ny, the columns -1 and nx) read zeros: the Dirichlet boundary with no
 // bounds checks.  The box starts at x0 - 2 with x0 a multiple of 64, so its x
 // coordinate times 8 bytes is a multiple of 16 as TMA requires; the map needs
 // nx even (16-byte row stride) and p 16-byte aligned, which the host checks.
-// Every thread converts its own two values of each new plane to fixed point in
+// Every thread converts its own four values of each new plane to fixed point in
 // place (and warps 0-2 the halo), so each staged value is converted once.
 //
 // Each mbarrier wait is bounded (about a second); one that runs out marks the
@@ -33,23 +34,11 @@
 
 namespace hcg {
 
-constexpr int kSpNst = 6;
+constexpr int kSpNst = 4;
 constexpr uint32_t kSpBoxBytes = (uint32_t)kSpPlane * sizeof(double);     // 10 x 68 doubles
 constexpr int kSpStage = (int)((kSpBoxBytes + 127) / 128 * 128 / sizeof(double));
 static_assert(kSpBW * sizeof(double) % 16 == 0, "TMA box rows are a 16-byte multiple");
 static_assert(kSpD * sizeof(double) == 16, "the box starts 16 bytes left of the tile");
-
-__device__ __forceinline__ void ld_pair(const long long* p, long long (&o)[2])
-{
-    const longlong2 v = *reinterpret_cast<const longlong2*>(p);
-    o[0] = v.x;
-    o[1] = v.y;
-}
-
-__device__ __forceinline__ void st_pair(long long* p, const long long (&o)[2])
-{
-    *reinterpret_cast<longlong2*>(p) = make_longlong2(o[0], o[1]);
-}
 
 template <bool CONV>
 __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const OpDev& A,
@@ -58,49 +47,48 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
                                                 uint64_t* bars, uint32_t& seq, bool& aborted,
                                                 bool& drained)
 {
-    constexpr int V = 2, BW = kSpBW, NST = kSpNst;
+    constexpr int V = 2, RT = kSpRT, BW = kSpBW, NST = kSpNst;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int nx = A.nx, ny = A.ny;
     const int64_t sxy = (int64_t)nx * ny;
     const int x0 = (int)(tile % P.tiles_x) * kSpTW, y0 = (int)(tile / P.tiles_x) * kSpTY;
-    const int X = x0 + V * tx, Y = y0 + ty;
-    const int own = (ty + 1) * BW + kSpD + V * tx;
-    // nx is even and X is even: both points of the pair are inside or both outside
-    const bool ok = Y < ny && X < nx;
-    // the values this thread converts besides its own pair: a pair of halo row
-    // 0 (warp 0) or 9 (warp 1), or one halo-column value (warp 2)
+    const int X = x0 + V * tx, Y0 = y0 + RT * ty;
+    const int own = (RT * ty + 1) * BW + kSpD + V * tx;   // row j: + j BW
+    // nx is even and X is even: both points of a pair are inside or both outside
+    bool ok[RT];
+#pragma unroll
+    for (int j = 0; j < RT; ++j) ok[j] = Y0 + j < ny && X < nx;
+    // the values this thread converts besides its own: a pair of halo row 0
+    // (warp 0) or 9 (warp 1), or one halo-column value (warp 2)
     int extra = -1;
     if (ty == 0) extra = kSpD + V * tx;
     else if (ty == 1) extra = (kSpTY + 1) * BW + kSpD + V * tx;
     else if (ty == 2 && tx < 2 * kSpTY)
         extra = tx < kSpTY ? (tx + 1) * BW + kSpD - 1 : (tx - kSpTY + 1) * BW + kSpD + kSpTW;
-    const bool dp = (ty & 1) != 0;
     const int np = ke - kb + 2;   // planes kb-1 .. ke
-    // plane j of this item sits in ring slot (seq + j) % NST, phase ((seq + j) / NST) & 1;
-    // the loop steps slot and phase instead of dividing
     const int s0 = (int)(seq % NST);
     const uint32_t ph0 = (seq / NST) & 1u;
     bool bad = false;   // a wait of this thread ran out
     auto wait = [&](int sl, uint32_t ph) {
         if (!mbar_wait_bounded(&bars[sl], ph)) bad = true;
     };
-    auto convert = [&](long long* pl, long long (&fx)[V], double (&raw)[V]) {
-        long long b[V];
-        ld_pair(pl + own, b);
-        raw[0] = __longlong_as_double(b[0]);
-        raw[1] = __longlong_as_double(b[1]);
-        fx[0] = CONV ? xs_fix(b[0], emax) : b[0];
-        fx[1] = CONV ? xs_fix(b[1], emax) : b[1];
+    auto fix = [&](long long b) -> long long { return CONV ? xs_fix(b, emax) : b; };
+    auto convert = [&](long long* pl, long long (&fx)[RT][V], double (&raw)[RT][V]) {
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            const longlong2 b = *reinterpret_cast<const longlong2*>(pl + own + j * BW);
+            raw[j][0] = __longlong_as_double(b.x);
+            raw[j][1] = __longlong_as_double(b.y);
+            fx[j][0] = fix(b.x);
+            fx[j][1] = fix(b.y);
+            if constexpr (CONV) *reinterpret_cast<longlong2*>(pl + own + j * BW) = make_longlong2(fx[j][0], fx[j][1]);
+        }
         if constexpr (CONV) {
-            st_pair(pl + own, fx);
             if (ty < 2) {
-                long long h[V];
-                ld_pair(pl + extra, h);
-                h[0] = xs_fix(h[0], emax);
-                h[1] = xs_fix(h[1], emax);
-                st_pair(pl + extra, h);
+                const longlong2 h = *reinterpret_cast<const longlong2*>(pl + extra);
+                *reinterpret_cast<longlong2*>(pl + extra) = make_longlong2(fix(h.x), fix(h.y));
             } else if (extra >= 0) {
-                pl[extra] = xs_fix(pl[extra], emax);
+                pl[extra] = fix(pl[extra]);
             }
         }
     };
@@ -115,68 +103,58 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
     }
     // the planes below, at and above k (fixed-point values, raw bits when
     // !CONV) and the raw values at and above k
-    long long X0[V], X1[V], X2[V];
-    double R1[V], R2[V];
+    long long B[RT][V], C[RT][V], Ab[RT][V];
+    double RC[RT][V], RA[RT][V];
     int s_cur = s0;
     uint32_t ph_cur = ph0;
     wait(s_cur, ph_cur);
-    {
-        long long b[V];
-        ld_pair(stage + s_cur * kSpStage + own, b);
-        X0[0] = CONV ? xs_fix(b[0], emax) : b[0];
-        X0[1] = CONV ? xs_fix(b[1], emax) : b[1];
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+        const longlong2 b = *reinterpret_cast<const longlong2*>(stage + s_cur * kSpStage + own + j * BW);
+        B[j][0] = fix(b.x);
+        B[j][1] = fix(b.y);
     }
     if (++s_cur == NST) {
         s_cur = 0;
         ph_cur ^= 1u;
     }
     wait(s_cur, ph_cur);
-    convert(stage + s_cur * kSpStage, X1, R1);
+    convert(stage + s_cur * kSpStage, C, RC);
     if constexpr (CONV) fence_proxy_async_smem();
     // the barriers reduce the threads' wait results, so all agree on an abort
     aborted = __syncthreads_or(bad) != 0;
 
     double pq = 0.0;
-    double* dst = q + (int64_t)kb * sxy + (int64_t)(ok ? Y : 0) * nx + (ok ? X : 0);
-    // one plane: below B, at C (raw RC, in slot s_cur), above A (raw RA) filled
-    // here from the next slot; false once the block gives up
-    auto step = [&](const long long (&B)[V], const long long (&C)[V], long long (&A)[V],
-                    const double (&RC)[V], double (&RA)[V]) -> bool {
+    for (int k = kb; !aborted && k < ke; ++k) {
         const int s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
         const uint32_t ph_nxt = s_nxt == 0 ? ph_cur ^ 1u : ph_cur;
         wait(s_nxt, ph_nxt);
-        convert(stage + s_nxt * kSpStage, A, RA);
+        convert(stage + s_nxt * kSpStage, Ab, RA);
         const long long* pc = stage + s_cur * kSpStage + own;
-        long long ym[V], yp[V];
-        ld_pair(pc - BW, ym);
-        ld_pair(pc + BW, yp);
-        const long long left = pc[-1], right = pc[V];
-        double qv[V];
-        if constexpr (CONV) {
-            const long long L0 = 6 * C[0] - (((B[0] + ym[0]) + (left + C[1])) + (yp[0] + A[0]));
-            const long long L1 = 6 * C[1] - (((B[1] + ym[1]) + (C[0] + right)) + (yp[1] + A[1]));
-            qv[0] = dp ? xs_unfix_dp(L0, emax) : xs_unfix(L0, emax);
-            qv[1] = dp ? xs_unfix_dp(L1, emax) : xs_unfix(L1, emax);
-        } else {
-            auto d = [](long long b) { return __longlong_as_double(b); };
-            const double s0v = ((d(B[0]) + d(ym[0])) + (d(left) + d(C[1]))) + (d(yp[0]) + d(A[0]));
-            const double s1v = ((d(B[1]) + d(ym[1])) + (d(C[0]) + d(right))) + (d(yp[1]) + d(A[1]));
-            qv[0] = __fma_rn(6.0, d(C[0]), -s0v);
-            qv[1] = __fma_rn(6.0, d(C[1]), -s1v);
-        }
-        if (ok) {
-            *reinterpret_cast<double2*>(dst) = make_double2(qv[0], qv[1]);
-            pq = __fma_rn(RC[0], qv[0], pq);
-            pq = __fma_rn(RC[1], qv[1], pq);
-        }
-        dst += sxy;
+        const long long ym[V] = {pc[-BW], pc[1 - BW]}, yp[V] = {pc[RT * BW], pc[RT * BW + 1]};
+        const long long left[RT] = {pc[-1], pc[BW - 1]}, right[RT] = {pc[V], pc[BW + V]};
+        double qv[RT][V];
+        spmv_points<CONV>(B, C, Ab, ym, yp, left, right, emax, qv);
+#pragma unroll
+        for (int j = 0; j < RT; ++j)
+            if (ok[j]) {
+                double* dst = q + (int64_t)k * sxy + (int64_t)(Y0 + j) * nx + X;
+                *reinterpret_cast<double2*>(dst) = make_double2(qv[j][0], qv[j][1]);
+                pq = __fma_rn(RC[j][0], qv[j][0], pq);
+                pq = __fma_rn(RC[j][1], qv[j][1], pq);
+            }
+#pragma unroll
+        for (int j = 0; j < RT; ++j)
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                B[j][i] = C[j][i];
+                C[j][i] = Ab[j][i];
+                RC[j][i] = RA[j][i];
+            }
         if constexpr (CONV) fence_proxy_async_smem();
-        if (__syncthreads_or(bad)) {
-            aborted = true;
-            return false;
-        }
+        aborted = __syncthreads_or(bad) != 0;
         // the slot of the plane below is free: every thread is past its last use
-        if (tid == 0 && issued < np) {
+        if (!aborted && tid == 0 && issued < np) {
             const int sl = s_cur == 0 ? NST - 1 : s_cur - 1;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bars[sl], kSpBoxBytes);
@@ -185,20 +163,6 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
         }
         s_cur = s_nxt;
         ph_cur = ph_nxt;
-        return true;
-    };
-    if (!aborted) {
-        int k = kb;
-        bool go = true;
-        for (; go && k < ke; ++k) {
-            go = step(X0, X1, X2, R1, R2);
-            X0[0] = X1[0];
-            X0[1] = X1[1];
-            X1[0] = X2[0];
-            X1[1] = X2[1];
-            R1[0] = R2[0];
-            R1[1] = R2[1];
-        }
     }
     if (aborted && tid == 0) {
         // the last load issued into each slot, consumed or not, completes
@@ -214,13 +178,13 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
     return pq;
 }
 
-__global__ void __launch_bounds__(kCgBlock, 4)
+__global__ void __launch_bounds__(kSpBlock, 6)
     k_cg_spmv_tma(const __grid_constant__ CUtensorMap map, OpDev A, double* __restrict__ q,
                   double* partials, CgScalars* S)
 {
     __shared__ __align__(128) long long stage[kSpNst * kSpStage];
     __shared__ __align__(8) uint64_t bars[kSpNst];
-    __shared__ double sh[kCgBlock / 32];
+    __shared__ double sh[kSpBlock / 32];
     __shared__ int32_t s_done;
     const int tid = threadIdx.x;
     grid_dependency_wait();   // p, the scalars and the stop flag come from the kernels before
@@ -252,9 +216,9 @@ __global__ void __launch_bounds__(kCgBlock, 4)
         return;
     }
     allow_dependents();
-    const double blk = block_sum<kCgBlock>(pq, sh);
+    const double blk = block_sum<kSpBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
-    const double tot = sum_partials(partials, gridDim.x, sh);
+    const double tot = sum_partials_nt<kSpBlock>(partials, gridDim.x, sh);
     if (threadIdx.x == 0) {
         S->ticket = 0;
         S->pq = tot;
@@ -282,7 +246,7 @@ int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p)
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
                     int nblocks, cudaStream_t stream)
 {
-    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nblocks, kCgBlock, stream, map, A, q, partials, S);
+    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nblocks, kSpBlock, stream, map, A, q, partials, S);
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "cg: spmv+dot kernel (TMA-staged)");
 }
 
