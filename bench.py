@@ -43,10 +43,10 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (the measured copy ra
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture of the kernel as it stands, keyed by
 # (arithmetic, grid edge, steps per launch): the FP64 exact-sum Interior kernel
-# (two rows per thread) on 512^3 read 1182.8 MB and wrote 1025.6 MB per launch
-# (mean of 2 launches).  Re-capture after any change to that kernel; sizes not
-# listed report null.
-KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2208416128}
+# (two rows per thread, one point in four converted on the FP64 pipe) on 512^3
+# read 1187.2 MB and wrote 1025.9 MB per launch (mean of 2 launches).
+# Re-capture after any change to that kernel; sizes not listed report null.
+KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2213105024}
 HEAT_MODES = {
     # plain FP64 handle: FP64 fields, exact int64 neighbour sum, one FP64 FMA per point
     "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "hbm",
