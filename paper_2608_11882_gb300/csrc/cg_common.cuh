@@ -175,8 +175,8 @@ __host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A, int nblocks)
 
 // q for one thread's 2 x 2 points of a plane from their values B (below), C
 // (at), A (above), the row below the first row and above the last, and the x
-// neighbours beyond the pairs: the exact-sum form (fixed-point values; point
-// 0 of a row converted back on the FP64 pipe, point 1 with integers, the same
+// neighbours beyond the pairs: the exact-sum form (fixed-point values; one of
+// the four converted back on the FP64 pipe, the others with integers, the same
 // double either way) or the FP64 pipe on raw bits.
 template <bool CONV>
 __device__ __forceinline__ void spmv_points(const long long (&B)[2][2], const long long (&C)[2][2],
@@ -194,7 +194,7 @@ __device__ __forceinline__ void spmv_points(const long long (&B)[2][2], const lo
             const long long yh = j == 1 ? yp[i] : C[1][i];
             if constexpr (CONV) {
                 const long long L = 6 * C[j][i] - (((B[j][i] + yl) + (xm + xp)) + (yh + A[j][i]));
-                qv[j][i] = i == 0 ? xs_unfix_dp(L, emax) : xs_unfix(L, emax);
+                qv[j][i] = (j == 0 && i == 0) ? xs_unfix_dp(L, emax) : xs_unfix(L, emax);
             } else {
                 auto d = [](long long b) { return __longlong_as_double(b); };
                 const double sv = ((d(B[j][i]) + d(yl)) + (d(xm) + d(xp))) + (d(yh) + d(A[j][i]));

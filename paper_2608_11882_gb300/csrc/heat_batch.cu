@@ -255,8 +255,8 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
                 const Q yh = j == RT - 1 ? yp[i] : cur[j + 1][i];
                 if constexpr (CONV) {
                     const long long L = xs_numerator(cur[j][i], xm, xp, yl, yh, below[j][i], above[j][i]);
-                    v[i] = i == 0 ? xs_apply<true>(craw[j][i], L, r, r2, emax)
-                                  : xs_apply<false>(craw[j][i], L, r, r2, emax);
+                    v[i] = (j == 0 && i == 0) ? xs_apply<true>(craw[j][i], L, r, r2, emax)
+                                              : xs_apply<false>(craw[j][i], L, r, r2, emax);
                 } else {
                     v[i] = Point<T, false>::update(cur[j][i], xm, xp, yl, yh, below[j][i], above[j][i], (T)r, 0);
                 }
