@@ -10,7 +10,8 @@
 // The CG of each inner solve is the textbook one of Section 7.5.  Its dot
 // products accumulate in FP64 across the grid; each thread adds at most 8
 // FP32 products (4 in the vectorised kernels) before promoting them to its
-// FP64 sum, so the long sums --
+// FP64 sum (the TMA-staged SpMV keeps that sum as an exact FP32 pair and
+// converts it once), so the long sums --
 // the part whose stability needs FP64 -- stay FP64 while the FP64 pipe (about
 // 1/64 of FP32 issue on this GPU) sees one add per 8 elements.  alpha, beta
 // and the residual norms are FP64 device scalars.  Refinement converges while
@@ -99,6 +100,25 @@ struct Acc32 {
         hi += (double)s;
     }
     __device__ __forceinline__ double total() const { return hi + (double)lo; }
+};
+
+// The same sums kept in two FP32 words (Knuth's two-sum: hi + lo holds the
+// running sum to about 2^-48 of its size) and turned into FP64 once, at the
+// end: groups of four products summed in FP32 as in Acc32::add4, then added
+// without rounding error -- no FP64 instruction in the loop.
+struct AccF2 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add4(float a0, float b0, float a1, float b1, float a2, float b2, float a3,
+                                         float b3)
+    {
+        const float v = __fmaf_rn(a3, b3, __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0))));
+        const float s = __fadd_rn(hi, v);
+        const float bv = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
 };
 
 __device__ __forceinline__ float apply32_csr(const OpDev32& A, const float* __restrict__ p, int64_t row)
@@ -328,7 +348,7 @@ __global__ void __launch_bounds__(kCgBlock)
     uint32_t seq = 0;   // planes staged so far: plane j of the block sits in slot j % NST
     bool bad = false, aborted = false, drained = true;
     int issued = 0, np = 0;
-    Acc32 pq;
+    AccF2 pq;
     for (int64_t item = blockIdx.x; item < P.items && !aborted; item += gridDim.x) {
         const int64_t tile = item % P.tiles;
         const int kb = (int)(item / P.tiles) * P.kc, ke = min(kb + P.kc, A.nz);
@@ -593,8 +613,8 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
                 // dependent launches: each kernel's launch overlaps the previous
                 // kernel's final reduction (it waits for that kernel on entry)
                 if (m->tma)
-                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->pmap, m->A32, m->q,
-                                                 m->partials, m->S),
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->pmap,
+                                                 m->A32, m->q, m->partials, m->S),
                                 "cg mixed: kernel launch");
                 else if (c->A.kind == HS_OP_STENCIL7)
                     HS_TRY_CUDA(launch_dependent(k_mx_spmv_dot<HS_OP_STENCIL7>, G, kCgBlock, c->stream, m->A32,

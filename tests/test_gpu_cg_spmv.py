@@ -109,7 +109,7 @@ def check_against_exact_and_oracle(p, q, pq, conv, depth):
 
 def reduction_depth(shape):
     """Longest chain of additions in the fused p.q of any SpMV kernel: a
-    thread's own accumulation (two points per plane of each (tile, chunk) item
+    thread's own accumulation (four points per plane of each (tile, chunk) item
     it takes in the staged kernels, its rows in the row kernel), the block's
     shuffle tree (8 levels), a thread's share of the partials, and the final
     tree.  The work split restates the plan the kernels use for cg_run's block
@@ -121,8 +121,8 @@ def reduction_depth(shape):
     chunks = max(1, min(-(-grid // tiles), max(nz // 4, 1)))
     kc = -(-nz // chunks)
     items = tiles * -(-nz // kc)
-    chain = max(2 * kc * -(-items // grid), -(-n // (grid * 256)))
-    return chain + 8 + -(-grid // 256) + 8
+    chain = max(4 * kc * -(-items // grid), -(-n // (grid * 256)))
+    return chain + 8 + -(-grid // 128) + 8
 
 
 SHAPES = [(176, 176, 176), (200, 101, 190), (160, 120, 177), (256, 256, 256)]
