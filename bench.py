@@ -116,8 +116,30 @@ def parse_args():
     ap.add_argument("--tdepth", type=int, default=0,
                     help="steps per pass of the timed heat handle (0: library choice)")
     ap.add_argument("--no-side", action="store_true",
-                    help="skip the untimed one-solve runs of the other heat modes")
+                    help="skip every side measurement (same as --sides none)")
+    ap.add_argument("--sides", default="all",
+                    help="comma list of side measurements after the timed steps: modes, batching, "
+                         "paper, mixed, serving; 'all' or 'none'")
     return ap.parse_args()
+
+
+SIDES = ("modes", "batching", "paper", "mixed", "serving")
+
+
+def sides_of(args) -> set:
+    """The side measurements to run after the timed steps."""
+    if args.no_side or args.sides == "none":
+        return set()
+    if args.sides == "all":
+        out = set(SIDES)
+    else:
+        out = {x.strip() for x in args.sides.split(",") if x.strip()}
+        bad = out - set(SIDES)
+        if bad:
+            raise SystemExit(f"unknown --sides entries: {sorted(bad)}")
+    if args.no_serving:
+        out.discard("serving")
+    return out
 
 
 def dist_info():
@@ -635,8 +657,10 @@ def run_ours(args):
                        "covers": "heat: heat_upload from pinned host, heat_step, heat_read to pinned host",
                        "cg_matrix_free_host_buffers_its_per_s": it_mf[-1] / statistics.median(e2e_cg)}
 
+    sides = sides_of(args)
+
     # ---- the other heat modes, one untimed-region solve each -------------------
-    if not args.no_side:
+    if "modes" in sides:
         def solve_once(h, src):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -690,15 +714,15 @@ def run_ours(args):
         line["heat_modes"] = side
 
     # ---- batching: 256 uneven heat grids in one persistent launch, 64 CG solves -
-    if not args.no_side:
+    if "batching" in sides:
         line["batching"] = batching_side(pkg, stream, hbm_gbs, peak_kind)
 
     # ---- the paper's own problem: variable kappa, N = 512, 500 steps ---------------
-    if not args.no_side:
+    if "paper" in sides:
         line["paper_problem"] = paper_problem_side(pkg, stream, hbm_gbs, peak_kind)
 
     # ---- mixed-precision CG beside the FP64 solves (untimed region) ------------
-    if not args.no_side:
+    if "mixed" in sides:
         mixed = {}
         for kind, op in (("matrix_free", pkg.Operator.stencil(m, m, m)), ("csr", pkg.Operator.csr(*csr_dev))):
             with pkg.CG(op, stream=stream, mixed=True) as cgm:
@@ -724,7 +748,7 @@ def run_ours(args):
         line["cg"]["mixed_f32_krylov"] = mixed
 
     # ---- serving: the Poisson request stream, closed loop and one offered load ----
-    if not args.no_side and not args.no_serving:
+    if "serving" in sides:
         line["serving"] = serving_side(args, loads=(0.7,))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

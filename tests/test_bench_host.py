@@ -101,3 +101,14 @@ def test_reference_arm_json_line():
 def test_reference_arm_other_ranks_exit_quietly():
     p = run_reference({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0 and not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_side_selection(bench):
+    import argparse
+    ns = lambda **kw: argparse.Namespace(**{"no_side": False, "no_serving": False, "sides": "all", **kw})
+    assert bench.sides_of(ns()) == set(bench.SIDES)
+    assert bench.sides_of(ns(no_side=True)) == set()
+    assert bench.sides_of(ns(sides="mixed,batching")) == {"mixed", "batching"}
+    assert bench.sides_of(ns(no_serving=True)) == set(bench.SIDES) - {"serving"}
+    with pytest.raises(SystemExit):
+        bench.sides_of(ns(sides="bogus"))
