@@ -8,10 +8,10 @@
 //     x += d                    in FP64
 //
 // The CG of each inner solve is the textbook one of Section 7.5.  Its dot
-// products accumulate in FP64 across the grid; each thread adds at most 8
-// FP32 products (4 in the vectorised kernels) before promoting them to its
-// FP64 sum (the TMA-staged SpMV keeps that sum as an exact FP32 pair and
-// converts it once), so the long sums --
+// products accumulate in FP64 across the grid: each thread adds at most 4
+// FP32 products before promoting them to its FP64 sum (the SpMV kernels keep
+// that sum as an exact FP32 two-sum pair instead and convert it once), so
+// the long sums --
 // the part whose stability needs FP64 -- stay FP64 while the FP64 pipe (about
 // 1/64 of FP32 issue on this GPU) sees one add per 8 elements.  alpha, beta
 // and the residual norms are FP64 device scalars.  Refinement converges while
@@ -118,6 +118,16 @@ struct AccF2 {
         hi = s;
         lo = __fadd_rn(lo, err);
     }
+    // one product, rounded to FP32, added without rounding error
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float v = __fmul_rn(a, b);
+        const float s = __fadd_rn(hi, v);
+        const float bv = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
     __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
 };
 
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(kCgBlock)
     grid_dependency_wait();
     if (*(volatile int32_t*)&S->inner_done) return;
     __shared__ double sh[kCgBlock / 32];
-    Acc32 pq;
+    AccF2 pq;
     const int64_t row0 = (int64_t)blockIdx.x * kCgBlock + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * kCgBlock;
     if (KIND == HS_OP_STENCIL7) {
@@ -229,46 +239,26 @@ __global__ void __launch_bounds__(kCgBlock)
             int64_t c = (int64_t)kb * sxy + (int64_t)j * nx + i;
             float below = kb > 0 ? __ldg(p + c - sxy) : 0.0f;
             float cur = __ldg(p + c);
-            // planes in groups of four: the four products are promoted together
-            for (int k4 = kb; k4 < ke; k4 += 4) {
-                float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f}, qs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = k4 + u;
-                    if (k < ke) {
-                        const float above = k < nz - 1 ? __ldg(p + c + sxy) : 0.0f;
-                        const float ym = j > 0 ? __ldg(p + c - nx) : 0.0f;
-                        const float xm = i > 0 ? __ldg(p + c - 1) : 0.0f;
-                        const float xp = i < nx - 1 ? __ldg(p + c + 1) : 0.0f;
-                        const float yp = j < ny - 1 ? __ldg(p + c + nx) : 0.0f;
-                        const float sum = ((below + ym) + (xm + xp)) + (yp + above);
-                        const float qv = __fmaf_rn(6.0f, cur, -sum);
-                        q[c] = qv;
-                        pv[u] = cur;
-                        qs[u] = qv;
-                        below = cur;
-                        cur = above;
-                        c += sxy;
-                    }
-                }
-                pq.add4(pv[0], qs[0], pv[1], qs[1], pv[2], qs[2], pv[3], qs[3]);
+            for (int k = kb; k < ke; ++k) {
+                const float above = k < nz - 1 ? __ldg(p + c + sxy) : 0.0f;
+                const float ym = j > 0 ? __ldg(p + c - nx) : 0.0f;
+                const float xm = i > 0 ? __ldg(p + c - 1) : 0.0f;
+                const float xp = i < nx - 1 ? __ldg(p + c + 1) : 0.0f;
+                const float yp = j < ny - 1 ? __ldg(p + c + nx) : 0.0f;
+                const float sum = ((below + ym) + (xm + xp)) + (yp + above);
+                const float qv = __fmaf_rn(6.0f, cur, -sum);
+                q[c] = qv;
+                pq.add(cur, qv);
+                below = cur;
+                cur = above;
+                c += sxy;
             }
         }
     } else {
-        // rows row0, row0 + stride, ... in groups of four: the four products are promoted together
-        for (int64_t row4 = row0; row4 < A.n; row4 += 4 * stride) {
-            float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f}, qs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t row = row4 + u * stride;
-                if (row < A.n) {
-                    const float qv = apply32_csr(A, p, row);
-                    q[row] = qv;
-                    pv[u] = __ldg(p + row);
-                    qs[u] = qv;
-                }
-            }
-            pq.add4(pv[0], qs[0], pv[1], qs[1], pv[2], qs[2], pv[3], qs[3]);
+        for (int64_t row = row0; row < A.n; row += stride) {
+            const float qv = apply32_csr(A, p, row);
+            q[row] = qv;
+            pq.add(__ldg(p + row), qv);
         }
     }
     allow_dependents();
