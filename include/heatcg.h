@@ -386,8 +386,9 @@ int cg_run(hs_cg_t c, const void* b, void* x, int host_buffers, double rtol, int
  * with its Krylov vectors (d, r', p, q) and operator in FP32 solves A d = r,
  * reducing its residual by inner_rtol or by just what reaching rtol needs
  * (with a factor-2 margin), whichever is less, x += d in FP64, repeat.  Dot products accumulate in FP64 (each
- * thread promotes after at most 8 FP32 products); alpha, beta and the residual
- * norms are FP64.  The stop test and info->relres_true use the FP64 residual,
+ * thread promotes after at most 4 FP32 products, or keeps an exact FP32
+ * two-sum pair that it converts once); alpha, beta and the residual norms are
+ * FP64.  The stop test and info->relres_true use the FP64 residual,
  * so the returned x meets rtol in FP64 terms; info->iters counts inner
  * iterations (max_iter bounds them) and info->refinements the inner solves.
  * A CSR operator's values are rounded to an FP32 copy the context owns.
