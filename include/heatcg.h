@@ -117,7 +117,8 @@ typedef struct {
     uint32_t flags;        /* HS_* heat flags                                 */
     int32_t  dtype;        /* HS_F64 or HS_F32: storage and arithmetic type   */
     int32_t  tdepth;       /* time steps per pass over HBM: 0 = library choice
-                              (currently 1), 1 = the Interior + Boundary
+                              (2 for HS_F32 without HS_VARKAPPA or
+                              HS_SCHED_FULL, else 1), 1 = the Interior + Boundary
                               kernels every step, or 2, 3, 4 = temporal
                               blocking (see heat_step)                     */
     void*    stream;       /* cudaStream_t for all work of this handle        */

@@ -573,22 +573,30 @@ int timed_interior(hs_heat* h)
     return HS_OK;
 }
 
-// Temporal depth when the descriptor leaves it to the library: FP64 is bound
-// by the FP64 pipe (blocking saves only bytes), the others by HBM.
-int default_tdepth(Arith)
+// Temporal depth when the descriptor leaves it to the library.  FP32 is bound
+// by HBM, and two steps per pass move half the bytes of one: at 512^3 the
+// L = 2 pass runs 880 GLUP/s against 761 for one step per pass, while depths 3
+// and 4 (one block per SM) fall below one step per pass.  FP64 and FIXED64 are
+// bound by the FP64 pipe and the integer pipes: blocking saves only bytes and
+// adds the halo's work.  The variable-coefficient problem runs one step per
+// pass.
+int default_tdepth(Arith a, uint32_t flags)
 {
-    return 1;
+    return (a == A_F32 && !(flags & HS_VARKAPPA)) ? 2 : 1;
 }
 
-int pick_kc_tb(const HeatGeom& g, int L)
+int pick_kc_tb(const HeatGeom& g, int arith, int L)
 {
-    const int TX = 32 - 2 * L, TY = kTbRows - 2 * L;
+    int TX = 0, TY = 0;
+    tb_tile(arith, L, g.nx, &TX, &TY);
     const int64_t tiles = (int64_t)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    const int64_t target = (int64_t)kNumSMs * 2 * 6;   // about six waves of two blocks per SM
+    // about six waves of two blocks per SM: 35-plane chunks at 512^3 in FP32,
+    // measured ahead of 27 (eight waves) and 52 or 64 (three or four)
+    const int64_t target = (int64_t)kNumSMs * 12;
     int64_t chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
     int64_t kc = (g.nz + chunks - 1) / chunks;
-    const int64_t floor_kc = 16 * L;                   // keep the z halo (2L planes) small
+    const int64_t floor_kc = 8 * L;                    // keep the z halo (2L planes) small
     if (kc < floor_kc) kc = floor_kc;
     if (kc > g.nz) kc = g.nz;
     return (int)kc;
@@ -619,7 +627,7 @@ int tb_pass(hs_heat* h, int L)
     TbCall c;
     c.arith = h->arith;
     c.L = L;
-    c.kc = pick_kc_tb(h->g, L);
+    c.kc = pick_kc_tb(h->g, h->arith, L);
     c.map = &h->maps[h->cur];
     c.dst = h->buf[1 - h->cur];
     c.g = &h->g;
@@ -794,7 +802,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     h->cur = 0;
     h->steps = 0;
     h->kchunk = pick_kchunk(h->g);
-    h->tdepth = desc->tdepth ? desc->tdepth : default_tdepth(h->arith);
+    h->tdepth = desc->tdepth ? desc->tdepth : default_tdepth(h->arith, desc->flags);
     if (h->flags & HS_SCHED_FULL) h->tdepth = 1;
     const size_t bytes = (size_t)h->g.total * h->elem;
     rc = check_user_buffers(desc, bytes);
@@ -856,7 +864,7 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
                                        : h->dtype == HS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
         uint32_t box_x = 0, box_y = 0;
-        tb_box(h->arith, &box_x, &box_y);
+        tb_box(h->arith, h->g.nx, &box_x, &box_y);
         h->tbox[0] = box_x;
         h->tbox[1] = box_y;
         for (int b = 0; b < 2; ++b) {

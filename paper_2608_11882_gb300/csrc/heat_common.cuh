@@ -265,8 +265,9 @@ inline T tb_param(const TbCall& c)
 }
 
 int tb_launch(const TbCall& c);
-// TMA box (elements x rows) the temporally blocked kernel loads for an arithmetic.
-int tb_box(int arith, uint32_t* box_x, uint32_t* box_y);
+// TMA box (elements x rows) the temporally blocked kernel loads for an
+// arithmetic and a grid nx points wide.
+int tb_box(int arith, int nx, uint32_t* box_x, uint32_t* box_y);
 
 // One launch of the streaming Interior kernel (heat_stream.cu): one step over
 // the k-planes [kbeg, kend).
@@ -339,8 +340,12 @@ int heat_batch_view(hs_heat_t h, HeatBatchView* v);
 // Records that a batch advanced the handle by `steps` steps.
 int heat_batch_advance(hs_heat_t h, int64_t steps);
 
-// Rows of the temporally blocked kernel's thread block (its tile is
-// (32 - 2L) x (kTbRows - 2L) columns).
-constexpr int kTbRows = 32;
+// Thread rows of the temporally blocked kernel's block and rows per thread:
+// its region is kTbThreadRows kTbRowsPerThread rows high (the tile that plus
+// the halo of L rows on each side).
+constexpr int kTbThreadRows = 12;
+constexpr int kTbRowsPerThread = 2;
+// Output tile (x columns, y rows) of the temporally blocked kernel.
+void tb_tile(int arith, int L, int nx, int* tx, int* ty);
 
 }  // namespace hcg

@@ -10,7 +10,12 @@ from workloads import heat_u0_single_mode
 pytestmark = pytest.mark.gpu
 
 DEPTHS = [2, 3, 4]
-SHAPES = [(1, 1, 1), (2, 3, 5), (33, 9, 17), (70, 3, 40), (40, 65, 31), (5, 100, 90)]
+# (70, 90, 300), (43, 67, 263) and (40, 70, 384) hold blocks whose every
+# computed point lies inside the interior (the unmasked form) beside edge
+# blocks, several z-chunks and ragged tails; FP32 grids 384 and 250 wide take
+# the 34-thread rows (128-column tiles), the others 32-thread rows
+SHAPES = [(1, 1, 1), (2, 3, 5), (33, 9, 17), (70, 3, 40), (40, 65, 31), (5, 100, 90),
+          (70, 90, 300), (43, 67, 263), (40, 70, 384), (9, 30, 250)]
 
 
 @pytest.fixture(scope="module")
@@ -68,3 +73,17 @@ def test_bad_tdepth(pkg):
             pkg.Heat(8, 8, 8, 0.1, tdepth=bad)
     with pytest.raises(pkg.HeatCGError):
         pkg.Heat(8, 8, 8, 0.1, flags=pkg.HS_SCHED_FULL, tdepth=2)
+
+
+def test_default_depth(pkg):
+    """The library's choice: two steps per pass for FP32 (HBM-bound), one step
+    per pass for FP64, for the one-step schedule and for the
+    variable-coefficient problem."""
+    with pkg.Heat(8, 8, 8, 0.1, dtype="f32") as h:
+        assert h.tdepth == 2
+    with pkg.Heat(8, 8, 8, 0.1) as h:
+        assert h.tdepth == 1
+    with pkg.Heat(8, 8, 8, 0.1, dtype="f32", flags=pkg.HS_SCHED_FULL) as h:
+        assert h.tdepth == 1
+    with pkg.Heat(8, 8, 8, 0.01, dtype="f32", flags=pkg.HS_VARKAPPA) as h:
+        assert h.tdepth == 1
