@@ -44,9 +44,11 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (the measured copy ra
 # dominant kernel, from one ncu capture of the kernel as it stands, keyed by
 # (arithmetic, grid edge, steps per launch): the FP64 exact-sum Interior kernel
 # (two rows per thread, one point in four converted on the FP64 pipe) on 512^3
-# read 1187.2 MB and wrote 1025.9 MB per launch (mean of 2 launches).
+# read 1187.2 MB and wrote 1025.9 MB per launch (mean of 2 launches); the FP32
+# blocked kernel at depth 2 (34-thread rows, plane loop unrolled by three) on
+# 512^3 read 626.5 MB and wrote 494.2 MB per pass (mean of 2 passes).
 # Re-capture after any change to that kernel; sizes not listed report null.
-KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2213105024}
+KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2213105024, ("f32", 512, 2): 1120694016}
 HEAT_MODES = {
     # plain FP64 handle: FP64 fields, exact int64 neighbour sum, one FP64 FMA per point
     "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "hbm",
@@ -606,13 +608,15 @@ def run_ours(args):
         "config": {"workload": f"heat {n}^3 {args.heat_mode} r={args.r} {hsteps} steps (u0 = 8 sine modes k in "
                                f"[1,16] + 1e-3 U[-1,1]) + CG {m}^3 FP64 7-pt Dirichlet Laplacian, "
                                f"matrix-free and CSR int32 (nnz {nnz}), b ~ N(0,1), rtol {args.rtol}",
-                   "arithmetic": mode["desc"] if heat.tdepth == 1 or mode.get("desc", "").startswith(
-                       "FP64 fields; 5") else "FP64 fields; FP64 pipe (temporal blocking)",
+                   "arithmetic": "FP64 fields; FP64 pipe (temporal blocking)"
+                   if args.heat_mode == "f64" and heat.tdepth > 1 else mode["desc"],
+                   "tdepth": heat.tdepth,
                    "value_covers": "heat segment (upload + steps + device readback), device time",
                    "l2": "no flush: every input exceeds L2 (field 1.07 GB, vectors 134 MB)",
                    "parallelism": f"replicas x{world}", "seed": SEED},
         "heat": {"glups": value / world, "ms_per_solve": heat_ms / args.steps,
-                 "hbm_frac_16B_per_lup": value / world * 16 / hbm_gbs},
+                 "bytes_per_lup": mode["bytes"],
+                 "hbm_frac_one_step_per_pass": value / world * mode["bytes"] / hbm_gbs},
         "cg": {"matrix_free": {"iters": it_mf[-1], "its_per_s": it_mf[-1] / (statistics.median(seg["cg_mf"]) * 1e-3),
                                "ms_per_solve": statistics.median(seg["cg_mf"]),
                                "relres_true": infos[-1][0]["relres_true"],
