@@ -12,8 +12,9 @@
 // What differs is how p arrives: each plane of the tile with its one-point
 // halo is one 3-D tiled TMA box, (8 + 2) rows of 68 doubles starting 16 bytes
 // left of the tile, loaded into a ring of kSpNst = 4 stages up to 2 planes
-// ahead of use (six blocks of 128 threads per SM, 85 registers: measured
-// ahead of eight blocks at 64 registers).  The tensor map spans the unpadded nx x ny x nz vector,
+// ahead of use (five blocks of 128 threads per SM, 94 registers: 3730 CG
+// iterations/s at 256^3 against 3659 with six blocks, whose 80 registers
+// spill, and fewer with eight blocks at 64 registers).  The tensor map spans the unpadded nx x ny x nz vector,
 // so boxes that reach past the box of the grid (the planes -1 and nz, the rows
 // -1 and ny, the columns -1 and nx) read zeros: the Dirichlet boundary with no
 // bounds checks.  The box starts at x0 - 2 with x0 a multiple of 64, so its x
@@ -178,7 +179,7 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const Op
     return pq;
 }
 
-__global__ void __launch_bounds__(kSpBlock, 6)
+__global__ void __launch_bounds__(kSpBlock, 5)
     k_cg_spmv_tma(const __grid_constant__ CUtensorMap map, OpDev A, double* __restrict__ q,
                   double* partials, CgScalars* S)
 {
