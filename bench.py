@@ -76,7 +76,7 @@ HEAT_MODES = {
 #    entry and 4 B per row for CSR), update 24 B, p update 12 B; per refinement:
 #    FP64 SpMV 16 B (+ 12 B per entry, 4 B per row for CSR), residual 36 B
 #    (read b, A x; write r in FP64 and r, p, d in FP32), correction 20 B.
-VK_FP64_OPS_PER_LUP = 23
+VK_FP64_OPS_PER_LUP = 16   # FP64 variable-kappa update from precomputed face sums of kappa
 CG_BYTES_PER_ROW = 88
 MIXED_INNER_BYTES_PER_ROW = 44
 MIXED_REFINE_BYTES_PER_ROW = 72
@@ -260,9 +260,12 @@ def paper_problem_side(pkg, stream, hbm_gbs, peak_kind):
             ms = e0.elapsed_time(e1)
         lups = float(n) ** 3 * steps
         out[dtype] = {"glups": lups / (ms * 1e-3) / 1e9, "ms": ms}
-        bpl = 32 if dtype == "f64" else 16
-        hbm = hbm_roofline(f"k_vk_interior<{'double' if dtype == 'f64' else 'float'}> + k_vk_boundary",
-                           lups * bpl, ms, hbm_gbs, peak_kind, bytes_per_lup=bpl)
+        # FP64: u read and written, three face-sum arrays of kappa, dt f (48 B);
+        # FP32: u read and written, kappa, dt f (16 B)
+        bpl = 48 if dtype == "f64" else 16
+        kname = "k_vk_interior_faces + k_vk_boundary_faces" if dtype == "f64" else \
+            "k_vk_interior<float> + k_vk_boundary<float>"
+        hbm = hbm_roofline(kname, lups * bpl, ms, hbm_gbs, peak_kind, bytes_per_lup=bpl)
         if dtype == "f64":
             rate = lups * VK_FP64_OPS_PER_LUP / (ms * 1e-3) / 1e12
             out[dtype]["roofline"] = {"bound": "alu", "kernel": hbm["kernel"], "achieved": rate,

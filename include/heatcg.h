@@ -86,8 +86,10 @@ extern "C" {
  * (the paper does not print D; this is the reading consistent with its
  * beta = dt/(2h^2)).  Here r means dt / h_min^2 (the paper's choice is
  * dt = h^2/(12 kappa_max), r = 1/(12 * 0.95)); the stability bound is
- * r <= 1/(6 kappa_max).  kappa (on every node, boundary included) and dt f
- * live on the device beside u, as in the paper's 1-GPU Baseline.  HS_F64 or
+ * r <= 1/(6 kappa_max).  The coefficients (on every node, boundary included)
+ * and dt f live on the device beside u, as in the paper's 1-GPU Baseline:
+ * kappa itself for HS_F32, for HS_F64 the three face sums k[i+1] + k[i] of
+ * each node (constant in time; the same values the formula forms).  HS_F64 or
  * HS_F32; excludes HS_FIXED64, HS_EXACT_ROUNDING, HS_SCHED_FULL and tdepth > 1;
  * cannot join a heat batch. */
 #define HS_VARKAPPA         0x10u
@@ -150,8 +152,9 @@ int heat_buffer_bytes(const hs_heat_desc* desc, size_t* bytes);
 
 /* Device bytes heat_create would allocate for desc (for admission control):
  * the two field buffers unless the caller supplies them, and the per-step
- * state of the exact-sum and FIXED64 arithmetics (and kappa, dt f for
- * HS_VARKAPPA). */
+ * state of the exact-sum and FIXED64 arithmetics (and the coefficient
+ * arrays and dt f for HS_VARKAPPA: two fields' worth for HS_F32, four for
+ * HS_F64). */
 int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
 
 /* Load the interior field u (nx*ny*nz elements of the handle's dtype, x

@@ -310,7 +310,7 @@ struct hs_heat {
     uint32_t tbox[2];      // box of maps[]
     uint32_t sbox[2];      // box of smaps[]
     int kc_stream;         // k-planes per block of the streaming Interior kernel
-    void* kap;             // HS_VARKAPPA: kappa on every padded node
+    void* kap;             // HS_VARKAPPA: FP32 kappa on every padded node, FP64 its three face sums
     void* fdt;             // HS_VARKAPPA: dt f on the interior
     double vbx, vby, vbz;  // HS_VARKAPPA: dt / (2 h_d^2)
     // Large grids run each step's Boundary kernel on a side stream, beside the
@@ -776,7 +776,8 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
     *bytes = user_bufs ? 0 : 2 * (size_t)g.total * elem_size(desc->dtype);
     const Arith a = pick_arith(desc);
     if (a == A_FX64 || a == A_F64_XS) *bytes += sizeof(FxState);
-    if (desc->flags & HS_VARKAPPA) *bytes += 2 * (size_t)g.total * elem_size(desc->dtype);
+    if (desc->flags & HS_VARKAPPA)   // coefficients (FP64: three face arrays) and dt f
+        *bytes += (desc->dtype == HS_F64 ? 4 : 2) * (size_t)g.total * elem_size(desc->dtype);
     return HS_OK;
 }
 
@@ -889,9 +890,11 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
     }
     if (h->flags & HS_VARKAPPA) {
         const size_t bytes = (size_t)h->g.total * h->elem;
-        cudaError_t e = dev_alloc(&h->kap, bytes, h->stream);
+        // FP64 keeps the three face sums of kappa, FP32 kappa itself
+        const size_t cbytes = h->dtype == HS_F64 ? 3 * bytes : bytes;
+        cudaError_t e = dev_alloc(&h->kap, cbytes, h->stream);
         if (e == cudaSuccess) e = dev_alloc(&h->fdt, bytes, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->kap, 0, bytes, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->kap, 0, cbytes, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->fdt, 0, bytes, h->stream);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "heat_create: kappa/source arrays");

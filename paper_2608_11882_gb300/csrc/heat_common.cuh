@@ -314,7 +314,8 @@ struct VkCall {
     int f64;                 // 1: FP64, 0: FP32
     const void* src;
     void* dst;
-    void* kap;               // kappa on every padded node
+    void* kap;               // FP32: kappa on every padded node; FP64: the three face
+                             // sums of kappa (x, y, z arrays of g.total elements each)
     void* fdt;               // dt f on the interior
     const HeatGeom* g;
     double bx, by, bz;       // dt / (2 h_d^2)

@@ -4,12 +4,17 @@
 //     u' = u + dt f + sum_d dt/(2 h_d^2) D_d(u),
 //     D_x = (k[i+1] + k[i]) (u[i+1] - u[i]) - (k[i] + k[i-1]) (u[i] - u[i-1])
 // (face-averaged kappa: the reading of the unprinted D that matches
-// beta = dt/(2h^2)).  As in the paper's Algorithm "1-GPU Baseline", kappa and
-// dt f are arrays resident beside u: kappa on every node of the padded box
-// (the boundary nodes carry kappa too), dt f on the interior.  Interior and
-// Boundary kernels as for the constant-coefficient update; per point 11 loads
-// (u and kappa at the centre's six neighbours, u, kappa and dt f at the
-// centre, mostly from L1), 22 floating-point instructions.
+// beta = dt/(2h^2)).  As in the paper's Algorithm "1-GPU Baseline", the
+// coefficients and dt f are arrays resident beside u, dt f on the interior.
+// Interior and Boundary kernels as for the constant-coefficient update.
+//
+// FP32 keeps kappa on every node of the padded box (16 bytes per update:
+// the kernel is bound by HBM, where three face arrays would cost more than the
+// six additions they save).  FP64 is bound by the FP64 pipe, so it keeps the
+// three face sums k[i+1] + k[i] of each node instead (constant in time, formed
+// once at creation, bit for bit the sums the formula forms every step) and
+// carries the z difference u[k+1] - u[k] to the next plane: 16 FP64
+// instructions per update instead of 23, at 48 bytes per update.
 #include <cmath>
 
 #include "heat_common.cuh"
@@ -37,6 +42,100 @@ __global__ void __launch_bounds__(256) k_vk_init(T* __restrict__ kap, T* __restr
         const bool interior = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
         fdt[c] = interior ? (T)(dt * (1.0 + cospi(x) * cospi(y) * cospi(z))) : (T)0;
     }
+}
+
+// FP64: the three face sums of kappa on every padded node (f*[c] = kappa at the
+// node's +d neighbour + kappa at the node, zero where that neighbour lies
+// outside the padded box) and dt f on the interior.  The kappa values are the
+// same expression as k_vk_init's, so the sums are the bits the formula forms.
+__global__ void __launch_bounds__(256) k_vk_init_faces(double* __restrict__ fc, double* __restrict__ fdt,
+                                                       HeatGeom g, double dt)
+{
+    const double hx = 1.0 / (g.nx + 1), hy = 1.0 / (g.ny + 1), hz = 1.0 / (g.nz + 1);
+    const int64_t n = (int64_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+    auto kappa = [&](int I, int J, int K) {
+        return 0.5 + 0.45 * sinpi(I * hx) * sinpi(J * hy) * sinpi(K * hz);
+    };
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t % (g.nx + 2));
+        const int64_t jk = t / (g.nx + 2);
+        const int J = (int)(jk % (g.ny + 2));
+        const int K = (int)(jk / (g.ny + 2));
+        const int64_t c = (int64_t)K * g.plane + (int64_t)J * g.pitch + g.lead - 1 + I;
+        const double kc = kappa(I, J, K);
+        fc[c] = I <= g.nx ? kappa(I + 1, J, K) + kc : 0.0;
+        fc[g.total + c] = J <= g.ny ? kappa(I, J + 1, K) + kc : 0.0;
+        fc[2 * g.total + c] = K <= g.nz ? kappa(I, J, K + 1) + kc : 0.0;
+        const bool interior = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
+        fdt[c] = interior ? dt * (1.0 + cospi(I * hx) * cospi(J * hy) * cospi(K * hz)) : 0.0;
+    }
+}
+
+// One FP64 update from the face sums: cxp = k[i+1] + k[i], cxm = k[i] + k[i-1]
+// (the -x neighbour's +x face) and so on, and the z difference below the
+// point, dzm = u[k] - u[k-1], carried from the plane below.
+__device__ __forceinline__ double vk_point_faces(double uc, double uxm, double uxp, double uym, double uyp,
+                                                 double dzp, double dzm, double cxm, double cxp, double cym,
+                                                 double cyp, double czm, double czp, double f, double bx,
+                                                 double by, double bz)
+{
+    const double dx = __fma_rn(cxp, __dsub_rn(uxp, uc), -__dmul_rn(cxm, __dsub_rn(uc, uxm)));
+    const double dy = __fma_rn(cyp, __dsub_rn(uyp, uc), -__dmul_rn(cym, __dsub_rn(uc, uym)));
+    const double dz = __fma_rn(czp, dzp, -__dmul_rn(czm, dzm));
+    return __dadd_rn(__dadd_rn(uc, f), __fma_rn(bz, dz, __fma_rn(by, dy, __dmul_rn(bx, dx))));
+}
+
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_interior_faces(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
+                        const double* __restrict__ fdt, HeatGeom g, double bx, double by, double bz, int kbeg,
+                        int kend, int kchunk)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = kbeg + (int)blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, kend);
+    if (k0 >= k1) return;
+    const int64_t P = g.plane, Y = g.pitch;
+    const double* fx = fc;
+    const double* fy = fc + g.total;
+    const double* fz = fc + 2 * g.total;
+    int64_t c = g.at(i, j, k0);
+    double uc = __ldg(src + c);
+    double dzm = __dsub_rn(uc, __ldg(src + c - P));
+    double czm = __ldg(fz + c - P);
+    for (int k = k0; k < k1; ++k) {
+        const double ua = __ldg(src + c + P), cza = __ldg(fz + c);
+        const double dzp = __dsub_rn(ua, uc);
+        dst[c] = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y),
+                                __ldg(src + c + Y), dzp, dzm, __ldg(fx + c - 1), __ldg(fx + c),
+                                __ldg(fy + c - Y), __ldg(fy + c), czm, cza, __ldg(fdt + c), bx, by, bz);
+        uc = ua;
+        dzm = dzp;
+        czm = cza;
+        c += P;
+    }
+}
+
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_boundary_faces(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
+                        const double* __restrict__ fdt, HeatGeom g, double bx, double by, double bz)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
+    const int64_t P = g.plane, Y = g.pitch;
+    const int64_t c = g.at(i, j, k);
+    const double* fx = fc;
+    const double* fy = fc + g.total;
+    const double* fz = fc + 2 * g.total;
+    const double uc = __ldg(src + c);
+    dst[c] = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y), __ldg(src + c + Y),
+                            __dsub_rn(__ldg(src + c + P), uc), __dsub_rn(uc, __ldg(src + c - P)),
+                            __ldg(fx + c - 1), __ldg(fx + c), __ldg(fy + c - Y), __ldg(fy + c),
+                            __ldg(fz + c - P), __ldg(fz + c), __ldg(fdt + c), bx, by, bz);
 }
 
 template <typename T>
@@ -100,7 +199,7 @@ int vk_init(const VkCall& c, double dt)
     int64_t blocks = (n + 255) / 256;
     if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
     if (c.f64)
-        k_vk_init<double><<<(unsigned)blocks, 256, 0, c.stream>>>((double*)c.kap, (double*)c.fdt, *c.g, dt);
+        k_vk_init_faces<<<(unsigned)blocks, 256, 0, c.stream>>>((double*)c.kap, (double*)c.fdt, *c.g, dt);
     else
         k_vk_init<float><<<(unsigned)blocks, 256, 0, c.stream>>>((float*)c.kap, (float*)c.fdt, *c.g, dt);
     HS_CHECK_LAUNCH("heat: kappa/source init kernel");
@@ -113,18 +212,30 @@ int vk_launch_t(const VkCall& c)
     const HeatGeom& g = *c.g;
     dim3 block(kVkBX, kVkBY, 1);
     const T bx = (T)c.bx, by = (T)c.by, bz = (T)c.bz;
+    constexpr bool kFaces = std::is_same<T, double>::value;
     if (c.part == 0) {
         if (g.nz < 3) return HS_OK;
         const int kbeg = 1, kend = g.nz - 1;
         const int nchunks = (kend - kbeg + c.kchunk - 1) / c.kchunk;
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, nchunks);
-        k_vk_interior<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
-                                                       (const T*)c.fdt, g, bx, by, bz, kbeg, kend, c.kchunk);
+        if constexpr (kFaces)
+            k_vk_interior_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                              (const double*)c.kap, (const double*)c.fdt, g,
+                                                              bx, by, bz, kbeg, kend, c.kchunk);
+        else
+            k_vk_interior<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
+                                                           (const T*)c.fdt, g, bx, by, bz, kbeg, kend,
+                                                           c.kchunk);
         HS_CHECK_LAUNCH("heat variable-kappa interior kernel");
     } else {
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, g.nz >= 2 ? 2 : 1);
-        k_vk_boundary<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
-                                                       (const T*)c.fdt, g, bx, by, bz);
+        if constexpr (kFaces)
+            k_vk_boundary_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                              (const double*)c.kap, (const double*)c.fdt, g,
+                                                              bx, by, bz);
+        else
+            k_vk_boundary<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
+                                                           (const T*)c.fdt, g, bx, by, bz);
         HS_CHECK_LAUNCH("heat variable-kappa boundary kernel");
     }
     return HS_OK;
