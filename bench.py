@@ -264,7 +264,7 @@ def paper_problem_side(pkg, stream, hbm_gbs, peak_kind):
         # FP32: u read and written, kappa, dt f (16 B)
         bpl = 48 if dtype == "f64" else 16
         kname = "k_vk_interior_faces + k_vk_boundary_faces" if dtype == "f64" else \
-            "k_vk_interior<float> + k_vk_boundary<float>"
+            "k_vk_interior_f4 + k_vk_boundary<float>"
         hbm = hbm_roofline(kname, lups * bpl, ms, hbm_gbs, peak_kind, bytes_per_lup=bpl)
         if dtype == "f64":
             rate = lups * VK_FP64_OPS_PER_LUP / (ms * 1e-3) / 1e12

@@ -40,8 +40,12 @@ def test_vk_without_initial_field_grows_from_the_source(pkg):
     assert np.all(u >= 0) and rel_max_err(u, ref) <= F64_REL
 
 
-def test_vk_f32_within_bound(pkg):
-    u0 = heat_u0_single_mode(48, 48, 48, seed=14)
+@pytest.mark.parametrize("shape", [(48, 48, 48), (9, 13, 37), (30, 7, 22), (5, 3, 1)])
+def test_vk_f32_within_bound(pkg, shape):
+    """FP32 (four x points per thread; 37, 22 and 1 wide leave ragged vectors)
+    against the FP64 oracle within the FP32 rounding bound."""
+    nz, ny, nx = shape
+    u0 = heat_u0_single_mode(nx, ny, nz, seed=14)
     ref = oracle.heat_vk_run(u0, R_PAPER, 100, threads=oracle.max_threads())
     got = run_vk(pkg, u0.astype(np.float32), R_PAPER, 100, dtype="f32")
     # each step adds at most ~24 float roundings of values <= max|u| + dt f
