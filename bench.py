@@ -46,9 +46,12 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (the measured copy ra
 # (two rows per thread, one point in four converted on the FP64 pipe) on 512^3
 # read 1187.2 MB and wrote 1025.9 MB per launch (mean of 2 launches); the FP32
 # blocked kernel at depth 2 (34-thread rows, plane loop unrolled by three) on
-# 512^3 read 626.5 MB and wrote 494.2 MB per pass (mean of 2 passes).
+# 512^3 read 626.5 MB and wrote 494.2 MB per pass (mean of 2 passes); the FIXED64
+# streaming kernel (plane loop unrolled by three) on 512^3 read 1149.5 MB and
+# wrote 1025.9 MB per launch (mean of 2 launches).
 # Re-capture after any change to that kernel; sizes not listed report null.
-KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2213105024, ("f32", 512, 2): 1120694016}
+KERNEL_TRAFFIC_BYTES = {("f64", 512, 1): 2213105024, ("f32", 512, 2): 1120694016,
+                        ("fixed64", 512, 1): 2175355904}
 HEAT_MODES = {
     # plain FP64 handle: FP64 fields, exact int64 neighbour sum, one FP64 FMA per point
     "f64": {"dtype": "f64", "flags": "", "arith": "f64", "bytes": 16, "bound": "hbm",
@@ -117,6 +120,9 @@ def parse_args():
                     help="skip the serving workload in the default run")
     ap.add_argument("--tdepth", type=int, default=0,
                     help="steps per pass of the timed heat handle (0: library choice)")
+    ap.add_argument("--paper-n", type=int, default=510,
+                    help="paper side: interior points per axis (510 = the paper's N = 512)")
+    ap.add_argument("--paper-steps", type=int, default=500, help="paper side: steps")
     ap.add_argument("--no-side", action="store_true",
                     help="skip every side measurement (same as --sides none)")
     ap.add_argument("--sides", default="all",
@@ -232,18 +238,19 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def paper_problem_side(pkg, stream, hbm_gbs, peak_kind):
+def paper_problem_side(pkg, stream, hbm_gbs, peak_kind, n=510, steps=500):
     """The paper's variable-coefficient problem at its N = 512 (510^3 interior
-    nodes, dt = h^2/(12 kappa_max)), 500 steps, FP64 and FP32.  The paper's
+    nodes, dt = h^2/(12 kappa_max)), 500 steps, FP64 and FP32 (n and steps:
+    another size, for small profiling runs).  The paper's
     measured k = 6.4042e-11 s per point-step for OpenMP offload on one H100
     (Table of used measurements) is 15.6 GLUP/s -- another GPU's number, for
     context."""
     import torch
 
     from workloads import heat_u0_single_mode
-    n, steps = 510, 500
     u0 = heat_u0_single_mode(n, n, n)
-    out = {"grid": "510^3 interior (paper N = 512)", "steps": steps, "r": 1.0 / (12 * 0.95),
+    out = {"grid": f"{n}^3 interior" + (" (paper N = 512)" if n == 510 else ""), "steps": steps,
+           "r": 1.0 / (12 * 0.95),
            "paper_h100_openmp_glups": 1.0 / 6.4042e-11 / 1e9}
     for dtype in ("f64", "f32"):
         src = torch.from_numpy(u0).cuda()
@@ -726,7 +733,8 @@ def run_ours(args):
 
     # ---- the paper's own problem: variable kappa, N = 512, 500 steps ---------------
     if "paper" in sides:
-        line["paper_problem"] = paper_problem_side(pkg, stream, hbm_gbs, peak_kind)
+        line["paper_problem"] = paper_problem_side(pkg, stream, hbm_gbs, peak_kind, args.paper_n,
+                                                   args.paper_steps)
 
     # ---- mixed-precision CG beside the FP64 solves (untimed region) ------------
     if "mixed" in sides:
