@@ -440,8 +440,11 @@ int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_it
  *   - A's arrays, b and x must be device memory (A->host == 0).
  *   - n > HS_NOALLOC_MAX_N is rejected with HS_EINVAL before any work.
  *   - The first call on a device does a one-time set-up on that device (it
- *     looks up the scratch array's device address); make that first call
- *     before any stream capture.
+ *     looks up the scratch array's device address and keeps it for the rest
+ *     of the process); make that first call before any stream capture.  The
+ *     kept address belongs to the device's current context: after
+ *     cudaDeviceReset on that device it is stale, so do not call
+ *     cg_solve_noalloc in a process that has reset the device.
  *   - Every call, on any stream, uses the same scratch array.  Calls whose
  *     work overlaps on the GPU race and corrupt each other's results:
  *     serialise them (one stream, or events between streams).  Each call

@@ -610,7 +610,9 @@ constexpr size_t kNoAllocDoubles =
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 // Device address of g_noalloc_scratch per device (host code may not use the
-// symbol itself: on the host it names a stand-in, not device memory).
+// symbol itself: on the host it names a stand-in, not device memory).  Looked
+// up once per device and kept for the process: it is not refreshed after a
+// cudaDeviceReset, which ends the context the address belongs to.
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_addr[kNoAllocMaxDevices];
