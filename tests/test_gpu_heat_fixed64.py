@@ -112,7 +112,7 @@ def test_errors(pkg):
 
 @pytest.mark.parametrize("tdepth", [1, 2, 3, 4])
 def test_temporal_depths_against_oracle(pkg, tdepth):
-    for shape in [(37, 29, 41), (40, 50, 150)]:   # the second holds unmasked interior blocks
+    for shape in [(37, 29, 41), (150, 50, 40)]:   # (nx, ny, nz); the second holds unmasked interior blocks
         u0 = heat_u0_single_mode(*shape, seed=6)
         ref = oracle.heat_run(u0, 0.13, 29)
         assert rel_max_err(run_fx(pkg, u0, 0.13, 29, tdepth=tdepth), ref) <= F64_REL

@@ -53,8 +53,11 @@ def test_blocked_equals_stepwise_bitwise(pkg, tdepth, shape, dtype):
 
 
 @pytest.mark.parametrize("tdepth", DEPTHS)
-def test_blocked_exact_rounding_equals_oracle_bitwise(pkg, tdepth):
-    u0 = heat_u0_single_mode(45, 38, 29, seed=12)
+@pytest.mark.parametrize("shape", [(45, 38, 29), (150, 50, 40)])
+def test_blocked_exact_rounding_equals_oracle_bitwise(pkg, tdepth, shape):
+    """One rounding per operation in the written order: the oracle bit for
+    bit (the 150-wide grid holds unmasked interior blocks)."""
+    u0 = heat_u0_single_mode(*shape, seed=12)
     ref = oracle.heat_run(u0, 0.1, 25)
     assert np.array_equal(run(pkg, u0, 0.1, 25, flags=pkg.HS_EXACT_ROUNDING, tdepth=tdepth), ref)
 
