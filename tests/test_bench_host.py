@@ -35,9 +35,21 @@ def test_hbm_roofline_object(bench):
 
 
 def test_roofline_traffic_is_null_where_not_captured(bench):
-    for mode, n in (("f32", 512), ("fixed64", 512), ("f64", 256)):
-        r = bench.interior_roofline(mode, n, 0.2, 6758.5, "measured", 1)
+    for mode, n, depth in (("f32", 512, 1), ("fixed64", 256, 1), ("f64", 256, 1), ("f32", 512, 3)):
+        r = bench.interior_roofline(mode, n, 0.2, 6758.5, "measured", depth)
         assert r["traffic"] is None and r["traffic_per_algorithmic"] is None
+
+
+def test_roofline_traffic_where_captured(bench):
+    """Captured kernels report their DRAM bytes per launch, within a few
+    percent above the algorithmic bytes (8 B per point per two-step FP32 pass
+    over all 512^3 points; 16 B per FIXED64 point of planes 1..510)."""
+    r = bench.interior_roofline("f32", 512, 0.27, 6758.5, "measured", 2)
+    assert r["traffic"] == bench.KERNEL_TRAFFIC_BYTES[("f32", 512, 2)]
+    assert 1.0 <= r["traffic_per_algorithmic"] < 1.06
+    r = bench.interior_roofline("fixed64", 512, 0.364, 6758.5, "measured", 1)
+    assert r["traffic"] == bench.KERNEL_TRAFFIC_BYTES[("fixed64", 512, 1)]
+    assert 1.0 <= r["traffic_per_algorithmic"] < 1.05
 
 
 def test_alu_roofline_object(bench):
