@@ -242,8 +242,8 @@ int heat_destroy(hs_heat_t h);
  * grid i by steps[i] steps of the update of Section 4, Eq. 4 -- the work of
  * the Interior and Boundary kernels of each step -- with the same per-point
  * arithmetic as heat_step, so the results match running each grid alone bit
- * for bit.  Work items are (step, grid, column tile of 64 x 8 or 32 x 16,
- * chunk of planes) taken from a device work counter; each item stages its planes in
+ * for bit.  Work items are (step, grid, column tile -- FP64 64 x 8 or 32 x 16,
+ * FP32 64 x 16 or 32 x 32 --, chunk of planes) taken from a device work counter; each item stages its planes in
  * shared memory (converted once in the exact-sum FP64 arithmetic); a grid's step starts once its previous step is complete, a wait
  * that is bounded (about a second), after which heat_batch_wait reports
  * HS_ETIMEOUT. */
@@ -258,7 +258,8 @@ int heat_batch_create(hs_batch_t* out, const hs_heat_t* grids, const int64_t* st
 /* heat_batch_create with the work split chosen per grid.  kz[i] >= 1 splits
  * each step of grid i into z-chunks of kz[i] planes (each chunk of each column
  * tile is one item); 0 leaves it to the library (chunks of 32 planes).
- * tile_w[i] is the column tile: 64 (64 x 8 columns), 32 (32 x 16) or 0 for the
+ * tile_w[i] is the column tile width: 64 (64 x 8 columns for FP64 grids,
+ * 64 x 16 for FP32), 32 (32 x 16, FP32 32 x 32) or 0 for the
  * library's choice (the one that stages fewer values per plane, so narrow
  * grids keep their warps busy).  Either array may be NULL (all 0).  The split
  * changes speed only: every point is computed the same way. */

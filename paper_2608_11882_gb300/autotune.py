@@ -4,7 +4,7 @@ For a single grid it chooses the temporal depth (steps per pass over HBM: 1 =
 the Interior + Boundary kernels every step, 2..4 = the temporally blocked
 kernel) together with the Interior kernel's planes per block (the library's
 choice, half of it or twice it); for a grid inside a batch it chooses the
-planes per work item and the column tile (64 x 8 or 32 x 16) of the
+planes per work item and the column tile width (64 or 32 columns) of the
 persistent batched kernel (or the library's choice of both).  Each candidate is
 timed on the actual device on a short sample of steps of a grid of the same
 shape and arithmetic; the fastest is cached in a JSON file keyed by GPU name,

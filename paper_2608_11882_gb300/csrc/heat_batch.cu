@@ -73,9 +73,10 @@ struct BatchDev {
 };
 
 // One work item of step m -- a column tile and a chunk [kb, ke) of its planes.
-// A block of 32 x 4 threads owns a 64 x 8 tile of the grid's columns and
-// marches up the chunk; every thread computes two consecutive x points in each
-// of two adjacent rows.  Each plane of the tile with its one-point halo
+// A block of 32 x 4 threads owns a TW x TY tile of the grid's columns and
+// marches up the chunk; every thread computes one 16-byte vector of
+// consecutive x points (two doubles or four floats) in each of two adjacent
+// rows.  Each plane of the tile with its one-point halo
 // ((8 + 2) rows of BW elements) arrives by TMA into a ring of kBatchNst stages
 // up to kBatchNst - 2 planes ahead of use, through a tensor map of the grid's
 // source buffer kept in the batch's device memory; the ring and its mbarrier
@@ -86,45 +87,34 @@ struct BatchDev {
 // and FP64-pipe planes are used as they are.  The per-point arithmetic is that
 // of heat_step, so every grid matches stepping it alone bit for bit.  Returns
 // false when a bounded wait ran out (the block then stops).
-// Tiles are TW x TY columns: 64 x 8 (a warp per two rows of 64 points) or,
-// for narrow grids, 32 x 16 (half a warp per two rows of 32 points).
+// Tiles are TW x TY columns, TW = 64 or, for narrow grids, 32: FP64 64 x 8 (a
+// warp per two rows of 64 points) or 32 x 16, FP32 64 x 16 or 32 x 32.
 constexpr int kBatchRT = 2, kBatchTY = 4;   // rows per thread, warps per block
 constexpr int kBatchNst = 4;
 constexpr int kBatchSlot = 688;   // stage stride in 8-byte words: the largest box, 5440 B, to 128 B
 
 template <typename T, int TW>
 struct BatchShape {
-    static constexpr int TY = TW == 64 ? 8 : 16;                 // tile rows
-    static constexpr int LPR = TW / 2;                           // lanes per tile row
+    static constexpr int V = Vec<T>::V;                          // points per thread row: 16 bytes
+    static constexpr int LPR = TW / V;                           // lanes per tile row
+    static constexpr int TY = kBatchTY * (32 / LPR) * kBatchRT;  // tile rows
     static constexpr int A = 16 / (int)sizeof(T);                // elements per 16 bytes
     static constexpr int D = A;                                  // offset of the tile's first point
     static constexpr int BW = (D + TW + 1 + A - 1) / A * A;      // stage row, a 16-byte multiple
     static constexpr uint32_t BOX_BYTES = (TY + 2) * BW * (uint32_t)sizeof(T);
-    static_assert(TY == kBatchTY * (32 / LPR) * kBatchRT, "the block covers the tile");
     static_assert(BOX_BYTES <= kBatchSlot * 8, "a box fits a stage");
 };
 
-template <typename T>
-__device__ __forceinline__ void st_pair(T* p, const T (&v)[2])
+// Tile rows and stage row width of a grid's tiles (host side).
+inline int batch_tile_rows(int tw, bool f32)
 {
-    if constexpr (sizeof(T) == 8)
-        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-    else
-        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    return f32 ? (tw == 64 ? BatchShape<float, 64>::TY : BatchShape<float, 32>::TY)
+               : (tw == 64 ? BatchShape<double, 64>::TY : BatchShape<double, 32>::TY);
 }
-
-template <typename T>
-__device__ __forceinline__ void ld_pair(const T* p, T (&v)[2])
+inline int batch_stage_row(int tw, bool f32)
 {
-    if constexpr (sizeof(T) == 8) {
-        const double2 q = *reinterpret_cast<const double2*>(p);
-        v[0] = q.x;
-        v[1] = q.y;
-    } else {
-        const float2 q = *reinterpret_cast<const float2*>(p);
-        v[0] = q.x;
-        v[1] = q.y;
-    }
+    return f32 ? (tw == 64 ? BatchShape<float, 64>::BW : BatchShape<float, 32>::BW)
+               : (tw == 64 ? BatchShape<double, 64>::BW : BatchShape<double, 32>::BW);
 }
 
 template <typename T, int KIND, int TW>
@@ -133,8 +123,9 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
                                            int* err)
 {
     using S = BatchShape<T, TW>;
-    constexpr int V = 2, RT = kBatchRT, BW = S::BW, NST = kBatchNst, TY = S::TY, LPR = S::LPR;
+    constexpr int V = S::V, RT = kBatchRT, BW = S::BW, NST = kBatchNst, TY = S::TY, LPR = S::LPR;
     constexpr bool CONV = KIND == K_F64_XS;
+    static_assert(!CONV || (V == 2 && 2 * TY <= 32), "the halo conversion roles below are FP64's");
     // stage words: fixed-point integers (exact-sum FP64), raw bits otherwise
     using Q = typename std::conditional<CONV, long long, T>::type;
     const HeatGeom& g = G.g;
@@ -172,15 +163,15 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
     auto convert = [&](Q* pl, Q (&q)[RT][V], T (&raw)[RT][V]) {
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
-            ld_pair(reinterpret_cast<const T*>(pl) + own + j * BW, raw[j]);
+            ld_vec(reinterpret_cast<const T*>(pl) + own + j * BW, raw[j]);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 if constexpr (CONV) q[j][i] = xs_fix(__double_as_longlong(raw[j][i]), emax);
                 else q[j][i] = raw[j][i];
             }
             if constexpr (CONV) {
-                pl[own + j * BW] = q[j][0];
-                pl[own + j * BW + 1] = q[j][1];
+#pragma unroll
+                for (int i = 0; i < V; ++i) pl[own + j * BW + i] = q[j][i];
             }
         }
         if constexpr (CONV) {
@@ -215,7 +206,7 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
 #pragma unroll
     for (int j = 0; j < RT; ++j) {
         T b[V];
-        ld_pair(reinterpret_cast<const T*>(slot(s_cur)) + own + j * BW, b);
+        ld_vec(reinterpret_cast<const T*>(slot(s_cur)) + own + j * BW, b);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             if constexpr (CONV) below[j][i] = xs_fix(__double_as_longlong(b[i]), emax);
@@ -239,10 +230,11 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
         convert(slot(s_nxt), above, araw);
         const Q* pl = slot(s_cur) + own;
         Q ym[V], yp[V];
-        ym[0] = pl[-BW];
-        ym[1] = pl[1 - BW];
-        yp[0] = pl[RT * BW];
-        yp[1] = pl[RT * BW + 1];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            ym[i] = pl[i - BW];
+            yp[i] = pl[RT * BW + i];
+        }
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
             const Q left = pl[j * BW - 1], right = pl[j * BW + V];
@@ -264,9 +256,11 @@ __device__ __forceinline__ bool batch_item(const BatchGrid& G, const CUtensorMap
             const int nvalid = Y0 + j < g.ny ? nx_ok : 0;
             T* o = out + j * g.pitch;
             if (nvalid == V) {
-                st_pair(o, v);
-            } else if (nvalid == 1) {
-                o[0] = v[0];
+                st_vec(o, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V - 1; ++i)
+                    if (i < nvalid) o[i] = v[i];
             }
             if constexpr (KIND == K_F64_XS || KIND == K_F64_XS_NATIVE) {
 #pragma unroll
@@ -399,11 +393,13 @@ int batch_default_kz(const HeatGeom& g, int)
 // Tile width when the caller leaves it to the library: the one that stages
 // fewer values per plane (tiles with their halo rows and columns), so narrow
 // grids do not leave half of every warp idle.
-int batch_default_tw(const HeatGeom& g)
+int batch_default_tw(const HeatGeom& g, bool f32)
 {
-    const int64_t c64 = (int64_t)((g.nx + 63) / 64) * ((g.ny + 7) / 8) * 68 * 10;
-    const int64_t c32 = (int64_t)((g.nx + 31) / 32) * ((g.ny + 15) / 16) * 36 * 18;
-    return c32 < c64 ? 32 : 64;
+    auto staged = [&](int tw) {
+        const int ty = batch_tile_rows(tw, f32);
+        return (int64_t)((g.nx + tw - 1) / tw) * ((g.ny + ty - 1) / ty) * batch_stage_row(tw, f32) * (ty + 2);
+    };
+    return staged(32) < staged(64) ? 32 : 64;
 }
 
 }  // namespace
@@ -476,10 +472,12 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
         G.m3 = 0;
         if (tw && tw[i] != 0 && tw[i] != 32 && tw[i] != 64)
             return fail(HS_EINVAL, "heat_batch_create: tile width %d of grid %d is not 0, 32 or 64", tw[i], i);
-        G.tw = (tw && tw[i]) ? tw[i] : batch_default_tw(v.g);
+        const bool f32 = G.kind == K_F32;
+        G.tw = (tw && tw[i]) ? tw[i] : batch_default_tw(v.g, f32);
         G.pad = 0;
         G.tiles_x = (v.g.nx + G.tw - 1) / G.tw;
-        G.tiles_xy = G.tiles_x * ((v.g.ny + (G.tw == 64 ? 8 : 16) - 1) / (G.tw == 64 ? 8 : 16));
+        const int tyr = batch_tile_rows(G.tw, f32);
+        G.tiles_xy = G.tiles_x * ((v.g.ny + tyr - 1) / tyr);
         if (kz && kz[i] < 0) return fail(HS_EINVAL, "heat_batch_create: kz[%d] < 0", i);
         G.kz = (kz && kz[i]) ? std::min(kz[i], v.g.nz) : batch_default_kz(v.g, G.tiles_xy);
         G.tiles = G.tiles_xy * ((v.g.nz + G.kz - 1) / G.kz);
@@ -540,9 +538,8 @@ int heat_batch_create_tiled(hs_batch_t* out, const hs_heat_t* grids, const int64
     for (int32_t i = 0; i < n; ++i) {
         const BatchGrid& G = hg[(size_t)i];
         const bool f32 = G.kind == K_F32;
-        const uint32_t bx = G.tw == 64 ? (f32 ? BatchShape<float, 64>::BW : BatchShape<double, 64>::BW)
-                                       : (f32 ? BatchShape<float, 32>::BW : BatchShape<double, 32>::BW);
-        const uint32_t by = (G.tw == 64 ? BatchShape<double, 64>::TY : BatchShape<double, 32>::TY) + 2;
+        const uint32_t bx = (uint32_t)batch_stage_row(G.tw, f32);
+        const uint32_t by = (uint32_t)batch_tile_rows(G.tw, f32) + 2;
         for (int bi = 0; bi < 2; ++bi) {
             const int e = encode_field_map(&maps[2 * (size_t)i + bi], G.buf[bi],
                                            f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
