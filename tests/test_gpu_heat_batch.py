@@ -173,3 +173,27 @@ def test_tuned_batch_equals_alone(pkg, tmp_path, monkeypatch):
     for s, h in zip(specs, heats):
         assert np.array_equal(h.read(), alone(pkg, s, s["steps"]))
         h.close()
+
+
+def test_batch_with_blocked_handles_then_heat_step(pkg):
+    """Handles at their default depth (FP32: two steps per pass) join a batch,
+    which steps them one step per item; heat_step then continues them in
+    blocked passes from the buffer the batch left current.  FP32 results equal
+    one-step stepping bit for bit at every depth; the plain FP64 handle (exact
+    sum at depth 1) equals itself stepped alone."""
+    specs = draw_batch(4, seed=31, edge=(20, 90), steps=(5, 9))
+    heats = []
+    for s in specs:
+        nz, ny, nx = s["shape"]
+        h = pkg.Heat(nx, ny, nz, s["r"], dtype=s["dtype"])
+        assert h.tdepth == (2 if s["dtype"] == "f32" else 1)
+        h.upload(s["u0"].astype(h.np_dtype))
+        heats.append(h)
+    with pkg.HeatBatch(heats, [s["steps"] for s in specs]) as b:
+        b.run(use_graph=False)
+        b.wait()
+    for s, h in zip(specs, heats):
+        h.step(5)
+        assert h.steps_done == s["steps"] + 5
+        assert np.array_equal(h.read(), alone(pkg, s, s["steps"] + 5)), s["shape"]
+        h.close()
