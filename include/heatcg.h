@@ -162,9 +162,12 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes);
  * copies u_old and u_new alike, Algorithm "1-GPU Baseline"; here the spare
  * buffer needs no copy: its boundary layer is zero from creation and the next
  * step writes every interior value of it before any is read.)  u is host memory
- * if src_is_device == 0 (one strided copy; pinned host memory makes it
- * asynchronous), device memory otherwise (a re-layout kernel).  Enqueued on
- * the handle's stream. */
+ * if src_is_device == 0, device memory otherwise.  Device memory and pinned,
+ * mapped host memory (cudaHostAlloc, cudaMallocHost, cudaHostRegister; pinned
+ * torch tensors) are read by a re-layout kernel, the latter through its mapped
+ * device address, so the call returns at once; pageable host memory goes
+ * through one strided copy.  Enqueued on the handle's stream; a pinned source
+ * must stay unchanged until the stream has passed the upload. */
 int heat_upload(hs_heat_t h, const void* u, int src_is_device);
 
 /* Advance n_steps >= 0 steps.  With tdepth 1 each step runs the Boundary
@@ -209,9 +212,11 @@ int heat_interior_time(hs_heat_t h, double* mean_ms, int64_t* launches);
 
 /* Copy the current interior field to dst (Algorithm "1-GPU Baseline", the
  * device-to-host copy of the result after the time loop; nx*ny*nz elements, x fastest):
- * host memory if dst_is_device == 0 (one strided copy), device memory
- * otherwise (a re-layout kernel).  Synchronises the handle's stream and
- * reports any asynchronous error. */
+ * host memory if dst_is_device == 0, device memory otherwise.  Device memory
+ * and pinned, mapped host memory are written by a re-layout kernel (host
+ * memory through its mapped device address); pageable host memory by one
+ * strided copy.  Synchronises the handle's stream and reports any
+ * asynchronous error. */
 int heat_read(hs_heat_t h, void* dst, int dst_is_device);
 
 /* Steps applied since the last heat_upload. */
@@ -369,7 +374,9 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
  * x += alpha p, r -= alpha q, rho' = r.r, stop when sqrt(rho')/||b|| <= rtol,
  * else p = r + (rho'/rho) p.  x holds x0 on entry (zeros allowed) and the
  * last iterate on exit.  b and x are host arrays if host_buffers != 0 (copied
- * in and out on the context's stream), device arrays otherwise.  Dot products
+ * in and out on the context's stream: by a copy kernel through the mapped
+ * address when they are pinned, mapped host memory, else by cudaMemcpyAsync),
+ * device arrays otherwise.  Dot products
  * accumulate in FP64 in a fixed order, so repeated runs agree bit for bit.
  * For the matrix-free operator the SpMV forms 6p - (sum of the neighbours)
  * exactly in 64-bit fixed point on p's current scale (its largest exponent,

@@ -557,10 +557,9 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
         for (int t = 0; t < 2; ++t)
             if (!c->bx_dev[t])
                 HS_TRY_CUDA(dev_alloc((void**)&c->bx_dev[t], vbytes, c->stream), "cg_run: staging buffer");
-        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[0], b_in, vbytes, cudaMemcpyHostToDevice, c->stream),
-                    "cg_run: copy of b");
-        HS_TRY_CUDA(cudaMemcpyAsync(c->bx_dev[1], x_inout, vbytes, cudaMemcpyHostToDevice, c->stream),
-                    "cg_run: copy of x0");
+        int rc_ = copy_host(c->bx_dev[0], b_in, vbytes, true, c->stream, "cg_run: copy of b");
+        if (rc_ == HS_OK) rc_ = copy_host(c->bx_dev[1], x_inout, vbytes, true, c->stream, "cg_run: copy of x0");
+        if (rc_ != HS_OK) return rc_;
         b = c->bx_dev[0];
         x = c->bx_dev[1];
     }
@@ -646,9 +645,10 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
         ++outer;
     }
     if (m->S_host->zero_rhs) HS_TRY_CUDA(cudaMemsetAsync(x, 0, vbytes, c->stream), "cg_run: zero solution");
-    if (host_buffers)
-        HS_TRY_CUDA(cudaMemcpyAsync(x_inout, x, vbytes, cudaMemcpyDeviceToHost, c->stream),
-                    "cg_run: copy of x");
+    if (host_buffers) {
+        const int rc_ = copy_host(x_inout, x, vbytes, false, c->stream, "cg_run: copy of x");
+        if (rc_ != HS_OK) return rc_;
+    }
     HS_TRY_CUDA(cudaStreamSynchronize(c->stream), "cg_run: synchronize");
     if (breakdown) return fail(HS_ECUDA, "cg_run: breakdown in the FP32 inner solve");
     const MxScalars f = *m->S_host;   // from the last residual evaluation

@@ -43,6 +43,14 @@ namespace hcg {
 
 constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
+// The device address of pinned, mapped host memory, or nullptr for any other
+// pointer (pageable host memory in particular) -- api.cu.
+void* mapped_host_ptr(const void* p);
+// bytes between host memory and device memory, enqueued on s: a copy kernel
+// through the mapped address when the host side is pinned and mapped, else
+// cudaMemcpyAsync -- api.cu.
+int copy_host(void* dst, const void* src, size_t bytes, bool to_device, cudaStream_t s, const char* what);
+
 // Device memory of handles and contexts comes from the stream-ordered
 // allocator on the object's own stream: unlike cudaMalloc/cudaFree these calls
 // never synchronise the whole device, so creating or releasing one object does

@@ -947,10 +947,13 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
     // interior value of it is written by the next step before it is read, and
     // its boundary layer has been zero since creation -- the same state the
     // paper reaches by uploading u_old and u_new alike.
-    // device sources are re-laid out by a kernel at HBM speed; host sources
+    // device sources and pinned, mapped host sources are re-laid out by a
+    // kernel (the latter reading host memory directly); pageable host sources
     // go through one strided 3-D copy (measured faster over the host link than
     // a contiguous copy into a staging buffer plus the re-layout)
+    const void* mapped = src_is_device ? nullptr : mapped_host_ptr(u);
     int rc = src_is_device ? interior_copy(h, u, h->buf[0], true)
+             : mapped      ? interior_copy(h, mapped, h->buf[0], true)
                            : copy_interior(h, h->buf[0], u, nullptr, cudaMemcpyHostToDevice);
     if (rc != HS_OK) return rc;
     if (h->arith == A_FX64) {
@@ -1084,8 +1087,11 @@ int heat_read(hs_heat_t h, void* dst, int dst_is_device)
         HS_CHECK_LAUNCH("heat_read: fixed-point decode kernel");
         src = spare;
     }
-    // device destinations by a kernel, host ones by one strided 3-D copy
+    // device and pinned, mapped host destinations by a kernel, pageable host
+    // ones by one strided 3-D copy
+    void* mapped = dst_is_device ? nullptr : mapped_host_ptr(dst);
     int rc = dst_is_device ? interior_copy(h, src, dst, false)
+             : mapped      ? interior_copy(h, src, mapped, false)
                            : copy_interior(h, src, nullptr, dst, cudaMemcpyDeviceToHost);
     if (rc != HS_OK) return rc;
     // status reads on the handle's own stream (a legacy-stream copy would also

@@ -76,6 +76,26 @@ def test_cg_is_deterministic_and_host_path_matches(pkg):
     assert i1 == i2 and i1["iters"] == i3["iters"]
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_pinned_host_vectors(pkg, mixed):
+    """Pinned host tensors for b and x (copied by a kernel through their
+    mapped address) give the solve of device vectors bit for bit, in FP64 and
+    in mixed precision; a start vector in x is read too."""
+    torch = require_cuda()
+    nz, ny, nx = 21, 17, 14
+    n = nx * ny * nz
+    b = cg_rhs(n, seed=13)
+    op = pkg.Operator.stencil(nx, ny, nz)
+    x0 = np.random.default_rng(14).uniform(-1, 1, n)
+    with pkg.CG(op, mixed=mixed) as cg:
+        xd, idev = cg.run(dev(b), dev(x0), rtol=1e-10, max_iter=3000)
+        bp = torch.from_numpy(b.copy()).pin_memory()
+        xp = torch.from_numpy(x0.copy()).pin_memory()
+        _, ipin = cg.run(bp, xp, rtol=1e-10, max_iter=3000)
+    assert np.array_equal(xp.numpy(), xd.cpu().numpy())
+    assert idev["iters"] == ipin["iters"] and idev["relres_true"] == ipin["relres_true"]
+
+
 def test_cg_eigenvector_one_iteration(pkg):
     nz, ny, nx = 7, 5, 6
     xs, ys, zs = [(np.arange(m) + 1) / (m + 1) for m in (nx, ny, nz)]

@@ -85,6 +85,31 @@ def test_zero_steps_and_device_upload(pkg):
         assert np.array_equal(out.cpu().numpy().reshape(u0.shape), u0)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(9, 7, 13), (12, 10, 64), (3, 5, 1)])
+def test_pinned_host_buffers(pkg, dtype, shape):
+    """Pinned host tensors are read and written by the re-layout kernel
+    through their mapped device address (pageable arrays by a strided copy):
+    the same field either way, rows whose bytes are or are not a multiple of
+    16 alike, and after steps the same result as the pageable path."""
+    torch = require_cuda()
+    nz, ny, nx = shape
+    u0 = heat_u0_single_mode(nx, ny, nz, seed=17)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    pinned = torch.from_numpy(u0).to(tdt).pin_memory()
+    back = torch.empty_like(pinned).pin_memory()
+    with pkg.Heat(nx, ny, nz, 0.12, dtype=dtype) as h:
+        h.upload(pinned)
+        h.read(back)
+        assert np.array_equal(back.numpy(), pinned.numpy())
+        h.step(7)
+        h.read(back)
+        pageable = h.read()
+    assert np.array_equal(back.numpy(), pageable)
+    with pkg.Heat(nx, ny, nz, 0.12, dtype=dtype) as h:
+        assert np.array_equal(h.upload(pinned.numpy().copy()).step(7).read(), pageable)
+
+
 def test_resume_from_snapshot_is_bitwise(pkg):
     u0 = heat_u0_single_mode(30, 20, 25, seed=8)
     straight = run_gpu(pkg, u0, 0.1, 50)
