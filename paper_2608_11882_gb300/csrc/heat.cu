@@ -538,6 +538,8 @@ int vk_part(hs_heat* h, Part p, cudaStream_t s)
     c.bz = h->vbz;
     c.kchunk = h->kchunk;
     c.stream = s;
+    c.fx = h->fx;   // FP64 cubic grids only
+    c.m3 = (int)(h->fxseq % 3);
     return vk_launch(c);
 }
 
@@ -781,7 +783,8 @@ int heat_device_bytes(const hs_heat_desc* desc, size_t* bytes)
     const Arith a = pick_arith(desc);
     if (a == A_FX64 || a == A_F64_XS) *bytes += sizeof(FxState);
     if (desc->flags & HS_VARKAPPA)   // coefficients (FP64: three face arrays) and dt f
-        *bytes += (desc->dtype == HS_F64 ? 4 : 2) * (size_t)g.total * elem_size(desc->dtype);
+        *bytes += (desc->dtype == HS_F64 ? 4 : 2) * (size_t)g.total * elem_size(desc->dtype) +
+                  (desc->dtype == HS_F64 ? sizeof(FxState) : 0);
     return HS_OK;
 }
 
@@ -922,6 +925,17 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             heat_destroy(h);
             return rc;
         }
+        // FP64 on a cubic grid (one beta for every axis): the exact-sum form,
+        // which tracks the field's largest exponent step by step
+        if (h->dtype == HS_F64 && h->vbx == h->vby && h->vby == h->vbz) {
+            e = dev_alloc((void**)&h->fx, sizeof(FxState), h->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "heat_create: exact-sum state");
+                heat_destroy(h);
+                return rc;
+            }
+        }
     }
     // A Boundary kernel beside the Interior one pays for its extra API calls
     // once the Interior kernel takes tens of microseconds (2^22 points and up).
@@ -963,7 +977,7 @@ int heat_upload(hs_heat_t h, const void* u, int src_is_device)
         HS_CHECK_LAUNCH("heat_upload: max|u| kernel");
         k_fx_encode<<<blocks, 256, 0, h->stream>>>((double*)h->buf[0], h->g, h->fx);
         HS_CHECK_LAUNCH("heat_upload: fixed-point encode kernel");
-    } else if (h->arith == A_F64_XS) {
+    } else if (h->arith == A_F64_XS || (h->fx && (h->flags & HS_VARKAPPA))) {
         // slot 0: the largest |u| bit pattern of the uploaded field
         HS_TRY_CUDA(cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream), "heat_upload: memset");
         k_fx_maxabs<<<conv_blocks(h->g), 256, 0, h->stream>>>((const double*)h->buf[0], h->g, h->fx);

@@ -321,6 +321,9 @@ struct VkCall {
     double bx, by, bz;       // dt / (2 h_d^2)
     int kchunk;
     cudaStream_t stream;
+    FxState* fx;             // FP64 cubic grids: the per-step maxima of the exact-sum form
+                             // (nullptr: the FP64 form, no maxima)
+    int m3;                  // slot of the current field in fx
 };
 int vk_init(const VkCall& c, double dt);
 int vk_launch(const VkCall& c);

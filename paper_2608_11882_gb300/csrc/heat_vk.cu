@@ -10,11 +10,15 @@
 //
 // FP32 keeps kappa on every node of the padded box (16 bytes per update:
 // the kernel is bound by HBM, where three face arrays would cost more than the
-// six additions they save).  FP64 is bound by the FP64 pipe, so it keeps the
-// three face sums k[i+1] + k[i] of each node instead (constant in time, formed
-// once at creation, bit for bit the sums the formula forms every step) and
-// carries the z difference u[k+1] - u[k] to the next plane: 16 FP64
-// instructions per update instead of 23, at 48 bytes per update.
+// six additions they save).  FP64 keeps the three face sums k[i+1] + k[i] of
+// each node instead (constant in time, formed once at creation, bit for bit
+// the sums the formula forms every step), 48 bytes per update.  On a cubic
+// grid (one beta for every axis: the paper's case) the FP64 update forms the
+// operator sum exactly in 128-bit integers on the field's fixed-point scale
+// and rounds it once, 2 FP64 instructions per update; other grids (and fields
+// outside the exact form's exponent range) use the FP64 form, 16 FP64
+// instructions per update with the z difference u[k+1] - u[k] carried to the
+// next plane (23 with kappa itself).
 #include <cmath>
 
 #include "heat_common.cuh"
@@ -136,6 +140,154 @@ __global__ void __launch_bounds__(kVkBX* kVkBY)
                             __dsub_rn(__ldg(src + c + P), uc), __dsub_rn(uc, __ldg(src + c - P)),
                             __ldg(fx + c - 1), __ldg(fx + c), __ldg(fy + c - Y), __ldg(fy + c),
                             __ldg(fz + c - P), __ldg(fz + c), __ldg(fdt + c), bx, by, bz);
+}
+
+// ---- FP64, exact sum (cubic grids: one beta for every axis) ----------------
+// The operator sum D = sum_d [c_d+ (u_d+ - u) - c_d- (u - u_d-)] on the field's
+// fixed-point scale: U the exact-sum integers of the u values (xsum.cuh, the
+// scale 2^(1080 - e) of the field's largest exponent field e, tracked per step
+// in the handle's FxState like the default FP64 arithmetic's), C the face
+// sums' 53-bit significands (every face sum of kappa = 0.5 + 0.45 s, s in
+// [0, 1], lies in [1, 2), so C = c 2^52 exactly), each product C dU exact and
+// their sum exact in 128 bits, rounded once to FP64; then
+// u' = fma(beta, D, u + dt f).  Two FP64 instructions per update instead of
+// sixteen; the error against the same formula in exact arithmetic is below
+// 6 * 2 * 1.9 * 4 * 2^-57 max|u| beta plus three roundings.  Fields whose
+// exponent lies outside [kVkEmaxLo, kVkEmaxHi] (all-zero or tiny fields,
+// values near overflow, NaN, Inf) take the FP64 form of vk_point_faces.
+constexpr int kVkEmaxLo = 120, kVkEmaxHi = 2030;
+
+__device__ __forceinline__ unsigned long long vk_face_sig(double c)
+{
+    // significand of c in [1, 2), its implicit bit included
+    return ((unsigned long long)__double_as_longlong(c) & 0x000fffffffffffffull) | 0x0010000000000000ull;
+}
+
+__device__ __forceinline__ bool vk_exact_ok(int emax) { return emax >= kVkEmaxLo && emax <= kVkEmaxHi; }
+
+// One update on the exact path from the seven u values (as doubles, the centre
+// also as its integer), the six face sums and dt f.
+__device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long long Uxm, long long Uxp,
+                                                 long long Uym, long long Uyp, long long dzp, long long dzm,
+                                                 double cxm, double cxp, double cym, double cyp, double czm,
+                                                 double czp, double f, double beta, int emax)
+{
+    I128 acc{0ull, 0ll};
+    i128_mac(acc, vk_face_sig(cxp), Uxp - Uc);
+    i128_mac(acc, vk_face_sig(cxm), Uxm - Uc);
+    i128_mac(acc, vk_face_sig(cyp), Uyp - Uc);
+    i128_mac(acc, vk_face_sig(cym), Uym - Uc);
+    i128_mac(acc, vk_face_sig(czp), dzp);
+    i128_mac(acc, vk_face_sig(czm), -dzm);
+    // C dU carries the scale 2^52 2^(1080 - e)
+    const double D = i128_to_double(acc, emax - 1132);
+    return __fma_rn(beta, D, __dadd_rn(uc, f));
+}
+
+// Interior (planes kbeg..kend-1) of a cubic FP64 grid: the exact sum while the
+// field's exponent allows it, the FP64 form otherwise; every output joins the
+// step's maximum (slot (m3 + 1) % 3).
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_interior_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
+                     const double* __restrict__ fdt, HeatGeom g, double beta, int kbeg, int kend, int kchunk,
+                     FxState* fx, int m3)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    const int k0 = kbeg + (int)blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, kend);
+    const int emax = xs_emax(fx, m3);
+    unsigned mx = 0;
+    if (i < g.nx && j < g.ny && k0 < k1) {
+        const int64_t P = g.plane, Y = g.pitch;
+        const double* fxs = fc;
+        const double* fys = fc + g.total;
+        const double* fzs = fc + 2 * g.total;
+        int64_t c = g.at(i, j, k0);
+        if (vk_exact_ok(emax)) {
+            auto fix = [emax](double v) { return xs_fix(__double_as_longlong(v), emax); };
+            double uc = __ldg(src + c);
+            long long Uc = fix(uc);
+            long long dzm = Uc - fix(__ldg(src + c - P));
+            double czm = __ldg(fzs + c - P);
+            for (int k = k0; k < k1; ++k) {
+                const double ua = __ldg(src + c + P), cza = __ldg(fzs + c);
+                const long long Ua = fix(ua);
+                const long long dzp = Ua - Uc;
+                const double v = vk_point_exact(uc, Uc, fix(__ldg(src + c - 1)), fix(__ldg(src + c + 1)),
+                                                fix(__ldg(src + c - Y)), fix(__ldg(src + c + Y)), dzp, dzm,
+                                                __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y),
+                                                __ldg(fys + c), czm, cza, __ldg(fdt + c), beta, emax);
+                dst[c] = v;
+                const unsigned a = xs_abs_hi(v);
+                mx = a > mx ? a : mx;
+                uc = ua;
+                Uc = Ua;
+                dzm = dzp;
+                czm = cza;
+                c += P;
+            }
+        } else {
+            double uc = __ldg(src + c);
+            double dzm = __dsub_rn(uc, __ldg(src + c - P));
+            double czm = __ldg(fzs + c - P);
+            for (int k = k0; k < k1; ++k) {
+                const double ua = __ldg(src + c + P), cza = __ldg(fzs + c);
+                const double dzp = __dsub_rn(ua, uc);
+                const double v = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y),
+                                                __ldg(src + c + Y), dzp, dzm, __ldg(fxs + c - 1), __ldg(fxs + c),
+                                                __ldg(fys + c - Y), __ldg(fys + c), czm, cza, __ldg(fdt + c),
+                                                beta, beta, beta);
+                dst[c] = v;
+                const unsigned a = xs_abs_hi(v);
+                mx = a > mx ? a : mx;
+                uc = ua;
+                dzm = dzp;
+                czm = cza;
+                c += P;
+            }
+        }
+    }
+    fx_finish<kVkBX * kVkBY>((unsigned long long)mx << 32, fx, m3, 0,
+                             blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+}
+
+// Boundary planes 0 and nz-1 of a cubic FP64 grid, as k_vk_interior_xs.
+__global__ void __launch_bounds__(kVkBX* kVkBY)
+    k_vk_boundary_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
+                     const double* __restrict__ fdt, HeatGeom g, double beta, FxState* fx, int m3)
+{
+    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int j = blockIdx.y * kVkBY + threadIdx.y;
+    const int emax = xs_emax(fx, m3);
+    unsigned mx = 0;
+    if (i < g.nx && j < g.ny) {
+        const int k = (blockIdx.z == 0) ? 0 : g.nz - 1;
+        const int64_t P = g.plane, Y = g.pitch;
+        const int64_t c = g.at(i, j, k);
+        const double* fxs = fc;
+        const double* fys = fc + g.total;
+        const double* fzs = fc + 2 * g.total;
+        const double uc = __ldg(src + c);
+        double v;
+        if (vk_exact_ok(emax)) {
+            auto fix = [emax](double w) { return xs_fix(__double_as_longlong(w), emax); };
+            const long long Uc = fix(uc);
+            v = vk_point_exact(uc, Uc, fix(__ldg(src + c - 1)), fix(__ldg(src + c + 1)), fix(__ldg(src + c - Y)),
+                               fix(__ldg(src + c + Y)), fix(__ldg(src + c + P)) - Uc, Uc - fix(__ldg(src + c - P)),
+                               __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y), __ldg(fys + c),
+                               __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), beta, emax);
+        } else {
+            v = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y), __ldg(src + c + Y),
+                               __dsub_rn(__ldg(src + c + P), uc), __dsub_rn(uc, __ldg(src + c - P)),
+                               __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y), __ldg(fys + c),
+                               __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), beta, beta, beta);
+        }
+        dst[c] = v;
+        mx = xs_abs_hi(v);
+    }
+    fx_finish<kVkBX * kVkBY>((unsigned long long)mx << 32, fx, m3, 0,
+                             blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
 template <typename T>
@@ -267,10 +419,16 @@ int vk_launch_t(const VkCall& c)
         const int kbeg = 1, kend = g.nz - 1;
         const int nchunks = (kend - kbeg + c.kchunk - 1) / c.kchunk;
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, nchunks);
-        if constexpr (kFaces)
-            k_vk_interior_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
-                                                              (const double*)c.kap, (const double*)c.fdt, g,
-                                                              bx, by, bz, kbeg, kend, c.kchunk);
+        if constexpr (kFaces) {
+            if (c.fx)
+                k_vk_interior_xs<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                               (const double*)c.kap, (const double*)c.fdt, g,
+                                                               bx, kbeg, kend, c.kchunk, c.fx, c.m3);
+            else
+                k_vk_interior_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                                  (const double*)c.kap, (const double*)c.fdt, g,
+                                                                  bx, by, bz, kbeg, kend, c.kchunk);
+        }
         else {
             dim3 grid4((g.nx + 4 * kVkBX - 1) / (4 * kVkBX), grid.y, grid.z);
             k_vk_interior_f4<<<grid4, block, 0, c.stream>>>((const float*)c.src, (float*)c.dst,
@@ -281,10 +439,16 @@ int vk_launch_t(const VkCall& c)
         HS_CHECK_LAUNCH("heat variable-kappa interior kernel");
     } else {
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, g.nz >= 2 ? 2 : 1);
-        if constexpr (kFaces)
-            k_vk_boundary_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
-                                                              (const double*)c.kap, (const double*)c.fdt, g,
-                                                              bx, by, bz);
+        if constexpr (kFaces) {
+            if (c.fx)
+                k_vk_boundary_xs<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                               (const double*)c.kap, (const double*)c.fdt, g,
+                                                               bx, c.fx, c.m3);
+            else
+                k_vk_boundary_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                                  (const double*)c.kap, (const double*)c.fdt, g,
+                                                                  bx, by, bz);
+        }
         else
             k_vk_boundary<T><<<grid, block, 0, c.stream>>>((const T*)c.src, (T*)c.dst, (const T*)c.kap,
                                                            (const T*)c.fdt, g, bx, by, bz);

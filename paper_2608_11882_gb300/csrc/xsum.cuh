@@ -100,6 +100,59 @@ __device__ __forceinline__ double xs_apply(double uc, long long L, double r, dou
     return __fma_rn(r, xs_unfix(L, emax), uc);
 }
 
+// ---- exact weighted sums: 128-bit accumulation ---------------------------
+// A sum of products C d, C < 2^53 an integer weight and d a difference of two
+// fixed-point values (|d| < 2^60), is exact in a 128-bit two's-complement
+// accumulator (hi:lo) for up to 2^14 terms; it is rounded once to FP64 by
+// i128_to_double.
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+// a += C d, exactly.
+__device__ __forceinline__ void i128_mac(I128& a, unsigned long long C, long long d)
+{
+    const unsigned long long plo = (unsigned long long)d * C;   // the low 64 bits, signed or not
+    const long long phi = __mul64hi(d, (long long)C);          // the signed high 64 bits (C < 2^63)
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(plo), "l"(phi));
+}
+
+// (hi:lo) 2^s rounded to the nearest double, ties to even.  The caller keeps
+// |hi:lo| < 2^120 and s such that every nonzero result is a normal number.
+__device__ __forceinline__ double i128_to_double(I128 a, int s)
+{
+    const unsigned long long sign = (unsigned long long)(a.hi >> 63);
+    unsigned long long mlo, mhi;   // |hi:lo|
+    if (sign) {
+        mlo = 0ull - a.lo;
+        mhi = ~(unsigned long long)a.hi + (a.lo == 0ull ? 1ull : 0ull);
+    } else {
+        mlo = a.lo;
+        mhi = (unsigned long long)a.hi;
+    }
+    if ((mhi | mlo) == 0ull) return 0.0;
+    const int lz = mhi ? __clzll((long long)mhi) : 64 + __clzll((long long)mlo);   // >= 8
+    // the magnitude shifted left by lz - 1: its leading one at bit 126, so the
+    // top 64 bits n hold it at bit 62; the bits below join n's bit 0 (sticky)
+    const int t = lz - 1;
+    unsigned long long n, rest;
+    if (t >= 64) {
+        n = mlo << (t - 64);
+        rest = 0ull;
+    } else {
+        n = (mhi << t) | (mlo >> (64 - t));   // t >= 7, so 64 - t < 64
+        rest = mlo << t;
+    }
+    n |= rest != 0ull ? 1ull : 0ull;
+    const unsigned long long q = (n + 0x1ffull + ((n >> 10) & 1ull)) >> 10;   // 2^52 <= q <= 2^53
+    // the leading one is bit p = 127 - lz of the magnitude: biased exponent
+    // p + s + 1023; q's bit 52 (or a carry to 53) adds into the exponent field
+    const long long e1 = (long long)(127 - lz + s + 1022);
+    const unsigned long long bits = ((unsigned long long)e1 << 52) + q + (sign << 63);
+    return __longlong_as_double((long long)bits);
+}
+
 // |u| of a result as the high word of its bit pattern (the exponent field and
 // the top of the mantissa): what the per-step maximum needs.
 __device__ __forceinline__ unsigned xs_abs_hi(double v)

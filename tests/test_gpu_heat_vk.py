@@ -53,6 +53,35 @@ def test_vk_f32_within_bound(pkg, shape):
     assert float(np.max(np.abs(got - ref))) <= bound
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-250, 1e250, 1e-300])
+def test_vk_f64_cubic_exact_sum_against_oracle(pkg, scale):
+    """Cubic FP64 grids take the exact-sum form (the operator sum exact in 128
+    bits on the field's fixed-point scale, rounded once) while the field's
+    exponent allows; 1e-300 starts on the FP64 form and the source lifts the
+    field into range within a step, 1e-250 and 1e250 run exact throughout."""
+    n = 33
+    u0 = heat_u0_single_mode(n, n, n, seed=16) * scale
+    ref = oracle.heat_vk_run(u0, R_PAPER, 40, threads=oracle.max_threads())
+    assert rel_max_err(run_vk(pkg, u0, R_PAPER, 40), ref) <= F64_REL
+
+
+def test_vk_f64_cubic_from_zero_field(pkg):
+    u = run_vk(pkg, np.zeros((24, 24, 24)), R_PAPER, 30)
+    ref = oracle.heat_vk_run(np.zeros((24, 24, 24)), R_PAPER, 30)
+    assert np.all(u >= 0) and rel_max_err(u, ref) <= F64_REL
+
+
+def test_vk_f64_cubic_tight_against_oracle(pkg):
+    """The exact-sum form rounds the operator sum once per point, so after 50
+    steps at 40^3 it stays within 1e-13 of the oracle (relative to max|u|),
+    ten times inside the FP64 gate."""
+    n = 40
+    u0 = heat_u0_single_mode(n, n, n, seed=18)
+    ref = oracle.heat_vk_run(u0, R_PAPER, 50, threads=oracle.max_threads())
+    got = run_vk(pkg, u0, R_PAPER, 50)
+    assert rel_max_err(got, ref) <= 1e-13
+
+
 def test_vk_errors(pkg):
     from paper_2608_11882_gb300._native import HS_EINVAL, HS_EUNSTABLE
     with pytest.raises(pkg.HeatCGError) as e:
