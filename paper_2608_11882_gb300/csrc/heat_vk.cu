@@ -186,65 +186,108 @@ __device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long l
 
 // Interior (planes kbeg..kend-1) of a cubic FP64 grid: the exact sum while the
 // field's exponent allows it, the FP64 form otherwise; every output joins the
-// step's maximum (slot (m3 + 1) % 3).
-__global__ void __launch_bounds__(kVkBX* kVkBY)
+// step's maximum (slot (m3 + 1) % 3).  Every thread takes two consecutive x
+// points (16-byte loads of u, the face sums and dt f): four conversions per
+// point and half the load instructions of one point per thread, whose loads
+// left the kernel waiting on memory (57 against 77 GLUP/s at 510^3; three
+// blocks per SM at 79 registers).  A thread whose second point is the
+// boundary node nx computes only the first.
+__global__ void __launch_bounds__(kVkBX* kVkBY, 3)
     k_vk_interior_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
-                     const double* __restrict__ fdt, HeatGeom g, double beta, int kbeg, int kend, int kchunk,
-                     FxState* fx, int m3)
+                      const double* __restrict__ fdt, HeatGeom g, double beta, int kbeg, int kend, int kchunk,
+                      FxState* fx, int m3)
 {
-    const int i = blockIdx.x * kVkBX + threadIdx.x;
+    const int i0 = (blockIdx.x * kVkBX + threadIdx.x) * 2;
     const int j = blockIdx.y * kVkBY + threadIdx.y;
     const int k0 = kbeg + (int)blockIdx.z * kchunk;
     const int k1 = min(k0 + kchunk, kend);
     const int emax = xs_emax(fx, m3);
     unsigned mx = 0;
-    if (i < g.nx && j < g.ny && k0 < k1) {
+    if (i0 < g.nx && j < g.ny && k0 < k1) {
+        const bool two = i0 + 1 < g.nx;
         const int64_t P = g.plane, Y = g.pitch;
         const double* fxs = fc;
         const double* fys = fc + g.total;
         const double* fzs = fc + 2 * g.total;
-        int64_t c = g.at(i, j, k0);
+        auto ld2 = [](const double* p, double (&o)[2]) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+            o[0] = v.x;
+            o[1] = v.y;
+        };
+        int64_t c = g.at(i0, j, k0);
         if (vk_exact_ok(emax)) {
             auto fix = [emax](double v) { return xs_fix(__double_as_longlong(v), emax); };
-            double uc = __ldg(src + c);
-            long long Uc = fix(uc);
-            long long dzm = Uc - fix(__ldg(src + c - P));
-            double czm = __ldg(fzs + c - P);
+            double uc[2], t[2], czm[2];
+            long long Uc[2], dzm[2];
+            ld2(src + c, uc);
+            ld2(src + c - P, t);
+            ld2(fzs + c - P, czm);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                Uc[q] = fix(uc[q]);
+                dzm[q] = Uc[q] - fix(t[q]);
+            }
             for (int k = k0; k < k1; ++k) {
-                const double ua = __ldg(src + c + P), cza = __ldg(fzs + c);
-                const long long Ua = fix(ua);
-                const long long dzp = Ua - Uc;
-                const double v = vk_point_exact(uc, Uc, fix(__ldg(src + c - 1)), fix(__ldg(src + c + 1)),
-                                                fix(__ldg(src + c - Y)), fix(__ldg(src + c + Y)), dzp, dzm,
-                                                __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y),
-                                                __ldg(fys + c), czm, cza, __ldg(fdt + c), beta, emax);
-                dst[c] = v;
-                const unsigned a = xs_abs_hi(v);
-                mx = a > mx ? a : mx;
-                uc = ua;
-                Uc = Ua;
-                dzm = dzp;
-                czm = cza;
+                double ua[2], ym[2], yp[2], cx[2], cym[2], cyp[2], cza[2], f[2];
+                ld2(src + c + P, ua);
+                ld2(src + c - Y, ym);
+                ld2(src + c + Y, yp);
+                ld2(fxs + c, cx);
+                ld2(fys + c - Y, cym);
+                ld2(fys + c, cyp);
+                ld2(fzs + c, cza);
+                ld2(fdt + c, f);
+                const long long Uxm = fix(__ldg(src + c - 1)), Uxp = fix(__ldg(src + c + 2));
+                const double cxm0 = __ldg(fxs + c - 1);
+                long long Ua[2], dzp[2];
+                double v[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    Ua[q] = fix(ua[q]);
+                    dzp[q] = Ua[q] - Uc[q];
+                    v[q] = vk_point_exact(uc[q], Uc[q], q == 0 ? Uxm : Uc[0], q == 0 ? Uc[1] : Uxp, fix(ym[q]),
+                                          fix(yp[q]), dzp[q], dzm[q], q == 0 ? cxm0 : cx[0], cx[q], cym[q],
+                                          cyp[q], czm[q], cza[q], f[q], beta, emax);
+                }
+                if (two) {
+                    *reinterpret_cast<double2*>(dst + c) = make_double2(v[0], v[1]);
+                } else {
+                    dst[c] = v[0];
+                    v[1] = 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const unsigned a = xs_abs_hi(v[q]);
+                    mx = a > mx ? a : mx;
+                    uc[q] = ua[q];
+                    Uc[q] = Ua[q];
+                    dzm[q] = dzp[q];
+                    czm[q] = cza[q];
+                }
                 c += P;
             }
         } else {
-            double uc = __ldg(src + c);
-            double dzm = __dsub_rn(uc, __ldg(src + c - P));
-            double czm = __ldg(fzs + c - P);
-            for (int k = k0; k < k1; ++k) {
-                const double ua = __ldg(src + c + P), cza = __ldg(fzs + c);
-                const double dzp = __dsub_rn(ua, uc);
-                const double v = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y),
-                                                __ldg(src + c + Y), dzp, dzm, __ldg(fxs + c - 1), __ldg(fxs + c),
-                                                __ldg(fys + c - Y), __ldg(fys + c), czm, cza, __ldg(fdt + c),
-                                                beta, beta, beta);
-                dst[c] = v;
-                const unsigned a = xs_abs_hi(v);
-                mx = a > mx ? a : mx;
-                uc = ua;
-                dzm = dzp;
-                czm = cza;
-                c += P;
+            // outside the exact form's range: the FP64 form, point by point
+            for (int q = 0; q < (two ? 2 : 1); ++q) {
+                int64_t cq = c + q;
+                double u = __ldg(src + cq);
+                double dzmq = __dsub_rn(u, __ldg(src + cq - P));
+                double czmq = __ldg(fzs + cq - P);
+                for (int k = k0; k < k1; ++k) {
+                    const double ua = __ldg(src + cq + P), cza = __ldg(fzs + cq);
+                    const double dzp = __dsub_rn(ua, u);
+                    const double w = vk_point_faces(u, __ldg(src + cq - 1), __ldg(src + cq + 1), __ldg(src + cq - Y),
+                                                    __ldg(src + cq + Y), dzp, dzmq, __ldg(fxs + cq - 1), __ldg(fxs + cq),
+                                                    __ldg(fys + cq - Y), __ldg(fys + cq), czmq, cza, __ldg(fdt + cq),
+                                                    beta, beta, beta);
+                    dst[cq] = w;
+                    const unsigned a = xs_abs_hi(w);
+                    mx = a > mx ? a : mx;
+                    u = ua;
+                    dzmq = dzp;
+                    czmq = cza;
+                    cq += P;
+                }
             }
         }
     }
@@ -252,7 +295,8 @@ __global__ void __launch_bounds__(kVkBX* kVkBY)
                              blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
-// Boundary planes 0 and nz-1 of a cubic FP64 grid, as k_vk_interior_xs.
+// Boundary planes 0 and nz-1 of a cubic FP64 grid, as k_vk_interior_xs (one
+// point per thread).
 __global__ void __launch_bounds__(kVkBX* kVkBY)
     k_vk_boundary_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
                      const double* __restrict__ fdt, HeatGeom g, double beta, FxState* fx, int m3)
@@ -420,10 +464,12 @@ int vk_launch_t(const VkCall& c)
         const int nchunks = (kend - kbeg + c.kchunk - 1) / c.kchunk;
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, nchunks);
         if constexpr (kFaces) {
-            if (c.fx)
-                k_vk_interior_xs<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
-                                                               (const double*)c.kap, (const double*)c.fdt, g,
-                                                               bx, kbeg, kend, c.kchunk, c.fx, c.m3);
+            if (c.fx) {
+                dim3 grid2((g.nx + 2 * kVkBX - 1) / (2 * kVkBX), grid.y, grid.z);
+                k_vk_interior_xs<<<grid2, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
+                                                                (const double*)c.kap, (const double*)c.fdt, g,
+                                                                bx, kbeg, kend, c.kchunk, c.fx, c.m3);
+            }
             else
                 k_vk_interior_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
                                                                   (const double*)c.kap, (const double*)c.fdt, g,
