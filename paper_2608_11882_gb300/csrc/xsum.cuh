@@ -118,6 +118,24 @@ __device__ __forceinline__ void i128_mac(I128& a, unsigned long long C, long lon
     asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(plo), "l"(phi));
 }
 
+// C d as a 128-bit value, exactly.
+__device__ __forceinline__ I128 i128_mul(unsigned long long C, long long d)
+{
+    return I128{(unsigned long long)d * C, __mul64hi(d, (long long)C)};
+}
+
+// a + b and a - b, exactly (two's complement, no overflow within the callers' ranges).
+__device__ __forceinline__ I128 i128_add(I128 a, I128 b)
+{
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+    return a;
+}
+__device__ __forceinline__ I128 i128_sub(I128 a, I128 b)
+{
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+    return a;
+}
+
 // (hi:lo) 2^s rounded to the nearest double, ties to even.  The caller keeps
 // |hi:lo| < 2^120 and s such that every nonzero result is a normal number.
 __device__ __forceinline__ double i128_to_double(I128 a, int s)
