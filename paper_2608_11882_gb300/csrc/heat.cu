@@ -923,14 +923,31 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
         c.fdt = h->fdt;
         c.g = &h->g;
         c.stream = h->stream;
+        int face_off = 1;
+        if (c.f64) {
+            e = dev_alloc((void**)&c.face_off, sizeof(int), h->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c.face_off, 0, sizeof(int), h->stream);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "heat_create: face-sum check word");
+                heat_destroy(h);
+                return rc;
+            }
+        }
         rc = vk_init(c, dt);
+        if (rc == HS_OK && c.f64) {
+            cudaError_t e2 = cudaMemcpyAsync(&face_off, c.face_off, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);
+            if (e2 != cudaSuccess) rc = cuda_fail(e2, "heat_create: face-sum check");
+        }
+        if (c.face_off) dev_free(c.face_off, h->stream);
         if (rc != HS_OK) {
             heat_destroy(h);
             return rc;
         }
-        // FP64 on a cubic grid (one beta for every axis): the exact-sum form,
-        // which tracks the field's largest exponent step by step
-        if (h->dtype == HS_F64 && h->vbx == h->vby && h->vby == h->vbz) {
+        // FP64 on a cubic grid (one beta for every axis), every face sum of
+        // kappa in [1, 2): the exact-sum form, which tracks the field's largest
+        // exponent step by step
+        if (h->dtype == HS_F64 && h->vbx == h->vby && h->vby == h->vbz && face_off == 0) {
             e = dev_alloc((void**)&h->fx, sizeof(FxState), h->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
             if (e != cudaSuccess) {

@@ -324,6 +324,7 @@ struct VkCall {
     FxState* fx;             // FP64 cubic grids: the per-step maxima of the exact-sum form
                              // (nullptr: the FP64 form, no maxima)
     int m3;                  // slot of the current field in fx
+    int* face_off;           // vk_init, FP64: device word set to 1 if a face sum lies outside [1, 2)
 };
 int vk_init(const VkCall& c, double dt);
 int vk_launch(const VkCall& c);

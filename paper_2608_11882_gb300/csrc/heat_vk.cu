@@ -52,8 +52,11 @@ __global__ void __launch_bounds__(256) k_vk_init(T* __restrict__ kap, T* __restr
 // node's +d neighbour + kappa at the node, zero where that neighbour lies
 // outside the padded box) and dt f on the interior.  The kappa values are the
 // same expression as k_vk_init's, so the sums are the bits the formula forms.
+// Sets *off = 1 if a face sum lies outside [1, 2), where the exact-sum form's
+// 53-bit significands would not hold it (kappa in [0.5, 1) keeps every face
+// sum inside).
 __global__ void __launch_bounds__(256) k_vk_init_faces(double* __restrict__ fc, double* __restrict__ fdt,
-                                                       HeatGeom g, double dt)
+                                                       HeatGeom g, double dt, int* off)
 {
     const double hx = 1.0 / (g.nx + 1), hy = 1.0 / (g.ny + 1), hz = 1.0 / (g.nz + 1);
     const int64_t n = (int64_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
@@ -68,9 +71,12 @@ __global__ void __launch_bounds__(256) k_vk_init_faces(double* __restrict__ fc, 
         const int K = (int)(jk / (g.ny + 2));
         const int64_t c = (int64_t)K * g.plane + (int64_t)J * g.pitch + g.lead - 1 + I;
         const double kc = kappa(I, J, K);
-        fc[c] = I <= g.nx ? kappa(I + 1, J, K) + kc : 0.0;
-        fc[g.total + c] = J <= g.ny ? kappa(I, J + 1, K) + kc : 0.0;
-        fc[2 * g.total + c] = K <= g.nz ? kappa(I, J, K + 1) + kc : 0.0;
+        const double sx = kappa(I + 1, J, K) + kc, sy = kappa(I, J + 1, K) + kc, sz = kappa(I, J, K + 1) + kc;
+        fc[c] = I <= g.nx ? sx : 0.0;
+        fc[g.total + c] = J <= g.ny ? sy : 0.0;
+        fc[2 * g.total + c] = K <= g.nz ? sz : 0.0;
+        auto out = [](double v) { return !(v >= 1.0 && v < 2.0); };
+        if ((I <= g.nx && out(sx)) || (J <= g.ny && out(sy)) || (K <= g.nz && out(sz))) atomicOr(off, 1);
         const bool interior = I >= 1 && I <= g.nx && J >= 1 && J <= g.ny && K >= 1 && K <= g.nz;
         fdt[c] = interior ? dt * (1.0 + cospi(I * hx) * cospi(J * hy) * cospi(K * hz)) : 0.0;
     }
@@ -456,7 +462,8 @@ int vk_init(const VkCall& c, double dt)
     int64_t blocks = (n + 255) / 256;
     if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
     if (c.f64)
-        k_vk_init_faces<<<(unsigned)blocks, 256, 0, c.stream>>>((double*)c.kap, (double*)c.fdt, *c.g, dt);
+        k_vk_init_faces<<<(unsigned)blocks, 256, 0, c.stream>>>((double*)c.kap, (double*)c.fdt, *c.g, dt,
+                                                                c.face_off);
     else
         k_vk_init<float><<<(unsigned)blocks, 256, 0, c.stream>>>((float*)c.kap, (float*)c.fdt, *c.g, dt);
     HS_CHECK_LAUNCH("heat: kappa/source init kernel");
