@@ -437,12 +437,10 @@ int stream_launch_xs(const StreamCall& c)
         return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
                     c.box[1], StreamShape<double>::BW, RY + 2);
     auto kern = k_heat_stream_xs<RY, RT, NST>;
-    static bool configured = false;
-    if (!configured) {
-        HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                    "heat: streaming kernel smem attribute");
-        configured = true;
-    }
+    // once per process, under the thread-safe initialisation of a local static
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    HS_TRY_CUDA(configured, "heat: streaming kernel smem attribute");
     const HeatGeom& g = *c.g;
     const int planes = c.kend - c.kbeg;
     if (planes <= 0) return HS_OK;
@@ -466,12 +464,10 @@ int stream_launch_t(const StreamCall& c)
         return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
                     c.box[1], StreamShape<T>::BW, RY + 2);
     auto kern = k_heat_stream<T, EXACT, RY, NST>;
-    static bool configured = false;
-    if (!configured) {
-        HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                    "heat: streaming kernel smem attribute");
-        configured = true;
-    }
+    // once per process, under the thread-safe initialisation of a local static
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    HS_TRY_CUDA(configured, "heat: streaming kernel smem attribute");
     const HeatGeom& g = *c.g;
     const int planes = c.kend - c.kbeg;
     if (planes <= 0) return HS_OK;

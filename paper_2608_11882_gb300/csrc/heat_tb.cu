@@ -325,12 +325,10 @@ int tb_launch_w(const TbCall& c)
         return fail(HS_EINVAL, "heat: tensor map box %ux%u does not match the kernel's %dx%d", c.box[0],
                     c.box[1], S::BW, S::ROWS);
     auto kern = k_heat_tb<T, EXACT, L, W, NST, MINB>;
-    static bool configured = false;
-    if (!configured) {
-        HS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                    "heat: temporal-blocking kernel smem attribute");
-        configured = true;
-    }
+    // once per process, under the thread-safe initialisation of a local static
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    HS_TRY_CUDA(configured, "heat: temporal-blocking kernel smem attribute");
     const HeatGeom& g = *c.g;
     dim3 grid((g.nx + S::TX - 1) / S::TX, (g.ny + S::TY - 1) / S::TY, (g.nz + c.kc - 1) / c.kc);
     dim3 block(W, S::RR, 1);
