@@ -12,10 +12,11 @@ pytestmark = pytest.mark.gpu
 DEPTHS = [2, 3, 4]
 # (70, 90, 300), (43, 67, 263) and (40, 70, 384) hold blocks whose every
 # computed point lies inside the interior (the unmasked form) beside edge
-# blocks, several z-chunks and ragged tails; FP32 grids 384 and 250 wide take
-# the 34-thread rows (128-column tiles), the others 32-thread rows
+# blocks, several z-chunks and ragged tails; FP32 grids 384, 256 and 250 wide
+# take the 34-thread rows (128-column tiles), the others 32-thread rows; (4, 2,
+# 256) has fewer rows than one tile
 SHAPES = [(1, 1, 1), (2, 3, 5), (33, 9, 17), (70, 3, 40), (40, 65, 31), (5, 100, 90),
-          (70, 90, 300), (43, 67, 263), (40, 70, 384), (9, 30, 250)]
+          (70, 90, 300), (43, 67, 263), (40, 70, 384), (9, 30, 250), (4, 2, 256)]
 
 
 @pytest.fixture(scope="module")
