@@ -196,7 +196,10 @@ __device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long l
 // points (16-byte loads of u, the face sums and dt f): four conversions per
 // point and half the load instructions of one point per thread, whose loads
 // left the kernel waiting on memory (57 against 77 GLUP/s at 510^3; three
-// blocks per SM at 80 registers).  The products through the face between a
+// blocks per SM at 80 registers; staging each plane through shared memory
+// so that every value is converted once, with one block barrier per plane,
+// measured slower: 55 GLUP/s, 71 with its loads issued one plane ahead, against
+// 85).  The products through the face between a
 // thread's two points and through the face below a plane (the face above it
 // one plane earlier) are formed once: 9 products for two points instead of
 // 12, and the sums stay exact, so the result is the same.  A thread whose
