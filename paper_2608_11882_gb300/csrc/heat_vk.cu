@@ -195,15 +195,15 @@ __device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long l
 // step's maximum (slot (m3 + 1) % 3).  Every thread takes two consecutive x
 // points (16-byte loads of u, the face sums and dt f): four conversions per
 // point and half the load instructions of one point per thread, whose loads
-// left the kernel waiting on memory (57 against 77 GLUP/s at 510^3; three
-// blocks per SM at 80 registers; staging each plane through shared memory
-// so that every value is converted once, with one block barrier per plane,
-// measured slower: 55 GLUP/s, 71 with its loads issued one plane ahead, against
-// 85).  The products through the face between a
-// thread's two points and through the face below a plane (the face above it
-// one plane earlier) are formed once: 9 products for two points instead of
-// 12, and the sums stay exact, so the result is the same.  A thread whose
-// second point is the boundary node nx computes only the first.
+// left the kernel waiting on memory; three blocks per SM at 80 registers.
+// The products through the face between a thread's two points and through the
+// face below a plane (the face above it one plane earlier) are formed once: 9
+// products for two points instead of 12, and the sums stay exact, so the
+// result is the same.  Measured at 510^3: one point per thread 57 GLUP/s, two
+// points 77, shared fluxes 85; staging each plane through shared memory so
+// that every value is converted once (one block barrier per plane) 55, 71 with
+// the staging loads issued one plane ahead.  A thread whose second point is
+// the boundary node nx computes only the first.
 __global__ void __launch_bounds__(kVkBX* kVkBY, 3)
     k_vk_interior_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
                       const double* __restrict__ fdt, HeatGeom g, double beta, int kbeg, int kend, int kchunk,
