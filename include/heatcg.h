@@ -89,12 +89,13 @@ extern "C" {
  * r <= 1/(6 kappa_max).  The coefficients (on every node, boundary included)
  * and dt f live on the device beside u, as in the paper's 1-GPU Baseline:
  * kappa itself for HS_F32, for HS_F64 the three face sums k[i+1] + k[i] of
- * each node (constant in time; the same values the formula forms).  On a
- * cubic HS_F64 grid the operator sum is formed exactly in integers on the
- * field's fixed-point scale (its largest exponent, tracked on the device as
- * for the default FP64 arithmetic) and rounded once: error below
- * 6 * 2 * 1.9 * 4 * 2^-57 max|u| beta plus three roundings per step; fields
- * outside [2^-903, 2^1007] in magnitude step in FP64 arithmetic.  HS_F64 or
+ * each node (constant in time; the same values the formula forms).  For
+ * HS_F64 the operator sums are formed exactly in integers on the field's
+ * fixed-point scale (its largest exponent, tracked on the device as for the
+ * default FP64 arithmetic) and rounded once -- the whole sum on a cubic grid,
+ * each axis's sum otherwise: error below 6 * 2 * 1.9 * 4 * 2^-57 max|u| beta
+ * plus a few roundings per step; fields outside [2^-903, 2^1007] in magnitude
+ * step in FP64 arithmetic.  HS_F64 or
  * HS_F32; excludes HS_FIXED64, HS_EXACT_ROUNDING, HS_SCHED_FULL and tdepth > 1;
  * cannot join a heat batch. */
 #define HS_VARKAPPA         0x10u

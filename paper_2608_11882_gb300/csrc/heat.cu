@@ -541,7 +541,7 @@ int vk_part(hs_heat* h, Part p, cudaStream_t s)
     c.bz = h->vbz;
     c.kchunk = h->kchunk;
     c.stream = s;
-    c.fx = h->fx;   // FP64 cubic grids only
+    c.fx = h->fx;   // FP64 only
     c.m3 = (int)(h->fxseq % 3);
     return vk_launch(c);
 }
@@ -944,10 +944,9 @@ int heat_create(hs_heat_t* out, const hs_heat_desc* desc)
             heat_destroy(h);
             return rc;
         }
-        // FP64 on a cubic grid (one beta for every axis), every face sum of
-        // kappa in [1, 2): the exact-sum form, which tracks the field's largest
-        // exponent step by step
-        if (h->dtype == HS_F64 && h->vbx == h->vby && h->vby == h->vbz && face_off == 0) {
+        // FP64 with every face sum of kappa in [1, 2): the exact-sum form,
+        // which tracks the field's largest exponent step by step
+        if (h->dtype == HS_F64 && face_off == 0) {
             e = dev_alloc((void**)&h->fx, sizeof(FxState), h->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->fx, 0, sizeof(FxState), h->stream);
             if (e != cudaSuccess) {

@@ -321,7 +321,7 @@ struct VkCall {
     double bx, by, bz;       // dt / (2 h_d^2)
     int kchunk;
     cudaStream_t stream;
-    FxState* fx;             // FP64 cubic grids: the per-step maxima of the exact-sum form
+    FxState* fx;             // FP64: the per-step maxima of the exact-sum form
                              // (nullptr: the FP64 form, no maxima)
     int m3;                  // slot of the current field in fx
     int* face_off;           // vk_init, FP64: device word set to 1 if a face sum lies outside [1, 2)

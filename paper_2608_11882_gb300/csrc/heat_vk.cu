@@ -12,13 +12,13 @@
 // the kernel is bound by HBM, where three face arrays would cost more than the
 // six additions they save).  FP64 keeps the three face sums k[i+1] + k[i] of
 // each node instead (constant in time, formed once at creation, bit for bit
-// the sums the formula forms every step), 48 bytes per update.  On a cubic
-// grid (one beta for every axis: the paper's case) the FP64 update forms the
-// operator sum exactly in 128-bit integers on the field's fixed-point scale
-// and rounds it once, 2 FP64 instructions per update; other grids (and fields
-// outside the exact form's exponent range) use the FP64 form, 16 FP64
-// instructions per update with the z difference u[k+1] - u[k] carried to the
-// next plane (23 with kappa itself).
+// the sums the formula forms every step), 48 bytes per update, and forms the
+// operator sums exactly in 128-bit integers on the field's fixed-point scale,
+// each rounded once: 2 FP64 instructions per update on a cubic grid (one beta
+// for every axis: the paper's case), 5 otherwise.  Fields outside the exact
+// form's exponent range use the FP64 form, 16 FP64 instructions per update
+// with the z difference u[k+1] - u[k] carried to the next plane (23 with kappa
+// itself).
 #include <cmath>
 
 #include "heat_common.cuh"
@@ -148,19 +148,22 @@ __global__ void __launch_bounds__(kVkBX* kVkBY)
                             __ldg(fz + c - P), __ldg(fz + c), __ldg(fdt + c), bx, by, bz);
 }
 
-// ---- FP64, exact sum (cubic grids: one beta for every axis) ----------------
-// The operator sum D = sum_d [c_d+ (u_d+ - u) - c_d- (u - u_d-)] on the field's
+// ---- FP64, exact sum ------------------------------------------------------
+// The operator sums D_d = c_d+ (u_d+ - u) - c_d- (u - u_d-) on the field's
 // fixed-point scale: U the exact-sum integers of the u values (xsum.cuh, the
 // scale 2^(1080 - e) of the field's largest exponent field e, tracked per step
 // in the handle's FxState like the default FP64 arithmetic's), C the face
 // sums' 53-bit significands (every face sum of kappa = 0.5 + 0.45 s, s in
-// [0, 1], lies in [1, 2), so C = c 2^52 exactly), each product C dU exact and
-// their sum exact in 128 bits, rounded once to FP64; then
-// u' = fma(beta, D, u + dt f).  Two FP64 instructions per update instead of
-// sixteen; the error against the same formula in exact arithmetic is below
-// 6 * 2 * 1.9 * 4 * 2^-57 max|u| beta plus three roundings.  Fields whose
-// exponent lies outside [kVkEmaxLo, kVkEmaxHi] (all-zero or tiny fields,
-// values near overflow, NaN, Inf) take the FP64 form of vk_point_faces.
+// [0, 1], lies in [1, 2), so C = c 2^52 exactly; heat_create checks it), each
+// product C dU exact and their sums exact in 128 bits.  On a cubic grid (one
+// beta for every axis, the paper's case) the whole operator sum is rounded
+// once and u' = fma(beta, D, u + dt f): two FP64 instructions per update
+// instead of sixteen; otherwise each axis sum is rounded once and combined as
+// the FP64 form combines them, five FP64 instructions.  The error against the
+// same formula in exact arithmetic is below 6 * 2 * 1.9 * 4 * 2^-57 max|u|
+// beta plus a few roundings.  Fields whose exponent lies outside
+// [kVkEmaxLo, kVkEmaxHi] (all-zero or tiny fields, values near overflow, NaN,
+// Inf) take the FP64 form of vk_point_faces.
 constexpr int kVkEmaxLo = 120, kVkEmaxHi = 2030;
 
 __device__ __forceinline__ unsigned long long vk_face_sig(double c)
@@ -171,26 +174,39 @@ __device__ __forceinline__ unsigned long long vk_face_sig(double c)
 
 __device__ __forceinline__ bool vk_exact_ok(int emax) { return emax >= kVkEmaxLo && emax <= kVkEmaxHi; }
 
+// u' from the exact operator sums: one sum (all axes) rounded once on a cubic
+// grid, u' = fma(beta, D, u + dt f); else the three axis sums, each rounded
+// once, combined as the FP64 form combines them: (u + dt f) + ((bx Dx + by Dy)
+// + bz Dz).  C dU carries the scale 2^52 2^(1080 - e).
+template <bool CUBIC>
+__device__ __forceinline__ double vk_combine(double uc, double f, I128 dx, I128 dy, I128 dz, double bx, double by,
+                                             double bz, int emax)
+{
+    if constexpr (CUBIC) {
+        const double D = i128_to_double(i128_add(i128_add(dx, dy), dz), emax - 1132);
+        return __fma_rn(bx, D, __dadd_rn(uc, f));
+    } else {
+        const double Dx = i128_to_double(dx, emax - 1132), Dy = i128_to_double(dy, emax - 1132),
+                     Dz = i128_to_double(dz, emax - 1132);
+        return __dadd_rn(__dadd_rn(uc, f), __fma_rn(bz, Dz, __fma_rn(by, Dy, __dmul_rn(bx, Dx))));
+    }
+}
+
 // One update on the exact path from the seven u values (as doubles, the centre
 // also as its integer), the six face sums and dt f.
+template <bool CUBIC>
 __device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long long Uxm, long long Uxp,
                                                  long long Uym, long long Uyp, long long dzp, long long dzm,
                                                  double cxm, double cxp, double cym, double cyp, double czm,
-                                                 double czp, double f, double beta, int emax)
+                                                 double czp, double f, double bx, double by, double bz, int emax)
 {
-    I128 acc{0ull, 0ll};
-    i128_mac(acc, vk_face_sig(cxp), Uxp - Uc);
-    i128_mac(acc, vk_face_sig(cxm), Uxm - Uc);
-    i128_mac(acc, vk_face_sig(cyp), Uyp - Uc);
-    i128_mac(acc, vk_face_sig(cym), Uym - Uc);
-    i128_mac(acc, vk_face_sig(czp), dzp);
-    i128_mac(acc, vk_face_sig(czm), -dzm);
-    // C dU carries the scale 2^52 2^(1080 - e)
-    const double D = i128_to_double(acc, emax - 1132);
-    return __fma_rn(beta, D, __dadd_rn(uc, f));
+    const I128 dx = i128_sub(i128_mul(vk_face_sig(cxp), Uxp - Uc), i128_mul(vk_face_sig(cxm), Uc - Uxm));
+    const I128 dy = i128_sub(i128_mul(vk_face_sig(cyp), Uyp - Uc), i128_mul(vk_face_sig(cym), Uc - Uym));
+    const I128 dz = i128_sub(i128_mul(vk_face_sig(czp), dzp), i128_mul(vk_face_sig(czm), dzm));
+    return vk_combine<CUBIC>(uc, f, dx, dy, dz, bx, by, bz, emax);
 }
 
-// Interior (planes kbeg..kend-1) of a cubic FP64 grid: the exact sum while the
+// Interior (planes kbeg..kend-1) of an FP64 grid: the exact sums while the
 // field's exponent allows it, the FP64 form otherwise; every output joins the
 // step's maximum (slot (m3 + 1) % 3).  Every thread takes two consecutive x
 // points (16-byte loads of u, the face sums and dt f): four conversions per
@@ -204,10 +220,11 @@ __device__ __forceinline__ double vk_point_exact(double uc, long long Uc, long l
 // that every value is converted once (one block barrier per plane) 55, 71 with
 // the staging loads issued one plane ahead.  A thread whose second point is
 // the boundary node nx computes only the first.
+template <bool CUBIC>
 __global__ void __launch_bounds__(kVkBX* kVkBY, 3)
     k_vk_interior_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
-                      const double* __restrict__ fdt, HeatGeom g, double beta, int kbeg, int kend, int kchunk,
-                      FxState* fx, int m3)
+                      const double* __restrict__ fdt, HeatGeom g, double bx, double by, double bz, int kbeg,
+                      int kend, int kchunk, FxState* fx, int m3)
 {
     const int i0 = (blockIdx.x * kVkBX + threadIdx.x) * 2;
     const int j = blockIdx.y * kVkBY + threadIdx.y;
@@ -264,13 +281,12 @@ __global__ void __launch_bounds__(kVkBX* kVkBY, 3)
                 for (int q = 0; q < 2; ++q) {
                     Ua[q] = fix(ua[q]);
                     const I128 fzp = i128_mul(vk_face_sig(cza[q]), Ua[q] - Uc[q]);
-                    I128 D = q == 0 ? i128_sub(fb, fa) : i128_sub(fcx, fb);
-                    D = i128_add(D, i128_mul(vk_face_sig(cyp[q]), fix(yp[q]) - Uc[q]));
-                    D = i128_sub(D, i128_mul(vk_face_sig(cym[q]), Uc[q] - fix(ym[q])));
-                    D = i128_add(D, i128_sub(fzp, fzm[q]));
+                    const I128 dx = q == 0 ? i128_sub(fb, fa) : i128_sub(fcx, fb);
+                    const I128 dy = i128_sub(i128_mul(vk_face_sig(cyp[q]), fix(yp[q]) - Uc[q]),
+                                             i128_mul(vk_face_sig(cym[q]), Uc[q] - fix(ym[q])));
+                    const I128 dz = i128_sub(fzp, fzm[q]);
                     fzm[q] = fzp;
-                    // C dU carries the scale 2^52 2^(1080 - e)
-                    v[q] = __fma_rn(beta, i128_to_double(D, emax - 1132), __dadd_rn(uc[q], f[q]));
+                    v[q] = vk_combine<CUBIC>(uc[q], f[q], dx, dy, dz, bx, by, bz, emax);
                 }
                 if (two) {
                     *reinterpret_cast<double2*>(dst + c) = make_double2(v[0], v[1]);
@@ -300,7 +316,7 @@ __global__ void __launch_bounds__(kVkBX* kVkBY, 3)
                     const double w = vk_point_faces(u, __ldg(src + cq - 1), __ldg(src + cq + 1), __ldg(src + cq - Y),
                                                     __ldg(src + cq + Y), dzp, dzmq, __ldg(fxs + cq - 1), __ldg(fxs + cq),
                                                     __ldg(fys + cq - Y), __ldg(fys + cq), czmq, cza, __ldg(fdt + cq),
-                                                    beta, beta, beta);
+                                                    bx, by, bz);
                     dst[cq] = w;
                     const unsigned a = xs_abs_hi(w);
                     mx = a > mx ? a : mx;
@@ -316,11 +332,13 @@ __global__ void __launch_bounds__(kVkBX* kVkBY, 3)
                              blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
 }
 
-// Boundary planes 0 and nz-1 of a cubic FP64 grid, as k_vk_interior_xs (one
+// Boundary planes 0 and nz-1 of an FP64 grid, as k_vk_interior_xs (one
 // point per thread).
+template <bool CUBIC>
 __global__ void __launch_bounds__(kVkBX* kVkBY)
     k_vk_boundary_xs(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ fc,
-                     const double* __restrict__ fdt, HeatGeom g, double beta, FxState* fx, int m3)
+                     const double* __restrict__ fdt, HeatGeom g, double bx, double by, double bz, FxState* fx,
+                     int m3)
 {
     const int i = blockIdx.x * kVkBX + threadIdx.x;
     const int j = blockIdx.y * kVkBY + threadIdx.y;
@@ -338,15 +356,16 @@ __global__ void __launch_bounds__(kVkBX* kVkBY)
         if (vk_exact_ok(emax)) {
             auto fix = [emax](double w) { return xs_fix(__double_as_longlong(w), emax); };
             const long long Uc = fix(uc);
-            v = vk_point_exact(uc, Uc, fix(__ldg(src + c - 1)), fix(__ldg(src + c + 1)), fix(__ldg(src + c - Y)),
-                               fix(__ldg(src + c + Y)), fix(__ldg(src + c + P)) - Uc, Uc - fix(__ldg(src + c - P)),
-                               __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y), __ldg(fys + c),
-                               __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), beta, emax);
+            v = vk_point_exact<CUBIC>(uc, Uc, fix(__ldg(src + c - 1)), fix(__ldg(src + c + 1)),
+                                      fix(__ldg(src + c - Y)), fix(__ldg(src + c + Y)),
+                                      fix(__ldg(src + c + P)) - Uc, Uc - fix(__ldg(src + c - P)),
+                                      __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y), __ldg(fys + c),
+                                      __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), bx, by, bz, emax);
         } else {
             v = vk_point_faces(uc, __ldg(src + c - 1), __ldg(src + c + 1), __ldg(src + c - Y), __ldg(src + c + Y),
                                __dsub_rn(__ldg(src + c + P), uc), __dsub_rn(uc, __ldg(src + c - P)),
                                __ldg(fxs + c - 1), __ldg(fxs + c), __ldg(fys + c - Y), __ldg(fys + c),
-                               __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), beta, beta, beta);
+                               __ldg(fzs + c - P), __ldg(fzs + c), __ldg(fdt + c), bx, by, bz);
         }
         dst[c] = v;
         mx = xs_abs_hi(v);
@@ -488,9 +507,10 @@ int vk_launch_t(const VkCall& c)
         if constexpr (kFaces) {
             if (c.fx) {
                 dim3 grid2((g.nx + 2 * kVkBX - 1) / (2 * kVkBX), grid.y, grid.z);
-                k_vk_interior_xs<<<grid2, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
-                                                                (const double*)c.kap, (const double*)c.fdt, g,
-                                                                bx, kbeg, kend, c.kchunk, c.fx, c.m3);
+                auto kern = (bx == by && by == bz) ? k_vk_interior_xs<true> : k_vk_interior_xs<false>;
+                kern<<<grid2, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst, (const double*)c.kap,
+                                                    (const double*)c.fdt, g, bx, by, bz, kbeg, kend, c.kchunk,
+                                                    c.fx, c.m3);
             }
             else
                 k_vk_interior_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
@@ -508,10 +528,11 @@ int vk_launch_t(const VkCall& c)
     } else {
         dim3 grid((g.nx + kVkBX - 1) / kVkBX, (g.ny + kVkBY - 1) / kVkBY, g.nz >= 2 ? 2 : 1);
         if constexpr (kFaces) {
-            if (c.fx)
-                k_vk_boundary_xs<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
-                                                               (const double*)c.kap, (const double*)c.fdt, g,
-                                                               bx, c.fx, c.m3);
+            if (c.fx) {
+                auto kern = (bx == by && by == bz) ? k_vk_boundary_xs<true> : k_vk_boundary_xs<false>;
+                kern<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst, (const double*)c.kap,
+                                                   (const double*)c.fdt, g, bx, by, bz, c.fx, c.m3);
+            }
             else
                 k_vk_boundary_faces<<<grid, block, 0, c.stream>>>((const double*)c.src, (double*)c.dst,
                                                                   (const double*)c.kap, (const double*)c.fdt, g,

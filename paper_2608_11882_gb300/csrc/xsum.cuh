@@ -100,23 +100,14 @@ __device__ __forceinline__ double xs_apply(double uc, long long L, double r, dou
     return __fma_rn(r, xs_unfix(L, emax), uc);
 }
 
-// ---- exact weighted sums: 128-bit accumulation ---------------------------
+// ---- exact weighted sums: 128-bit arithmetic -----------------------------
 // A sum of products C d, C < 2^53 an integer weight and d a difference of two
-// fixed-point values (|d| < 2^60), is exact in a 128-bit two's-complement
-// accumulator (hi:lo) for up to 2^14 terms; it is rounded once to FP64 by
-// i128_to_double.
+// fixed-point values (|d| < 2^60), is exact in 128-bit two's complement
+// (hi:lo) for up to 2^14 terms; it is rounded once to FP64 by i128_to_double.
 struct I128 {
     unsigned long long lo;
     long long hi;
 };
-
-// a += C d, exactly.
-__device__ __forceinline__ void i128_mac(I128& a, unsigned long long C, long long d)
-{
-    const unsigned long long plo = (unsigned long long)d * C;   // the low 64 bits, signed or not
-    const long long phi = __mul64hi(d, (long long)C);          // the signed high 64 bits (C < 2^63)
-    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(plo), "l"(phi));
-}
 
 // C d as a 128-bit value, exactly.
 __device__ __forceinline__ I128 i128_mul(unsigned long long C, long long d)

@@ -53,14 +53,16 @@ def test_vk_f32_within_bound(pkg, shape):
     assert float(np.max(np.abs(got - ref))) <= bound
 
 
+@pytest.mark.parametrize("shape", [(33, 33, 33), (21, 34, 27)])
 @pytest.mark.parametrize("scale", [1.0, 1e-250, 1e250, 1e-300])
-def test_vk_f64_cubic_exact_sum_against_oracle(pkg, scale):
-    """Cubic FP64 grids take the exact-sum form (the operator sum exact in 128
-    bits on the field's fixed-point scale, rounded once) while the field's
-    exponent allows; 1e-300 starts on the FP64 form and the source lifts the
-    field into range within a step, 1e-250 and 1e250 run exact throughout."""
-    n = 33
-    u0 = heat_u0_single_mode(n, n, n, seed=16) * scale
+def test_vk_f64_exact_sum_against_oracle(pkg, scale, shape):
+    """FP64 grids take the exact-sum form (the operator sums exact in 128 bits
+    on the field's fixed-point scale, rounded once: the whole sum on a cubic
+    grid, each axis's sum on the non-cubic one) while the field's exponent
+    allows; 1e-300 starts on the FP64 form and the source lifts the field into
+    range within a step, 1e-250 and 1e250 run exact throughout."""
+    nz, ny, nx = shape
+    u0 = heat_u0_single_mode(nx, ny, nz, seed=16) * scale
     ref = oracle.heat_vk_run(u0, R_PAPER, 40, threads=oracle.max_threads())
     assert rel_max_err(run_vk(pkg, u0, R_PAPER, 40), ref) <= F64_REL
 
@@ -72,14 +74,14 @@ def test_vk_f64_cubic_from_zero_field(pkg):
 
 
 def test_vk_f64_cubic_tight_against_oracle(pkg):
-    """The exact-sum form rounds the operator sum once per point, so after 50
-    steps at 40^3 it stays within 1e-13 of the oracle (relative to max|u|),
-    ten times inside the FP64 gate."""
-    n = 40
-    u0 = heat_u0_single_mode(n, n, n, seed=18)
-    ref = oracle.heat_vk_run(u0, R_PAPER, 50, threads=oracle.max_threads())
-    got = run_vk(pkg, u0, R_PAPER, 50)
-    assert rel_max_err(got, ref) <= 1e-13
+    """The exact-sum form rounds the operator sums once per point, so after 50
+    steps at 40^3 (and on a non-cubic grid) it stays within 1e-13 of the
+    oracle (relative to max|u|), ten times inside the FP64 gate."""
+    for nz, ny, nx in [(40, 40, 40), (36, 44, 41)]:
+        u0 = heat_u0_single_mode(nx, ny, nz, seed=18)
+        ref = oracle.heat_vk_run(u0, R_PAPER, 50, threads=oracle.max_threads())
+        got = run_vk(pkg, u0, R_PAPER, 50)
+        assert rel_max_err(got, ref) <= 1e-13, (nz, ny, nx)
 
 
 def test_vk_errors(pkg):
