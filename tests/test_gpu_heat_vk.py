@@ -84,6 +84,16 @@ def test_vk_f64_cubic_tight_against_oracle(pkg):
         assert rel_max_err(got, ref) <= 1e-13, (nz, ny, nx)
 
 
+def test_vk_f64_one_step_close_to_oracle(pkg):
+    """One step of the exact-sum form differs from the oracle's written-order
+    FP64 step only by roundings (each operator sum is exact before its one
+    rounding): within 2e-15 of max|u| on a cubic and a non-cubic grid."""
+    for nz, ny, nx in [(30, 30, 30), (26, 31, 35)]:
+        u0 = heat_u0_single_mode(nx, ny, nz, seed=19)
+        ref = oracle.heat_vk_run(u0, R_PAPER, 1)
+        assert rel_max_err(run_vk(pkg, u0, R_PAPER, 1), ref) <= 2e-15, (nz, ny, nx)
+
+
 def test_vk_errors(pkg):
     from paper_2608_11882_gb300._native import HS_EINVAL, HS_EUNSTABLE
     with pytest.raises(pkg.HeatCGError) as e:
