@@ -127,11 +127,11 @@ def parse_args():
                     help="skip every side measurement (same as --sides none)")
     ap.add_argument("--sides", default="all",
                     help="comma list of side measurements after the timed steps: modes, batching, "
-                         "paper, mixed, serving; 'all' or 'none'")
+                         "paper, mixed, precision, serving; 'all' or 'none'")
     return ap.parse_args()
 
 
-SIDES = ("modes", "batching", "paper", "mixed", "serving")
+SIDES = ("modes", "batching", "paper", "mixed", "precision", "serving")
 
 
 def sides_of(args) -> set:
@@ -762,6 +762,10 @@ def run_ours(args):
                                                         hbm_gbs, peak_kind)}
         line["cg"]["mixed_f32_krylov"] = mixed
 
+    # ---- precision: heat 1024^3 FP32 against FIXED64, CG 512^3 to 1e-10 ---------
+    if "precision" in sides:
+        line["precision"] = precision_side(pkg, stream)
+
     # ---- serving: the Poisson request stream, closed loop and one offered load ----
     if "serving" in sides:
         line["serving"] = serving_side(args, loads=(0.7,))
@@ -779,26 +783,21 @@ def run_ours(args):
     return 0
 
 
-def run_precision(args):
-    """The precision workload: heat 1024^3 FP32 (storage and arithmetic),
-    r = 0.1, 2000 steps, max error against the FIXED64 path (FP64 interface,
-    parity-tested against the FP64 oracle); CG on 512^3 to rtol 1e-10 with
-    FP32 Krylov vectors and FP64 refinement, beside FP64 CG."""
-    import numpy as np
+def precision_side(pkg, stream):
+    """The precision workload: heat 1024^3 FP32 (storage and arithmetic, the
+    default two steps per pass), r = 0.1, 2000 steps, max error against the
+    FIXED64 path (FP64 interface, parity-tested against the FP64 oracle); CG
+    on 512^3 to rtol 1e-10 with FP32 Krylov vectors and FP64 refinement,
+    beside FP64 CG.  The field is formed on the device (heat_u0_modes_device)."""
     import torch
 
-    from paper_2608_11882_gb300.build import build
-    build()
-    import paper_2608_11882_gb300 as pkg
-    from workloads import cg_rhs, heat_u0_modes
+    from workloads import cg_rhs, heat_u0_modes_device
 
-    stream = torch.cuda.current_stream()
     n, steps, r = 1024, 2000, 0.1
-    u0, _, _ = heat_u0_modes(n, n, n, seed=SEED)
     res = {}
     fields = {}
     for mode, dtype, flags in (("f32", "f32", 0), ("fixed64", "f64", pkg.HS_FIXED64)):
-        src = torch.from_numpy(u0).cuda()
+        src = heat_u0_modes_device(n, n, n, "cuda", seed=SEED)
         if dtype == "f32":
             src = src.float()
         with pkg.Heat(n, n, n, r, dtype=dtype, flags=flags, stream=stream) as h:
@@ -810,14 +809,15 @@ def run_precision(args):
             out = torch.empty_like(src)
             h.read(out)
             ms = e0.elapsed_time(e1)
-        res[mode] = {"glups": float(n) ** 3 * steps / (ms * 1e-3) / 1e9, "ms": ms}
+            res[mode] = {"glups": float(n) ** 3 * steps / (ms * 1e-3) / 1e9, "ms": ms, "tdepth": h.tdepth}
         fields[mode] = out.double()
-        del src
+        del src, out
     ref = fields["fixed64"]
     err = float((fields["f32"] - ref).abs().max())
     res["f32"]["max_abs_err_vs_fixed64"] = err
     res["f32"]["max_rel_err_vs_fixed64"] = err / float(ref.abs().max())
     del fields, ref
+    torch.cuda.empty_cache()
     m = 512
     b = torch.from_numpy(cg_rhs(m ** 3, seed=SEED)).cuda()
     cgres = {}
@@ -832,9 +832,22 @@ def run_precision(args):
             cgres[name] = {"ms": e0.elapsed_time(e1), "iters": info["iters"],
                            "refinements": info["refinements"], "relres_true": info["relres_true"],
                            "converged": info["converged"]}
-    line = {"workload": "precision: heat 1024^3 FP32 r=0.1 2000 steps; CG 512^3 matrix-free rtol 1e-10",
+    cgres["mixed_speedup"] = cgres["f64"]["ms"] / cgres["mixed_f32_krylov"]["ms"]
+    del b
+    torch.cuda.empty_cache()
+    return {"workload": "precision: heat 1024^3 FP32 r=0.1 2000 steps against FIXED64; "
+                        "CG 512^3 matrix-free rtol 1e-10, FP64 and mixed",
             "heat": res, "cg": cgres}
-    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """--workload precision: the precision workload alone."""
+    import torch
+
+    from paper_2608_11882_gb300.build import build
+    build()
+    import paper_2608_11882_gb300 as pkg
+    print(json.dumps(precision_side(pkg, torch.cuda.current_stream())), flush=True)
     return 0
 
 

@@ -71,6 +71,31 @@ def heat_u0_modes(nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED, n_modes: 
     return np.ascontiguousarray(u.astype(dtype, copy=False)), modes, amps
 
 
+def heat_u0_modes_device(nx: int, ny: int, nz: int, device, seed: int = DEFAULT_SEED, n_modes: int = 8,
+                         kmax: int = 16, noise: float = 1e-3):
+    """The sum of sine modes of heat_u0_modes (the same wave numbers and
+    amplitudes) formed directly on a torch device, for grids too large to
+    generate on the host in seconds (1024^3: 8.6 GB).  The noise, of the same
+    distribution, comes from torch's seeded generator on that device, so it
+    is a different draw than heat_u0_modes's."""
+    import torch
+    modes, amps = draw_modes(seed, n_modes, kmax)
+    f64 = torch.float64
+    xs = torch.from_numpy(grid_coords(nx)).to(device)
+    ys = torch.from_numpy(grid_coords(ny)).to(device)
+    zs = torch.from_numpy(grid_coords(nz)).to(device)
+    u = torch.zeros((nz, ny, nx), dtype=f64, device=device)
+    for (kx, ky, kz), a in zip(modes, amps):
+        sx = torch.sin(kx * np.pi * xs)
+        sy = torch.sin(ky * np.pi * ys)
+        sz = a * torch.sin(kz * np.pi * zs)
+        u += sz[:, None, None] * (sy[:, None] * sx[None, :])[None, :, :]
+    if noise:
+        gen = torch.Generator(device=device).manual_seed(seed * 7919 + 1)
+        u += noise * (2.0 * torch.rand((nz, ny, nx), dtype=f64, device=device, generator=gen) - 1.0)
+    return u
+
+
 def cg_rhs(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     return np.random.default_rng([seed, 2]).standard_normal(n)
 
