@@ -48,7 +48,8 @@ class Heat:
 
     def __init__(self, nx: int, ny: int, nz: int, r: float, dtype: str = "f64", flags: int = 0,
                  stream=None, tdepth=0, buffers=None):
-        """tdepth: steps per pass (0 = the library's default, 1..4), or "auto" for
+        """tdepth: steps per pass (0 = the library's default: 2 for FP32, 1
+        otherwise; 1..4), or "auto" for
         the autotuner's cached or freshly measured choice for this shape (the
         depth, and the Interior kernel's planes per block).
         buffers: optional pair of caller-owned CUDA tensors for the two padded
