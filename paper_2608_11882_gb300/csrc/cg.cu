@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(kCgBlock)
     }
 }
 
-// The matrix-free SpMV staged by loads (SP_STAGED), fused with p.q: blocks of
-// kSpBlock threads, as many as the other kernels of the solve use.
+// The matrix-free SpMV staged by loads (SP_STAGED), fused with p.q: one block
+// of kSpBlock threads per share (spmv_shares of the solve's block count).
 __global__ void __launch_bounds__(kSpBlock, kSpMinBlocks)
     k_cg_spmv_staged(OpDev A, const double* __restrict__ p, double* __restrict__ q, double* partials,
                      CgScalars* S)
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kSpBlock, kSpMinBlocks)
     grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kSpBlock / 32];
-    const double pq = spmv_stencil_blocks(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
+    const double pq = spmv_stencil_share(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
     allow_dependents();
     const double blk = block_sum<kSpBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
@@ -342,11 +342,11 @@ int cg_spmv(const hs_op* A, const void* p, void* q, int kernel, double* pq, void
     }
     if (e == cudaSuccess) {
         if (tma) {
-            rc = spmv_tma_launch(pmap, D, (double*)q, partials, S, grid, s);
+            rc = spmv_tma_launch(pmap, D, (double*)q, partials, S, spmv_shares(grid), s);
         } else {
             if (mode == SP_STAGED) {
-                e = launch_dependent(k_cg_spmv_staged, grid, kSpBlock, s, D, (const double*)p, (double*)q,
-                                     partials, S);
+                e = launch_dependent(k_cg_spmv_staged, spmv_shares(grid), kSpBlock, s, D, (const double*)p,
+                                     (double*)q, partials, S);
             } else {
                 auto kern = mode == SP_CSR ? k_cg_spmv_dot<SP_CSR> : k_cg_spmv_dot<SP_ROWS>;
                 e = launch_dependent(kern, grid, kCgBlock, s, D, (const double*)p, (double*)q, partials, S);
@@ -487,6 +487,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     if (rc != HS_OK) return rc;
     const int mode = spmv_mode(c->A, c->grid);
     const int track = mode == SP_STAGED;   // the staged SpMV needs p's largest exponent
+    const int shares = mode == SP_STAGED ? spmv_shares(c->grid) : c->grid;
     // the staged SpMV takes p through TMA when the grid and the vectors allow
     CUtensorMap pmap;
     const bool tma = mode == SP_STAGED && spmv_tma_eligible(c->A, c->p, c->q, c->grid) &&
@@ -509,10 +510,10 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
             switch (mode) {
             case SP_STAGED:
                 if (tma) {
-                    rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, c->grid, c->stream);
+                    rc = spmv_tma_launch(pmap, c->A, c->q, c->partials, c->S, shares, c->stream);
                     if (rc != HS_OK) return rc;
                 } else {
-                    HS_TRY_CUDA(launch_dependent(k_cg_spmv_staged, c->grid, kSpBlock, c->stream, c->A,
+                    HS_TRY_CUDA(launch_dependent(k_cg_spmv_staged, shares, kSpBlock, c->stream, c->A,
                                            (const double*)c->p, c->q, c->partials, c->S), "cg: kernel launch");
                 }
                 break;

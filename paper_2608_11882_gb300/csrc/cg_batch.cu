@@ -30,6 +30,7 @@ struct SysDev {
     int32_t nblocks;
     int32_t max_iter;
     int32_t mode;       // SpmvMode of the operator with this block count
+    int32_t nshares;    // SP_STAGED: shares of the SpMV (spmv_shares(nblocks)), else nblocks
 };
 
 // System of this block (binary search over block0) and the block's index in it.
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(NT, MINB) k_cgb_spmv_dot(const SysDev* sys, in
     const int64_t row0 = (int64_t)local * NT + threadIdx.x;
     const int64_t stride = (int64_t)s.nblocks * NT;
     if (MODE == SP_STAGED) {
-        pq = spmv_stencil_blocks(s.A, s.p, s.q, cg_pemax(s.S), local, s.nblocks);
+        // share `local` of a single solve's launch; the blocks beyond the shares add 0
+        if (local < s.nshares) pq = spmv_stencil_share(s.A, s.p, s.q, cg_pemax(s.S), local, s.nshares);
     } else for (int64_t row = row0; row < s.A.n; row += stride) {
         const double qv = MODE == SP_CSR ? apply_csr_row(s.A, s.p, row) : apply_stencil_row(s.A, s.p, row);
         s.q[row] = qv;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(NT, MINB) k_cgb_spmv_dot(const SysDev* sys, in
     allow_dependents();
     const double blk = block_sum<NT>(pq, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
-    const double tot = sum_partials_nt<NT>(s.partials, s.nblocks, sh);
+    const double tot = sum_partials_nt<NT>(s.partials, s.nshares, sh);
     if (threadIdx.x == 0) {
         CgScalars* S = s.S;
         S->ticket = 0;
@@ -279,6 +281,7 @@ int cg_batch_create(hs_cg_batch_t* out, const hs_op* ops, int32_t n, void* strea
         s.A = to_dev(&ops[i]);
         s.nblocks = grid_for(s.A.n);
         s.mode = spmv_mode(s.A, s.nblocks);
+        s.nshares = s.mode == SP_STAGED ? spmv_shares(s.nblocks) : s.nblocks;
         b->has_mode[s.mode] = true;
         s.block0 = (int32_t)blocks;
         blocks += s.nblocks;

@@ -128,12 +128,16 @@ __device__ __forceinline__ bool cg_xs_ok(int emax) { return emax >= kXsEmaxLo &&
 // written to one of two shared plane buffers; a thread keeps its own values
 // at k-1, k and k+1 in registers, reads the other neighbours from the buffer
 // of plane k, and one block barrier per plane orders the buffers.  Points
-// outside the grid are staged as zeros (the Dirichlet boundary).  Work items
-// (tile, chunk) are taken by the system's `nblocks` blocks in a fixed order,
-// and each thread adds its p.q products in a fixed order (row by row, x
-// ascending), so a block's partial p.q -- and the whole reduction -- repeats
-// bit for bit wherever the same operator runs with the same block count (a
-// batch uses its systems' own).
+// outside the grid are staged as zeros (the Dirichlet boundary).  The work is
+// cut into `nshares` equal shares of the (tile, plane) pairs in tile-major
+// order -- share b is one run of consecutive planes of one tile, or two at a
+// tile boundary -- where nshares is the number of TMA-staged blocks resident
+// on the device at once (spmv_shares), so one wave of blocks moves the same
+// bytes each and none waits for a second wave on part of the GPU.  Each
+// thread adds its p.q products in a fixed order (run by run, plane by plane,
+// row by row, x ascending) and the reduction sums the shares' partials in
+// share order, so p.q repeats bit for bit wherever the same operator runs
+// with the same share count (a batch uses its systems' own).
 constexpr int kSpTW = 64, kSpTY = 8, kSpBW = 68, kSpD = 2;   // tile width/rows, buffer row, x offset
 constexpr int kSpPlane = (kSpTY + 2) * kSpBW;                // buffer elements per plane
 constexpr int kSpBlock = 128, kSpRT = 2;                     // threads of a staged block, rows per thread
@@ -151,27 +155,41 @@ __device__ __forceinline__ double sum_partials_nt(const double* partials, int m,
 }
 
 struct SpmvPlan {
-    int64_t tiles, items;
-    int tiles_x, kc;       // tiles per row of tiles, planes per chunk
+    int64_t tiles;
+    int tiles_x;   // tiles per row of tiles
 };
 
-// About one work item per block (the longest chunks that still give every
-// block work: each item restages its first and last planes and waits for its
-// first loads), at least 4 planes per chunk.
-__host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A, int nblocks)
+__host__ __device__ inline SpmvPlan spmv_plan(const OpDev& A)
 {
     SpmvPlan P;
     P.tiles_x = (A.nx + kSpTW - 1) / kSpTW;
     P.tiles = (int64_t)P.tiles_x * ((A.ny + kSpTY - 1) / kSpTY);
-    int64_t chunks = ((int64_t)nblocks + P.tiles - 1) / P.tiles;
-    const int64_t maxc = A.nz / 4 > 1 ? A.nz / 4 : 1;
-    if (chunks > maxc) chunks = maxc;
-    if (chunks < 1) chunks = 1;
-    P.kc = (int)((A.nz + chunks - 1) / chunks);
-    chunks = (A.nz + P.kc - 1) / P.kc;
-    P.items = P.tiles * chunks;
     return P;
 }
+
+// Share b of nshares: the pairs [next, last) of the tile-major order, taken
+// as runs of planes [kb, ke) of one tile each by spmv_next_run.
+struct SpmvShare {
+    int64_t next, last;
+};
+
+__device__ __forceinline__ SpmvShare spmv_share(const OpDev& A, const SpmvPlan& P, int b, int nshares)
+{
+    const int64_t pairs = P.tiles * A.nz;
+    return SpmvShare{pairs * b / nshares, pairs * (b + 1) / nshares};
+}
+
+__device__ __forceinline__ void spmv_next_run(const OpDev& A, SpmvShare& sh, int64_t& tile, int& kb, int& ke)
+{
+    tile = sh.next / A.nz;
+    kb = (int)(sh.next % A.nz);
+    ke = sh.last - sh.next < (int64_t)(A.nz - kb) ? kb + (int)(sh.last - sh.next) : A.nz;
+    sh.next += ke - kb;
+}
+
+// The share count of the staged SpMV for a system of nblocks blocks: the
+// TMA-staged blocks resident on the device at once, at most nblocks (host).
+int spmv_shares(int nblocks);
 
 // q for one thread's 2 x 2 points of a plane from their values B (below), C
 // (at), A (above), the row below the first row and above the last, and the x
@@ -203,7 +221,7 @@ __device__ __forceinline__ void spmv_points(const long long (&B)[2][2], const lo
         }
 }
 
-// One work item: q = A p on the tile's planes [kb, ke), returning this
+// One run: q = A p on the tile's planes [kb, ke), returning this
 // thread's share of p.q.  CONV: the exact-sum form (emax = p's largest
 // exponent field); otherwise FP64 arithmetic on raw values.
 template <bool CONV>
@@ -355,19 +373,18 @@ __device__ __forceinline__ double spmv_item(const OpDev& A, const double* __rest
     return pq;
 }
 
-// The matrix-free SpMV of a block over its work items; returns the thread's p.q.
-__device__ __forceinline__ double spmv_stencil_blocks(const OpDev& A, const double* __restrict__ p,
-                                                      double* __restrict__ q, int emax, int local,
-                                                      int nblocks)
+// The matrix-free SpMV of share b of nshares; returns the thread's p.q.
+__device__ __forceinline__ double spmv_stencil_share(const OpDev& A, const double* __restrict__ p,
+                                                     double* __restrict__ q, int emax, int b, int nshares)
 {
     __shared__ __align__(16) long long buf[2 * kSpPlane];
-    const SpmvPlan P = spmv_plan(A, nblocks);
+    const SpmvPlan P = spmv_plan(A);
     double pq = 0.0;
     const bool conv = cg_xs_ok(emax);
-    for (int64_t item = local; item < P.items; item += nblocks) {
-        const int64_t tile = item % P.tiles;
-        const int kb = (int)(item / P.tiles) * P.kc;
-        const int ke = min(kb + P.kc, A.nz);
+    for (SpmvShare sh = spmv_share(A, P, b, nshares); sh.next < sh.last;) {
+        int64_t tile;
+        int kb, ke;
+        spmv_next_run(A, sh, tile, kb, ke);
         pq += conv ? spmv_item<true>(A, p, q, emax, P, tile, kb, ke, buf)
                    : spmv_item<false>(A, p, q, emax, P, tile, kb, ke, buf);
     }
@@ -375,17 +392,17 @@ __device__ __forceinline__ double spmv_stencil_blocks(const OpDev& A, const doub
 }
 
 // SpMV kernels, chosen per operator on the host: the matrix-free operator is
-// staged (exact-sum form) when its grid gives every block at least one (tile,
-// chunk) item of 4 or more planes, and runs row by row on the FP64 pipe
+// staged (exact-sum form) when a system of nblocks blocks has at least 4
+// (tile, plane) pairs per block, and runs row by row on the FP64 pipe
 // otherwise -- a rule of the operator and the block count only, so a batch
 // and a single solve pick the same kernel.  Separate kernels keep the staged
-// kernel's 64 registers from lowering the others' occupancy.
+// kernel's registers from lowering the others' occupancy.
 enum SpmvMode { SP_ROWS = 0, SP_CSR = 1, SP_STAGED = 2 };
 
 __host__ __device__ inline int spmv_mode(const OpDev& A, int nblocks)
 {
     if (A.kind == HS_OP_CSR) return SP_CSR;
-    const SpmvPlan P = spmv_plan(A, nblocks);
+    const SpmvPlan P = spmv_plan(A);
     return P.tiles * (A.nz / 4) >= nblocks ? SP_STAGED : SP_ROWS;
 }
 
@@ -478,12 +495,13 @@ struct CgMixed;   // mixed-precision state (cg_mixed.cu)
 
 // The TMA-staged form of the SP_STAGED SpMV (cg_spmv_tma.cu) for single
 // solves: eligible when nx is even and p, q are 16-byte aligned; the tensor
-// map spans p (spmv_tma_map returns 0 on success).  spmv_tma_launch leaves
-// the launch check and count to its caller.
+// map spans p (spmv_tma_map returns 0 on success).  spmv_tma_launch runs
+// nshares blocks (spmv_shares of the system's block count) and leaves the
+// launch check and count to its caller.
 bool spmv_tma_eligible(const OpDev& A, const double* p, const double* q, int nblocks);
 int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p);
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
-                    int nblocks, cudaStream_t stream);
+                    int nshares, cudaStream_t stream);
 
 int check_op(const hs_op* A);
 OpDev to_dev(const hs_op* A);

@@ -3,11 +3,15 @@
 // q = 6p - sum of the six face neighbours, Dirichlet zeros outside the box).
 //
 // The same work as the staged kernel of cg_common.cuh, in the same order and
-// with the same arithmetic: a block of 128 threads owns a 64 x 8 tile of one
-// z-chunk at a time, every thread two consecutive x points in each of two
-// adjacent rows, work items (tile, chunk) taken in the order spmv_plan gives.  q and every
-// thread's share of p.q therefore come out bit for bit as there, so a single
-// solve (this kernel) and a batched solve (the staged kernel) still agree.
+// with the same arithmetic: a block of 128 threads owns a 64 x 8 tile for a
+// run of z-planes at a time, every thread two consecutive x points in each of
+// two adjacent rows, block b taking share b of the (tile, plane) pairs as
+// spmv_share and spmv_next_run give them.  The grid is one resident wave: spmv_shares()
+// blocks (760 at five per SM), every block the same bytes to within a plane
+// (fixed 26-plane items for 1216 blocks left a second wave on part of the
+// GPU: 71.4 us at 256^3).  q and every thread's share of p.q therefore come
+// out bit for bit as in the staged kernel, so a single solve (this kernel)
+// and a batched solve (the staged kernel) still agree.
 //
 // What differs is how p arrives: each plane of the tile with its one-point
 // halo is one 3-D tiled TMA box, (8 + 2) rows of 68 doubles starting 16 bytes
@@ -199,14 +203,14 @@ __global__ void __launch_bounds__(kSpBlock, 5)
     if (s_done) return;
     const int emax = cg_pemax(S);
     const bool conv = cg_xs_ok(emax);
-    const SpmvPlan P = spmv_plan(A, gridDim.x);
+    const SpmvPlan P = spmv_plan(A);
     uint32_t seq = 0;
     bool aborted = false, drained = true;
     double pq = 0.0;
-    for (int64_t item = blockIdx.x; item < P.items; item += gridDim.x) {
-        const int64_t tile = item % P.tiles;
-        const int kb = (int)(item / P.tiles) * P.kc;
-        const int ke = min(kb + P.kc, A.nz);
+    for (SpmvShare sh = spmv_share(A, P, blockIdx.x, gridDim.x); sh.next < sh.last;) {
+        int64_t tile;
+        int kb, ke;
+        spmv_next_run(A, sh, tile, kb, ke);
         pq += conv ? spmv_item_tma<true>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained)
                    : spmv_item_tma<false>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained);
         if (aborted) break;   // the same in every thread
@@ -245,10 +249,27 @@ int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p)
 
 // The caller checks and counts the launch, as for the other SpMV kernels.
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
-                    int nblocks, cudaStream_t stream)
+                    int nshares, cudaStream_t stream)
 {
-    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nblocks, kSpBlock, stream, map, A, q, partials, S);
+    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nshares, kSpBlock, stream, map, A, q, partials, S);
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "cg: spmv+dot kernel (TMA-staged)");
+}
+
+// Resident TMA-staged blocks, asked once per process (a single GPU): blocks per
+// SM at the kernel's registers and shared memory, times the SM count.
+int spmv_shares(int nblocks)
+{
+    static const int slots = [] {
+        int per_sm = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv_tma, kSpBlock, 0) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return kNumSMs * kSpMinBlocks;
+        }
+        return per_sm > 0 && sms > 0 ? per_sm * sms : kNumSMs * kSpMinBlocks;
+    }();
+    return nblocks < slots ? nblocks : slots;
 }
 
 }  // namespace hcg

@@ -109,19 +109,19 @@ def check_against_exact_and_oracle(p, q, pq, conv, depth):
 
 def reduction_depth(shape):
     """Longest chain of additions in the fused p.q of any SpMV kernel: a
-    thread's own accumulation (four points per plane of each (tile, chunk) item
-    it takes in the staged kernels, its rows in the row kernel), the block's
-    shuffle tree (8 levels), a thread's share of the partials, and the final
-    tree.  The work split restates the plan the kernels use for cg_run's block
-    count."""
+    thread's own accumulation (four points per plane of its block's share of
+    the (tile, plane) pairs in the staged kernels, plus one addition per run of
+    planes; its rows in the row kernel), the block's shuffle tree (8 levels), a
+    thread's share of the partials, and the final tree.  The staged kernels
+    split the pairs into as many shares as blocks of theirs are resident at
+    once, at most cg_run's block count and at least one block per SM: the
+    bound takes the fewest shares, so the longest chain."""
     nz, ny, nx = shape
     n = nx * ny * nz
     grid = max(1, min(-(-n // 256), 152 * 8))
     tiles = -(-nx // 64) * -(-ny // 8)
-    chunks = max(1, min(-(-grid // tiles), max(nz // 4, 1)))
-    kc = -(-nz // chunks)
-    items = tiles * -(-nz // kc)
-    chain = max(4 * kc * -(-items // grid), -(-n // (grid * 256)))
+    share = -(-(tiles * nz) // min(grid, 152))
+    chain = max(4 * share + -(-share // nz) + 1, -(-n // (grid * 256)))
     return chain + 8 + -(-grid // 128) + 8
 
 
