@@ -75,13 +75,15 @@ HEAT_MODES = {
 #  * CG per unknown and iteration: SpMV 16 B (read p, write q), x/r update 48 B
 #    (read x, p, r, q; write x, r), p update 24 B (read r, p; write p) = 88 B
 #    matrix-free; CSR adds 12 B per stored entry and 4 B of row pointer per row;
-#  * mixed-precision CG per inner iteration and unknown: FP32 SpMV 8 B (+ 8 B per
-#    entry and 4 B per row for CSR), update 24 B, p update 12 B; per refinement:
+#  * mixed-precision CG per inner iteration and unknown: matrix-free (nx a multiple
+#    of 4), the p update folded into the SpMV 16 B (read r, p; write p', q) and the
+#    update 24 B = 40 B; CSR: SpMV 8 B + 8 B per entry and 4 B per row, update 24 B,
+#    p update 12 B; per refinement:
 #    FP64 SpMV 16 B (+ 12 B per entry, 4 B per row for CSR), residual 36 B
 #    (read b, A x; write r in FP64 and r, p, d in FP32), correction 20 B.
 VK_FP64_OPS_PER_LUP = 2    # FP64 variable-kappa update, exact-sum form: u + dt f, then one FMA
 CG_BYTES_PER_ROW = 88
-MIXED_INNER_BYTES_PER_ROW = 44
+MIXED_INNER_BYTES_PER_ROW = {"matrix_free": 40, "csr": 44}
 MIXED_REFINE_BYTES_PER_ROW = 72
 
 
@@ -753,7 +755,7 @@ def run_ours(args):
                 nrow = float(m) ** 3
                 csr_inner = (8.0 * nnz + 4 * nrow) if kind == "csr" else 0.0
                 csr_ref = (12.0 * nnz + 4 * nrow) if kind == "csr" else 0.0
-                nbytes = (im["iters"] * (MIXED_INNER_BYTES_PER_ROW * nrow + csr_inner)
+                nbytes = (im["iters"] * (MIXED_INNER_BYTES_PER_ROW[kind] * nrow + csr_inner)
                           + (im["refinements"] + 1) * (MIXED_REFINE_BYTES_PER_ROW * nrow + csr_ref))
                 mixed[kind] = {"ms_per_solve": ms, "inner_iters": im["iters"],
                                "refinements": im["refinements"], "relres_true": im["relres_true"],

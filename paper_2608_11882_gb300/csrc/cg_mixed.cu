@@ -70,8 +70,11 @@ struct hcg::CgMixed {
     MxScalars* S_host;   // host mirror
     double inner_rtol;
     int32_t max_inner;
-    bool tma;            // the matrix-free SpMV stages p by TMA (nx a multiple of 4)
-    CUtensorMap pmap;    // TMA map of p (unpadded nx x ny x nz floats)
+    bool tma;            // the matrix-free SpMV stages r and p by TMA (nx a multiple of 4)
+    float* p2;           // with tma: the second p buffer (p' goes to the other one)
+    int pcur;            // with tma: which of p, p2 holds the current direction
+    CUtensorMap rmap;    // TMA maps of r, p and p2 (unpadded nx x ny x nz floats)
+    CUtensorMap pmaps[2];
 };
 
 namespace hcg {
@@ -201,6 +204,7 @@ __global__ void __launch_bounds__(kCgBlock)
         if (rr_tot > 0.0 && need * need / rr_tot > f2) f2 = need * need / rr_tot;
         S->inner_stop = f2 * rho_tot;
         S->inner_done = 0;
+        S->beta = 0.0;   // the first direction of the inner solve is r itself
         S->outer_done = (S->zero_rhs || sqrt(rr_tot) / S->bnorm <= S->rtol) ? 1 : 0;
         if (S->outer_done || rho_tot == 0.0) S->inner_done = 1;
     }
@@ -275,25 +279,37 @@ __global__ void __launch_bounds__(kCgBlock)
     }
 }
 
-// The matrix-free FP32 SpMV with the planes of p staged by TMA: a block of 256
-// threads (8 warps) owns a tile of 128 x 8 points of the grid -- every lane
-// four consecutive x points of one row, one 16-byte vector -- and a chunk of
-// z-planes at a time, work items (tile, chunk) taken in a fixed order.  Each
-// plane of the tile with its one-point halo is one TMA box of (8 + 2) rows of
-// 136 floats starting 16 bytes left of the tile, over the unpadded vector, so
-// boxes that reach past the grid read zeros (the Dirichlet boundary).  Boxes
-// land in a ring of kMxNst stages up to kMxNst - 2 planes ahead of use; a
-// thread keeps its values at k-1, k and k+1 in registers and reads the rest
-// from the stage of plane k.  q = fma(6, p, -(((zm + ym) + (xm + xp)) + (yp +
-// zp))) point by point, as in the column kernel, so q is the same bit for bit.
+// The matrix-free FP32 SpMV with the direction update folded in, r and p staged
+// by TMA: it forms p' = r + beta p (the p update of the iteration before) and
+// q = A p' in one pass, so p is read once and written once per iteration
+// instead of twice, and the iteration runs two kernels instead of three.
+// Because blocks read the halo planes, rows and columns of their tiles, p' goes
+// to the other of two p buffers (p_old stays intact for every block).  A block
+// of 256 threads (8 warps) owns a tile of 128 x 8 points of the grid -- every
+// lane four consecutive x points of one row, one 16-byte vector -- and a chunk
+// of z-planes at a time, work items (tile, chunk) taken in a fixed order.  Each
+// plane of the tile with its one-point halo is two TMA boxes (r and p_old) of
+// (8 + 2) rows of 136 floats starting 16 bytes left of the tile, over the
+// unpadded vectors, so boxes that reach past the grid read zeros and give p' = 0
+// there (the Dirichlet boundary).  Boxes land in a ring of kMxNst stages up to
+// kMxNst - 2 planes ahead of use; once a plane lands, each thread forms p' in
+// place for its own vector (warps 0-1 also the halo rows, warp 2 the halo
+// columns) and keeps its own values at k-1, k and k+1 in registers; the other
+// neighbours are read from the stage of plane k after the block barrier.  p' =
+// fma(beta, p, r) and q = fma(6, p', -(((zm + ym) + (xm + xp)) + (yp + zp)))
+// point by point, as in the p-update kernel and the column kernel, so p, q and
+// every iterate are the same bit for bit as with the two separate passes.
 // Every mbarrier wait is bounded; one that runs out stops the inner solve
 // (inner_done 3) after the block's loads in flight have landed (4 if they do
-// not in time).
-constexpr int kMxTW = 128, kMxTY = 8, kMxD = 4, kMxBW = 136, kMxNst = 6;
+// not in time).  Measured at 256^3 before the fold: 30.0 us per SpMV and
+// 141.8-142.9 ms per solve; one resident wave of equal shares instead of the
+// fixed items was slower (144.1-144.5 ms: this launch is short and latency-bound).
+constexpr int kMxTW = 128, kMxTY = 8, kMxD = 4, kMxBW = 136, kMxNst = 4;
 constexpr uint32_t kMxBoxBytes = (kMxTY + 2) * kMxBW * sizeof(float);
 constexpr int kMxStage = (int)((kMxBoxBytes + 127) / 128 * 128 / sizeof(float));
 static_assert(kMxBW * sizeof(float) % 16 == 0 && kMxD * sizeof(float) == 16, "TMA box geometry");
 static_assert(kMxTY * 32 == kCgBlock, "one warp per tile row");
+static_assert(2 * kMxTY <= 32, "one warp forms the halo columns");
 
 struct MxPlan {
     int64_t tiles, items;
@@ -316,15 +332,16 @@ __host__ __device__ inline MxPlan mx_plan(const OpDev32& A, int nblocks)
 }
 
 __global__ void __launch_bounds__(kCgBlock)
-    k_mx_spmv_tma(const __grid_constant__ CUtensorMap map, OpDev32 A, float* __restrict__ q,
-                  double* partials, MxScalars* S)
+    k_mx_spmv_tma(const __grid_constant__ CUtensorMap rmap, const __grid_constant__ CUtensorMap pmap,
+                  OpDev32 A, float* __restrict__ pn, float* __restrict__ q, double* partials, MxScalars* S)
 {
-    __shared__ __align__(128) float stage[kMxNst * kMxStage];
+    // stage sl: the r box at 2 sl, the p box (p' once formed) at 2 sl + 1
+    __shared__ __align__(128) float stage[kMxNst * 2 * kMxStage];
     __shared__ __align__(8) uint64_t bars[kMxNst];
     __shared__ double sh[kCgBlock / 32];
     __shared__ int32_t s_done;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    grid_dependency_wait();   // p, the scalars and the stop flag come from the kernels before
+    grid_dependency_wait();   // r, p, the scalars and the stop flag come from the kernels before
     if (tid == 0) {
         s_done = *(volatile int32_t*)&S->inner_done;
         for (int sl = 0; sl < kMxNst; ++sl) mbar_init(&bars[sl], 1);
@@ -332,9 +349,17 @@ __global__ void __launch_bounds__(kCgBlock)
     }
     __syncthreads();
     if (s_done) return;
+    const float beta = (float)S->beta;
     const MxPlan P = mx_plan(A, gridDim.x);
     const int nx = A.nx, ny = A.ny;
     const int64_t sxy = (int64_t)nx * ny;
+    // this thread's vector in a box, and the halo it forms besides
+    const int own = (ty + 1) * kMxBW + kMxD + 4 * tx;
+    int hvec = -1, hone = -1;
+    if (ty < 2)
+        hvec = (ty == 0 ? 0 : kMxTY + 1) * kMxBW + kMxD + 4 * tx;
+    else if (ty == 2 && tx < 2 * kMxTY)
+        hone = tx < kMxTY ? (tx + 1) * kMxBW + kMxD - 1 : (tx - kMxTY + 1) * kMxBW + kMxD + kMxTW;
     uint32_t seq = 0;   // planes staged so far: plane j of the block sits in slot j % NST
     bool bad = false, aborted = false, drained = true;
     int issued = 0, np = 0;
@@ -344,7 +369,6 @@ __global__ void __launch_bounds__(kCgBlock)
         const int kb = (int)(item / P.tiles) * P.kc, ke = min(kb + P.kc, A.nz);
         const int x0 = (int)(tile % P.tiles_x) * kMxTW, y0 = (int)(tile / P.tiles_x) * kMxTY;
         const int X = x0 + 4 * tx, Y = y0 + ty;
-        const int own = (ty + 1) * kMxBW + kMxD + 4 * tx;
         const int nvalid = Y < ny ? min(4, nx - X) : 0;   // nx % 4 == 0: 4 or none
         np = ke - kb + 2;                                // planes kb-1 .. ke
         issued = 0;
@@ -352,31 +376,57 @@ __global__ void __launch_bounds__(kCgBlock)
             const uint32_t g = seq + (uint32_t)j;
             if (!mbar_wait_bounded(&bars[g % kMxNst], (g / kMxNst) & 1u)) bad = true;
         };
+        auto issue = [&](int j) {   // plane kb - 1 + j into its slot (thread 0)
+            const int sl = (int)((seq + j) % kMxNst);
+            mbar_arrive_expect_tx(&bars[sl], 2 * kMxBoxBytes);
+            tma_load_3d(stage + 2 * sl * kMxStage, &rmap, x0 - kMxD, y0 - 1, kb - 1 + j, &bars[sl]);
+            tma_load_3d(stage + (2 * sl + 1) * kMxStage, &pmap, x0 - kMxD, y0 - 1, kb - 1 + j, &bars[sl]);
+        };
         if (tid == 0) {
-            for (; issued < kMxNst && issued < np; ++issued) {
-                const int sl = (int)((seq + issued) % kMxNst);
-                mbar_arrive_expect_tx(&bars[sl], kMxBoxBytes);
-                tma_load_3d(stage + sl * kMxStage, &map, x0 - kMxD, y0 - 1, kb - 1 + issued, &bars[sl]);
-            }
+            fence_proxy_async_smem();   // the slots were last written by this block's threads
+            for (; issued < kMxNst && issued < np; ++issued) issue(issued);
         }
-        auto ld4 = [&](int j, float (&o)[4]) {
-            const float4 v = *reinterpret_cast<const float4*>(stage + ((seq + j) % kMxNst) * kMxStage + own);
+        // p' = fma(beta, p, r) in place in the p box of plane j; o: this thread's vector
+        auto form = [&](int j, float (&o)[4]) {
+            const int sl = (int)((seq + j) % kMxNst);
+            const float* rb = stage + 2 * sl * kMxStage;
+            float* pb = stage + (2 * sl + 1) * kMxStage;
+            auto vec = [&](int at) {
+                const float4 rv = *reinterpret_cast<const float4*>(rb + at);
+                float4 pv = *reinterpret_cast<const float4*>(pb + at);
+                pv.x = __fmaf_rn(beta, pv.x, rv.x);
+                pv.y = __fmaf_rn(beta, pv.y, rv.y);
+                pv.z = __fmaf_rn(beta, pv.z, rv.z);
+                pv.w = __fmaf_rn(beta, pv.w, rv.w);
+                *reinterpret_cast<float4*>(pb + at) = pv;
+                return pv;
+            };
+            const float4 v = vec(own);
             o[0] = v.x;
             o[1] = v.y;
             o[2] = v.z;
             o[3] = v.w;
+            if (hvec >= 0) vec(hvec);
+            if (hone >= 0) pb[hone] = __fmaf_rn(beta, pb[hone], rb[hone]);
+            fence_proxy_async_smem();   // before the barrier after which TMA may refill the slot
         };
         float below[4], cur[4], above[4];
         wait(0);
-        ld4(0, below);
+        form(0, below);
         wait(1);
-        ld4(1, cur);
-        float* dst = q + (int64_t)kb * sxy + (int64_t)(Y < ny ? Y : 0) * nx + (X < nx ? X : 0);
+        form(1, cur);
+        if (__syncthreads_or(bad)) {
+            aborted = true;
+            break;
+        }
+        const int64_t at = (int64_t)kb * sxy + (int64_t)(Y < ny ? Y : 0) * nx + (X < nx ? X : 0);
+        float* dst = q + at;
+        float* dstp = pn + at;
         for (int k = kb; k < ke; ++k) {
             const int j = k - kb + 1;   // plane k is plane j of the item
             wait(j + 1);
-            ld4(j + 1, above);
-            const float* pc = stage + ((seq + j) % kMxNst) * kMxStage + own;
+            form(j + 1, above);
+            const float* pc = stage + (2 * ((seq + j) % kMxNst) + 1) * kMxStage + own;
             const float4 ymv = *reinterpret_cast<const float4*>(pc - kMxBW);
             const float4 ypv = *reinterpret_cast<const float4*>(pc + kMxBW);
             const float ym[4] = {ymv.x, ymv.y, ymv.z, ymv.w}, yp[4] = {ypv.x, ypv.y, ypv.z, ypv.w};
@@ -390,10 +440,12 @@ __global__ void __launch_bounds__(kCgBlock)
                 qv[i] = __fmaf_rn(6.0f, cur[i], -sum);
             }
             if (nvalid == 4) {
+                *reinterpret_cast<float4*>(dstp) = make_float4(cur[0], cur[1], cur[2], cur[3]);
                 *reinterpret_cast<float4*>(dst) = make_float4(qv[0], qv[1], qv[2], qv[3]);
                 pq.add4(cur[0], qv[0], cur[1], qv[1], cur[2], qv[2], cur[3], qv[3]);
             }
             dst += sxy;
+            dstp += sxy;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 below[i] = cur[i];
@@ -405,9 +457,8 @@ __global__ void __launch_bounds__(kCgBlock)
             }
             // the slot of plane k-1 is free: every thread is past its last use
             if (tid == 0 && issued < np) {
-                const int sl = (int)((seq + issued) % kMxNst);
-                mbar_arrive_expect_tx(&bars[sl], kMxBoxBytes);
-                tma_load_3d(stage + sl * kMxStage, &map, x0 - kMxD, y0 - 1, kb - 1 + issued, &bars[sl]);
+                fence_proxy_async_smem();
+                issue(issued);
                 ++issued;
             }
         }
@@ -533,6 +584,7 @@ void cg_mixed_release(CgMixed* m, cudaStream_t s)
     dev_free(m->d, s);
     dev_free(m->r, s);
     dev_free(m->p, s);
+    dev_free(m->p2, s);
     dev_free(m->q, s);
     dev_free(m->val32, s);
     dev_free(m->partials, s);
@@ -577,7 +629,8 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
     for (;;) {
         int rc = launch_apply(c->A, x, m->q64, c->stream);   // A x in FP64
         if (rc != HS_OK) return rc;
-        k_mx_residual<<<G, kCgBlock, 0, c->stream>>>(n, b, m->q64, m->r64, m->r, m->p, m->d,
+        k_mx_residual<<<G, kCgBlock, 0, c->stream>>>(n, b, m->q64, m->r64, m->r,
+                                                    m->tma && m->pcur ? m->p2 : m->p, m->d,
                                                     m->partials, m->S);
         HS_CHECK_LAUNCH("cg mixed: residual kernel");
         HS_TRY_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(MxScalars), cudaMemcpyDeviceToHost, c->stream),
@@ -601,11 +654,21 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
             for (int32_t t = 0; t < todo; ++t) {
                 // dependent launches: each kernel's launch overlaps the previous
                 // kernel's final reduction (it waits for that kernel on entry)
-                if (m->tma)
-                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->pmap,
-                                                 m->A32, m->q, m->partials, m->S),
+                if (m->tma) {
+                    // p' = r + beta p into the other buffer, q = A p', then the update
+                    float* pn = m->pcur ? m->p : m->p2;
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->rmap,
+                                                 m->pmaps[m->pcur], m->A32, pn, m->q, m->partials, m->S),
                                 "cg mixed: kernel launch");
-                else if (c->A.kind == HS_OP_STENCIL7)
+                    HS_CHECK_LAUNCH("cg mixed: p update + spmv + dot kernel");
+                    HS_TRY_CUDA(launch_dependent(k_mx_update, G, kCgBlock, c->stream, n, m->d, m->r,
+                                                 (const float*)pn, (const float*)m->q, m->partials, m->S),
+                                "cg mixed: kernel launch");
+                    HS_CHECK_LAUNCH("cg mixed: update kernel");
+                    m->pcur ^= 1;
+                    continue;
+                }
+                if (c->A.kind == HS_OP_STENCIL7)
                     HS_TRY_CUDA(launch_dependent(k_mx_spmv_dot<HS_OP_STENCIL7>, G, kCgBlock, c->stream, m->A32,
                                                  (const float*)m->p, m->q, m->partials, m->S),
                                 "cg mixed: kernel launch");
@@ -738,14 +801,31 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
     m->A32.rowptr = c->A.rowptr;
     m->A32.col = c->A.col;
     m->A32.val = m->val32;
-    // the FP32 matrix-free SpMV stages p by TMA when rows are a 16-byte multiple
+    // the FP32 matrix-free SpMV stages r and p by TMA, with the p update folded in,
+    // when rows are a 16-byte multiple (the vectors start 256-byte aligned)
     m->tma = false;
-    if (m->A32.kind == HS_OP_STENCIL7 && m->A32.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(m->p) & 15) == 0 &&
-        (reinterpret_cast<uintptr_t>(m->q) & 15) == 0) {
-        const int e2 = encode_field_map(&m->pmap, m->p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float),
-                                        (uint64_t)m->A32.nx, (uint64_t)m->A32.ny, (uint64_t)m->A32.nz, kMxBW,
-                                        kMxTY + 2);
-        m->tma = e2 == 0;
+    m->pcur = 0;
+    if (m->A32.kind == HS_OP_STENCIL7 && m->A32.nx % 4 == 0) {
+        e = dev_alloc((void**)&m->p2, sizeof(float) * (size_t)n, s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cg_create_mixed: allocation");
+            cg_destroy(c);
+            return rc;
+        }
+        const float* v[3] = {m->r, m->p, m->p2};
+        CUtensorMap* maps[3] = {&m->rmap, &m->pmaps[0], &m->pmaps[1]};
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; ++i)
+            ok = (reinterpret_cast<uintptr_t>(v[i]) & 15) == 0 &&
+                 encode_field_map(maps[i], const_cast<float*>(v[i]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                  sizeof(float), (uint64_t)m->A32.nx, (uint64_t)m->A32.ny, (uint64_t)m->A32.nz,
+                                  kMxBW, kMxTY + 2) == 0;
+        ok = ok && (reinterpret_cast<uintptr_t>(m->q) & 15) == 0;
+        m->tma = ok;
+        if (!ok) {
+            dev_free(m->p2, s);
+            m->p2 = nullptr;
+        }
     }
     *out = c;
     return HS_OK;
