@@ -71,6 +71,7 @@ struct hcg::CgMixed {
     double inner_rtol;
     int32_t max_inner;
     bool tma;            // the matrix-free SpMV stages r and p by TMA (nx a multiple of 4)
+    int spmv_grid;       // its grid: the blocks resident at once, at most the context's grid
     float* p2;           // with tma: the second p buffer (p' goes to the other one)
     int pcur;            // with tma: which of p, p2 holds the current direction
     CUtensorMap rmap;    // TMA maps of r, p and p2 (unpadded nx x ny x nz floats)
@@ -286,8 +287,10 @@ __global__ void __launch_bounds__(kCgBlock)
 // Because blocks read the halo planes, rows and columns of their tiles, p' goes
 // to the other of two p buffers (p_old stays intact for every block).  A block
 // of 256 threads (8 warps) owns a tile of 128 x 8 points of the grid -- every
-// lane four consecutive x points of one row, one 16-byte vector -- and a chunk
-// of z-planes at a time, work items (tile, chunk) taken in a fixed order.  Each
+// lane four consecutive x points of one row, one 16-byte vector -- and a run of
+// z-planes at a time: the grid is one resident wave of blocks, block b taking
+// the b-th of gridDim.x equal shares of the (tile, plane) pairs in tile-major
+// order (one run of planes, or two at a tile boundary).  Each
 // plane of the tile with its one-point halo is two TMA boxes (r and p_old) of
 // (8 + 2) rows of 136 floats starting 16 bytes left of the tile, over the
 // unpadded vectors, so boxes that reach past the grid read zeros and give p' = 0
@@ -301,9 +304,10 @@ __global__ void __launch_bounds__(kCgBlock)
 // every iterate are the same bit for bit as with the two separate passes.
 // Every mbarrier wait is bounded; one that runs out stops the inner solve
 // (inner_done 3) after the block's loads in flight have landed (4 if they do
-// not in time).  Measured at 256^3 before the fold: 30.0 us per SpMV and
-// 141.8-142.9 ms per solve; one resident wave of equal shares instead of the
-// fixed items was slower (144.1-144.5 ms: this launch is short and latency-bound).
+// not in time).  Measured at 256^3 (solve to 1e-8): before the fold 30.0 us
+// per SpMV and 141.8-142.9 ms per solve (one wave of equal shares was slower
+// there: 144.1-144.5 ms); folded, with 1216 blocks of fixed 14-plane items (1.6
+// waves), 52.8 us per launch and 132.6-132.7 ms; folded, one wave: 131.0 ms.
 constexpr int kMxTW = 128, kMxTY = 8, kMxD = 4, kMxBW = 136, kMxNst = 4;
 constexpr uint32_t kMxBoxBytes = (kMxTY + 2) * kMxBW * sizeof(float);
 constexpr int kMxStage = (int)((kMxBoxBytes + 127) / 128 * 128 / sizeof(float));
@@ -311,25 +315,6 @@ static_assert(kMxBW * sizeof(float) % 16 == 0 && kMxD * sizeof(float) == 16, "TM
 static_assert(kMxTY * 32 == kCgBlock, "one warp per tile row");
 static_assert(2 * kMxTY <= 32, "one warp forms the halo columns");
 
-struct MxPlan {
-    int64_t tiles, items;
-    int tiles_x, kc;
-};
-
-__host__ __device__ inline MxPlan mx_plan(const OpDev32& A, int nblocks)
-{
-    MxPlan P;
-    P.tiles_x = (A.nx + kMxTW - 1) / kMxTW;
-    P.tiles = (int64_t)P.tiles_x * ((A.ny + kMxTY - 1) / kMxTY);
-    int64_t chunks = ((int64_t)nblocks + P.tiles - 1) / P.tiles;
-    const int64_t maxc = A.nz / 4 > 1 ? A.nz / 4 : 1;
-    if (chunks > maxc) chunks = maxc;
-    if (chunks < 1) chunks = 1;
-    P.kc = (int)((A.nz + chunks - 1) / chunks);
-    chunks = (A.nz + P.kc - 1) / P.kc;
-    P.items = P.tiles * chunks;
-    return P;
-}
 
 __global__ void __launch_bounds__(kCgBlock)
     k_mx_spmv_tma(const __grid_constant__ CUtensorMap rmap, const __grid_constant__ CUtensorMap pmap,
@@ -350,8 +335,8 @@ __global__ void __launch_bounds__(kCgBlock)
     __syncthreads();
     if (s_done) return;
     const float beta = (float)S->beta;
-    const MxPlan P = mx_plan(A, gridDim.x);
     const int nx = A.nx, ny = A.ny;
+    const int tiles_x = (nx + kMxTW - 1) / kMxTW;
     const int64_t sxy = (int64_t)nx * ny;
     // this thread's vector in a box, and the halo it forms besides
     const int own = (ty + 1) * kMxBW + kMxD + 4 * tx;
@@ -364,10 +349,16 @@ __global__ void __launch_bounds__(kCgBlock)
     bool bad = false, aborted = false, drained = true;
     int issued = 0, np = 0;
     AccF2 pq;
-    for (int64_t item = blockIdx.x; item < P.items && !aborted; item += gridDim.x) {
-        const int64_t tile = item % P.tiles;
-        const int kb = (int)(item / P.tiles) * P.kc, ke = min(kb + P.kc, A.nz);
-        const int x0 = (int)(tile % P.tiles_x) * kMxTW, y0 = (int)(tile / P.tiles_x) * kMxTY;
+    // this block's share of the (tile, plane) pairs in tile-major order
+    const int64_t pairs = (int64_t)tiles_x * ((ny + kMxTY - 1) / kMxTY) * A.nz;
+    int64_t next = pairs * blockIdx.x / gridDim.x;
+    const int64_t last = pairs * (blockIdx.x + 1) / gridDim.x;
+    while (next < last && !aborted) {
+        const int64_t tile = next / A.nz;
+        const int kb = (int)(next % A.nz);
+        const int ke = last - next < (int64_t)(A.nz - kb) ? kb + (int)(last - next) : A.nz;
+        next += ke - kb;
+        const int x0 = (int)(tile % tiles_x) * kMxTW, y0 = (int)(tile / tiles_x) * kMxTY;
         const int X = x0 + 4 * tx, Y = y0 + ty;
         const int nvalid = Y < ny ? min(4, nx - X) : 0;   // nx % 4 == 0: 4 or none
         np = ke - kb + 2;                                // planes kb-1 .. ke
@@ -423,7 +414,7 @@ __global__ void __launch_bounds__(kCgBlock)
         float* dst = q + at;
         float* dstp = pn + at;
         for (int k = kb; k < ke; ++k) {
-            const int j = k - kb + 1;   // plane k is plane j of the item
+            const int j = k - kb + 1;   // plane k is plane j of the run
             wait(j + 1);
             form(j + 1, above);
             const float* pc = stage + (2 * ((seq + j) % kMxNst) + 1) * kMxStage + own;
@@ -456,6 +447,7 @@ __global__ void __launch_bounds__(kCgBlock)
                 break;
             }
             // the slot of plane k-1 is free: every thread is past its last use
+            // (refilling plane k's slot, one plane earlier, measured no faster)
             if (tid == 0 && issued < np) {
                 fence_proxy_async_smem();
                 issue(issued);
@@ -657,7 +649,7 @@ int cg_run_mixed(hs_cg* c, const void* b_in, void* x_inout, int host_buffers, do
                 if (m->tma) {
                     // p' = r + beta p into the other buffer, q = A p', then the update
                     float* pn = m->pcur ? m->p : m->p2;
-                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, G, kCgBlock, c->stream, m->rmap,
+                    HS_TRY_CUDA(launch_dependent(k_mx_spmv_tma, m->spmv_grid, kCgBlock, c->stream, m->rmap,
                                                  m->pmaps[m->pcur], m->A32, pn, m->q, m->partials, m->S),
                                 "cg mixed: kernel launch");
                     HS_CHECK_LAUNCH("cg mixed: p update + spmv + dot kernel");
@@ -821,6 +813,17 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
                                   sizeof(float), (uint64_t)m->A32.nx, (uint64_t)m->A32.ny, (uint64_t)m->A32.nz,
                                   kMxBW, kMxTY + 2) == 0;
         ok = ok && (reinterpret_cast<uintptr_t>(m->q) & 15) == 0;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_spmv_tma, kCgBlock, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || per_sm < 1 || sms < 1) {
+            rc = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration,
+                           "cg_create_mixed: occupancy of the FP32 SpMV");
+            cg_destroy(c);
+            return rc;
+        }
+        m->spmv_grid = per_sm * sms < G ? per_sm * sms : G;
         m->tma = ok;
         if (!ok) {
             dev_free(m->p2, s);
