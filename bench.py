@@ -72,11 +72,9 @@ HEAT_MODES = {
 #    32 B (FP64) / 16 B (FP32) per update; the FP64 form is bound by the FP64 pipe
 #    at 23 operations per update (per axis 4 additions, a multiply and an FMA for
 #    the face differences; 5 to add dt f and the three scaled differences);
-#  * CG per unknown and iteration: matrix-free (nx even, staged), the p update
-#    folded into the SpMV 32 B (read r, p; write p', q) and the x/r update 48 B
-#    (read x, p, r, q; write x, r) = 80 B; CSR: SpMV 16 B (read p, write q) +
-#    12 B per stored entry and 4 B of row pointer per row, update 48 B, p update
-#    24 B (read r, p; write p) = 88 B per row;
+#  * CG per unknown and iteration: SpMV 16 B (read p, write q), x/r update 48 B
+#    (read x, p, r, q; write x, r), p update 24 B (read r, p; write p) = 88 B
+#    matrix-free; CSR adds 12 B per stored entry and 4 B of row pointer per row;
 #  * mixed-precision CG per inner iteration and unknown: matrix-free (nx a multiple
 #    of 4), the p update folded into the SpMV 16 B (read r, p; write p', q) and the
 #    update 24 B = 40 B; CSR: SpMV 8 B + 8 B per entry and 4 B per row, update 24 B,
@@ -84,7 +82,7 @@ HEAT_MODES = {
 #    FP64 SpMV 16 B (+ 12 B per entry, 4 B per row for CSR), residual 36 B
 #    (read b, A x; write r in FP64 and r, p, d in FP32), correction 20 B.
 VK_FP64_OPS_PER_LUP = 2    # FP64 variable-kappa update, exact-sum form: u + dt f, then one FMA
-CG_BYTES_PER_ROW = {"matrix_free": 80, "csr": 88}
+CG_BYTES_PER_ROW = 88
 MIXED_INNER_BYTES_PER_ROW = {"matrix_free": 40, "csr": 44}
 MIXED_REFINE_BYTES_PER_ROW = 72
 
@@ -610,11 +608,10 @@ def run_ours(args):
     nrow = float(m) ** 3
     cg_roof = {
         "matrix_free": hbm_roofline("CG matrix-free (SpMV + updates, whole solve)",
-                                    it_mf[-1] * CG_BYTES_PER_ROW["matrix_free"] * nrow,
-                                    statistics.median(seg["cg_mf"]), hbm_gbs, peak_kind,
-                                    bytes_per_row_per_iter=CG_BYTES_PER_ROW["matrix_free"]),
+                                    it_mf[-1] * CG_BYTES_PER_ROW * nrow, statistics.median(seg["cg_mf"]),
+                                    hbm_gbs, peak_kind, bytes_per_row_per_iter=CG_BYTES_PER_ROW),
         "csr": hbm_roofline("CG CSR (SpMV + updates, whole solve)",
-                            it_csr[-1] * (CG_BYTES_PER_ROW["csr"] * nrow + 12.0 * nnz + 4 * nrow),
+                            it_csr[-1] * (CG_BYTES_PER_ROW * nrow + 12.0 * nnz + 4 * nrow),
                             statistics.median(seg["cg_csr"]), hbm_gbs, peak_kind)}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,

@@ -347,9 +347,8 @@ int op_apply(const hs_op* A, const void* p, void* y, void* stream);
  * p.q (Section 7.5; Algorithm "spmv" (b) for CSR), through exactly one launch
  * of the kernel named by `kernel`, with the block count and work order cg_run
  * uses for A, so q and p.q are bit for bit what that kernel computes inside a
- * solve.  The exact-sum kernels' scale is p's largest exponent, taken from p
- * first, as in a solve's first iteration (whose direction is r0 itself; later
- * iterations bound the scale before p is formed, see cg_run).
+ * solve.  p's scale (its largest exponent, which the exact-sum kernels read)
+ * is taken from p first, as the kernels that form p record it during a solve.
  *   HS_SPMV_AUTO    the kernel cg_run picks for A, p and q;
  *   HS_SPMV_ROWS    one row per thread in FP64 arithmetic (matrix-free: the
  *                   sum ((zm + ym) + (xm + xp)) + (yp + zp), then
@@ -373,9 +372,7 @@ int cg_spmv(const hs_op* A, const void* p, void* q, int kernel, double* pq, void
 /* Create a CG context: checks A, takes a device copy of A's arrays when
  * A->host == 1 (otherwise it keeps A's device pointers, which must outlive
  * the context), and allocates the workspace (r, p, q, reduction partials and
- * device scalars, and for a matrix-free operator whose solve stages p by TMA
- * a second direction buffer, so the SpMV can form p itself: n more FP64
- * values).  Errors: HS_EINVAL, HS_ENOMEM, HS_ECUDA. */
+ * device scalars).  Errors: HS_EINVAL, HS_ENOMEM, HS_ECUDA. */
 int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
 
 /* Solve A x = b by unpreconditioned FP64 CG (textbook form, Section 7.5):
@@ -388,19 +385,14 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream);
  * device arrays otherwise.  Dot products
  * accumulate in FP64 in a fixed order, so repeated runs agree bit for bit.
  * For the matrix-free operator the SpMV forms 6p - (sum of the neighbours)
- * exactly in 64-bit fixed point and rounds it once to FP64.  The fixed-point
- * scale is a power of two 2^E no |p| reaches, fixed before p is formed: in the
- * first iteration p's own largest exponent, later that of max|r| + |beta|
- * max|p_prev| (tracked on the device, rounded up) plus one, so at most three
- * binades above p's own unless r and beta p_prev cancel.  Error below
- * 24 2^(E-58) plus
- * one rounding, where FP64 arithmetic rounds about seven times; a scale
- * outside the convertible range (see HS_FP64_PIPE) takes FP64 arithmetic.
- * op_apply always computes in FP64.  On grids large enough for the
- * shared-memory-staged SpMV, an even nx lets the kernel stage p by TMA and,
- * with the context's second direction buffer, form p = r + beta p_prev itself
- * in place of a separate p update (same results bit for bit; a bounded wait in
- * it that runs out stops the solve with HS_ETIMEOUT).
+ * exactly in 64-bit fixed point on p's current scale (its largest exponent,
+ * tracked on the device) and rounds it once to FP64 -- error below
+ * 24 2^-57 max|p| plus one rounding, where FP64 arithmetic rounds about seven
+ * times; a p whose exponents fall outside the convertible range (see
+ * HS_FP64_PIPE) takes FP64 arithmetic.  op_apply always computes in FP64.
+ * On grids large enough for the shared-memory-staged SpMV, an even nx lets
+ * the kernel stage p by TMA (same results bit for bit; a bounded wait in it
+ * that runs out stops the solve with HS_ETIMEOUT).
  * Synchronises the stream.  Returns HS_OK when converged, HS_ENOCONV when
  * max_iter iterations ran without reaching rtol (x and info are still
  * filled), or an error code.  info may be NULL. */
@@ -454,11 +446,8 @@ int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_it
  * example a serving loop that reserved its device memory up front and must
  * not let cudaMalloc/cudaFree synchronise the device under its other streams,
  * or code running under another framework's memory manager or fixed budget.
- * Same arguments and the same results as cg_solve, bit for bit, and the same
- * kernels except one: having no second direction buffer, it runs the p update
- * as its own kernel where cg_solve folds it into the TMA-staged SpMV (same
- * arithmetic, same scale).  It calls no cudaMalloc, cudaFree, cudaMallocHost
- * or other allocating routine.  The
+ * Same arguments, same kernels and the same results as cg_solve; it calls no
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.  The
  * solver's scratch (r, p, q, reduction partials, device scalars) lives in one
  * fixed array of about 50 MB inside the library, which every GPU that loads
  * the library holds until the process exits.

@@ -57,8 +57,7 @@ __global__ void __launch_bounds__(kCgBlock)
     }
     const double rr_blk = block_sum<kCgBlock>(rr, sh);
     const double bb_blk = block_sum<kCgBlock>(bb, sh);
-    // p0 = r0: iteration 0's direction and residual
-    if (track_pmax) cg_fold_max(pm, S->pmax, S->rmax, 0, blockIdx.x == 0);
+    if (track_pmax) cg_fold_pmax(pm, S, 0, blockIdx.x == 0);   // p0 = r0: iteration 0's direction
     // two partial arrays: [0, G) for r.r and [G, 2G) for b.b
     if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = bb_blk;
     if (!arrive_last(rr_blk, partials, &S->ticket)) return;
@@ -121,7 +120,7 @@ __global__ void __launch_bounds__(kSpBlock, kSpMinBlocks)
     grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kSpBlock / 32];
-    const double pq = spmv_stencil_share(A, p, q, cg_bound_emax(S), blockIdx.x, gridDim.x);
+    const double pq = spmv_stencil_share(A, p, q, cg_pemax(S), blockIdx.x, gridDim.x);
     allow_dependents();
     const double blk = block_sum<kSpBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
@@ -138,23 +137,19 @@ __global__ void __launch_bounds__(kSpBlock, kSpMinBlocks)
 }
 
 // x += alpha p, r -= alpha q fused with r.r; the last block tests convergence
-// and forms beta.  With track_rmax, the new residual's largest |r| goes to the
-// next iteration's slot (the matrix-free SpMV bounds its direction with it).
-__global__ void __launch_bounds__(kCgBlock, 4)
+// and forms beta.
+__global__ void __launch_bounds__(kCgBlock)
     k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                 const double* __restrict__ p, const double* __restrict__ q, double* partials,
-                CgScalars* S, int track_rmax)
+                CgScalars* S)
 {
     grid_dependency_wait();
     if (*(volatile int32_t*)&S->done) return;
     __shared__ double sh[kCgBlock / 32];
     const double alpha = S->alpha;
-    const int it = S->iters;   // read before the last block counts this iteration
-    unsigned rm;
     const double rr = cg_update_rows(n, x, r, p, q, alpha, (int64_t)blockIdx.x * kCgBlock + threadIdx.x,
-                                     (int64_t)gridDim.x * kCgBlock, rm);
+                                     (int64_t)gridDim.x * kCgBlock);
     allow_dependents();
-    if (track_rmax) cg_fold_max(rm, S->rmax, nullptr, (it + 1) % 3, blockIdx.x == 0);
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
     const double rho_new = sum_partials(partials, gridDim.x, sh);
@@ -183,12 +178,11 @@ __global__ void __launch_bounds__(kCgBlock)
                                         (int64_t)gridDim.x * kCgBlock);
     allow_dependents();
     // the update kernel has counted this iteration: p is the next one's direction
-    if (track_pmax) cg_fold_max(pm, S->pmax, nullptr, S->iters % 3, blockIdx.x == 0);
+    if (track_pmax) cg_fold_pmax(pm, S, S->iters % 3, blockIdx.x == 0);
 }
 
-// Largest |p| high word into S->pmax[0] and S->rmax[0], for cg_spmv: with
-// beta = 0 the matrix-free SpMV of iteration 0 takes p's own largest exponent
-// field as its scale.
+// Largest |p| high word into S->pmax[0] (the direction's scale the
+// matrix-free SpMV of iteration 0 reads), for cg_spmv.
 __global__ void __launch_bounds__(kCgBlock)
     k_cg_pmax(int64_t n, const double* __restrict__ p, CgScalars* S)
 {
@@ -196,7 +190,7 @@ __global__ void __launch_bounds__(kCgBlock)
     for (int64_t t = (int64_t)blockIdx.x * kCgBlock + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * kCgBlock)
         pm = max(pm, xs_abs_hi(p[t]));
-    cg_fold_max(pm, S->pmax, S->rmax, 0, false);
+    cg_fold_pmax(pm, S, 0, false);
 }
 
 // ||b - q||^2 into S->rr_true (q = A x).
@@ -385,7 +379,6 @@ int cg_destroy(hs_cg_t c)
     if (e != cudaSuccess) rc = cuda_fail(e, "cg_destroy: stream synchronize");
     dev_free(c->r, c->stream);
     dev_free(c->p, c->stream);
-    dev_free(c->p2, c->stream);
     dev_free(c->q, c->stream);
     dev_free(c->partials, c->stream);
     dev_free(c->S, c->stream);
@@ -422,9 +415,6 @@ int cg_create(hs_cg_t* out, const hs_op* A, void* stream)
     CG_ALLOC(c->r, sizeof(double) * n);
     CG_ALLOC(c->p, sizeof(double) * n);
     CG_ALLOC(c->q, sizeof(double) * n);
-    // a second direction buffer where the TMA-staged SpMV can fold the p update in
-    if (c->A.kind == HS_OP_STENCIL7 && spmv_mode(c->A, c->grid) == SP_STAGED && (c->A.nx & 1) == 0)
-        CG_ALLOC(c->p2, sizeof(double) * n);
     CG_ALLOC(c->partials, sizeof(double) * 2 * c->grid);
     CG_ALLOC(c->S, sizeof(CgScalars));
     // the host mirror of the scalars: ordinary memory (pinned memory would
@@ -498,17 +488,10 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
     const int mode = spmv_mode(c->A, c->grid);
     const int track = mode == SP_STAGED;   // the staged SpMV needs p's largest exponent
     const int shares = mode == SP_STAGED ? spmv_shares(c->grid) : c->grid;
-    // the staged SpMV takes p through TMA when the grid and the vectors allow,
-    // and folds in the p update when the context has a second direction buffer:
-    // p_i goes to the buffer p_(i-1) is not in (pbuf[cur ^ 1]), and r by TMA too
-    CUtensorMap pmap, rmap, pmaps[2];
+    // the staged SpMV takes p through TMA when the grid and the vectors allow
+    CUtensorMap pmap;
     const bool tma = mode == SP_STAGED && spmv_tma_eligible(c->A, c->p, c->q, c->grid) &&
                      spmv_tma_map(&pmap, c->A, c->p) == 0;
-    double* pbuf[2] = {c->p, c->p2};
-    const bool fold = tma && c->p2 && spmv_tma_eligible(c->A, c->p2, c->r, c->grid) &&
-                      spmv_tma_map(&rmap, c->A, c->r) == 0 && spmv_tma_map(&pmaps[1], c->A, c->p2) == 0;
-    pmaps[0] = pmap;
-    int cur = 0;   // fold: the buffer of the current direction (the start kernel writes p_0 to c->p)
     k_cg_start<<<c->grid, kCgBlock, 0, c->stream>>>(n, b, c->q, c->r, c->p, c->partials, c->S, track);
     HS_CHECK_LAUNCH("cg: start kernel");
 
@@ -524,18 +507,6 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
         for (int32_t t = 0; t < todo; ++t) {
             // x lives either in the caller's buffer or in the staging buffer
             const int64_t nn = n;
-            if (fold) {
-                double* pn = pbuf[cur ^ 1];
-                rc = spmv_tma_fold_launch(pmaps[cur], rmap, c->A, pn, c->q, c->partials, c->S, shares, c->stream);
-                if (rc != HS_OK) return rc;
-                HS_CHECK_LAUNCH("cg: p update + spmv + dot kernel");
-                HS_TRY_CUDA(launch_dependent(k_cg_update, c->grid, kCgBlock, c->stream, nn, x, c->r,
-                                             (const double*)pn, (const double*)c->q, c->partials, c->S, track),
-                            "cg: kernel launch");
-                HS_CHECK_LAUNCH("cg: update kernel");
-                cur ^= 1;
-                continue;
-            }
             switch (mode) {
             case SP_STAGED:
                 if (tma) {
@@ -556,7 +527,7 @@ int cg_run(hs_cg_t c, const void* b_in, void* x_inout, int host_buffers, double 
             }
             HS_CHECK_LAUNCH("cg: spmv+dot kernel");
             HS_TRY_CUDA(launch_dependent(k_cg_update, c->grid, kCgBlock, c->stream, nn, x, c->r, (const double*)c->p,
-                                   (const double*)c->q, c->partials, c->S, track), "cg: kernel launch");
+                                   (const double*)c->q, c->partials, c->S), "cg: kernel launch");
             HS_CHECK_LAUNCH("cg: update kernel");
             HS_TRY_CUDA(launch_dependent(k_cg_pupdate, c->grid, kCgBlock, c->stream, nn, (const double*)c->r, c->p,
                                    c->S, track), "cg: kernel launch");
@@ -623,14 +594,11 @@ int cg_solve(const hs_op* A, const void* b, void* x, double rtol, int32_t max_it
 // code that runs under another framework's memory manager or inside one of its
 // allocation hooks, where a fresh allocation would fail, fragment the pool or
 // re-enter the allocator; processes held to a fixed device-memory budget.
-// cg_solve_noalloc serves them.  It runs the host loop and kernels of cg_run,
-// with the solver's scratch (r, p, q, the reduction partials and the device
-// scalars) taken from one fixed array in the library's own device memory
-// instead of from cudaMalloc, and its scalar read-backs going through a
-// variable on the caller's stack instead of pinned memory.  Having no second
-// direction buffer, it runs the p update as its own kernel where cg_run folds
-// it into the TMA-staged SpMV; both take the same scale and arithmetic, so the
-// results are the same bit for bit.
+// cg_solve_noalloc serves them.  It runs exactly the kernels and host loop of
+// cg_run, with the solver's scratch (r, p, q, the reduction partials and the
+// device scalars) taken from one fixed array in the library's own device
+// memory instead of from cudaMalloc, and its scalar read-backs going through a
+// variable on the caller's stack instead of pinned memory.
 namespace hcg {
 
 constexpr int64_t kNoAllocMaxN = HS_NOALLOC_MAX_N;          // 2,097,152 unknowns = 128^3

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_start(const SysDev* sys, int n
     }
     const double rr_blk = block_sum<kCgBlock>(rr, sh);
     const double bb_blk = block_sum<kCgBlock>(bb, sh);
-    if (s.mode == SP_STAGED) cg_fold_max(pm, s.S->pmax, s.S->rmax, 0, local == 0);
+    if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, 0, local == 0);
     if (threadIdx.x == 0) s.partials[s.nblocks + local] = bb_blk;
     if (!arrive_last_sys(rr_blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho = sum_partials_n(s.partials, s.nblocks, sh);
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NT, MINB) k_cgb_spmv_dot(const SysDev* sys, in
     const int64_t stride = (int64_t)s.nblocks * NT;
     if (MODE == SP_STAGED) {
         // share `local` of a single solve's launch; the blocks beyond the shares add 0
-        if (local < s.nshares) pq = spmv_stencil_share(s.A, s.p, s.q, cg_bound_emax(s.S), local, s.nshares);
+        if (local < s.nshares) pq = spmv_stencil_share(s.A, s.p, s.q, cg_pemax(s.S), local, s.nshares);
     } else for (int64_t row = row0; row < s.A.n; row += stride) {
         const double qv = MODE == SP_CSR ? apply_csr_row(s.A, s.p, row) : apply_stencil_row(s.A, s.p, row);
         s.q[row] = qv;
@@ -171,12 +171,9 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_update(const SysDev* sys, int 
     if (*(volatile int32_t*)&s.S->done || s.S->iters >= s.max_iter) return;
     __shared__ double sh[kCgBlock / 32];
     const double alpha = s.S->alpha;
-    const int it = s.S->iters;   // read before the last block counts this iteration
-    unsigned rm;
     const double rr = cg_update_rows(s.A.n, s.x, s.r, s.p, s.q, alpha, (int64_t)local * kCgBlock + threadIdx.x,
-                                     (int64_t)s.nblocks * kCgBlock, rm);
+                                     (int64_t)s.nblocks * kCgBlock);
     allow_dependents();
-    if (s.mode == SP_STAGED) cg_fold_max(rm, s.S->rmax, nullptr, (it + 1) % 3, local == 0);
     const double blk = block_sum<kCgBlock>(rr, sh);
     if (!arrive_last_sys(blk, s.partials, &s.S->ticket, local, s.nblocks)) return;
     const double rho_new = sum_partials_n(s.partials, s.nblocks, sh);
@@ -204,7 +201,7 @@ __global__ void __launch_bounds__(kCgBlock) k_cgb_pupdate(const SysDev* sys, int
     const unsigned pm = cg_pupdate_rows(s.A.n, s.r, s.p, beta, (int64_t)local * kCgBlock + threadIdx.x,
                                         (int64_t)s.nblocks * kCgBlock);
     allow_dependents();
-    if (s.mode == SP_STAGED) cg_fold_max(pm, s.S->pmax, nullptr, s.S->iters % 3, local == 0);
+    if (s.mode == SP_STAGED) cg_fold_pmax(pm, s.S, s.S->iters % 3, local == 0);
 }
 
 // ||b - A x||^2 into rr_true (q = A x from k_cgb_apply_x).

@@ -26,13 +26,10 @@ struct CgScalars {
     int32_t iters;
     uint32_t ticket;   // blocks finished in the running reduction
     int32_t zero_rhs;  // ||b|| == 0
-    // Largest |p| and |r| high words (shifted to the top of the bit pattern) of
-    // the direction p_i and the residual r_i in slot i % 3 (matrix-free
-    // operator): the kernel that forms p_i (r_i) folds its values in and clears
-    // slot (i+1) % 3.  The SpMV of iteration i reads r_i's, p_(i-1)'s and beta to
-    // bound p_i = r_i + beta p_(i-1) before it is formed (cg_bound_emax).
+    // Largest |p| bit pattern of the direction p_i in slot i % 3 (matrix-free
+    // operator): the kernel that forms p_i folds its values in and clears slot
+    // (i+1) % 3; the SpMV of iteration i reads slot i % 3.
     unsigned long long pmax[3];
-    unsigned long long rmax[3];
 };
 
 constexpr int kCgBlock = 256;
@@ -111,26 +108,11 @@ __device__ __forceinline__ double apply_row(const OpDev& A, const double* __rest
     return apply_csr_row(A, p, row);
 }
 
-// The fixed-point scale of the direction p_i that the matrix-free SpMV of
-// iteration i converts: an exponent field no value of p_i exceeds, known before
-// p_i = r_i + beta p_(i-1) is formed, so that the SpMV may form p_i itself.
-// With beta = 0 (the first iteration; cg_spmv on its own) p_i = r_i and the
-// field is r_i's largest, exactly; otherwise it is the field of max|r_i| +
-// |beta| max|p_(i-1)|, from high words rounded up and a sum rounded up, plus
-// one -- at most three binades above p_i's own largest unless r_i and
-// beta p_(i-1) cancel.  Every SpMV of a solve (single, batched, with or without the p
-// update folded in) takes this scale, so they agree bit for bit.
-__device__ __forceinline__ int cg_bound_emax(const CgScalars* S)
+// Largest exponent field of the direction p of the current iteration, and
+// whether the matrix-free SpMV may use the exact-sum form for it.
+__device__ __forceinline__ int cg_pemax(const CgScalars* S)
 {
-    const int i = S->iters;
-    const unsigned long long rb = __ldcg(&S->rmax[i % 3]);
-    const double beta = __ldcg(&S->beta);
-    if (beta == 0.0) return (int)(rb >> 52);
-    const unsigned long long pb = __ldcg(&S->pmax[(i + 2) % 3]);
-    const double mr = __longlong_as_double((long long)(rb + (1ull << 32)));
-    const double mp = __longlong_as_double((long long)(pb + (1ull << 32)));
-    const double bound = __fma_ru(fabs(beta), mp, mr);
-    return (int)((unsigned long long)__double_as_longlong(bound) >> 52) + 1;
+    return (int)(__ldcg(&S->pmax[S->iters % 3]) >> 52);
 }
 
 __device__ __forceinline__ bool cg_xs_ok(int emax) { return emax >= kXsEmaxLo && emax <= kXsEmaxHi; }
@@ -434,14 +416,12 @@ __host__ __device__ inline int spmv_mode(const OpDev& A, int nblocks)
 // use these with the same partition, so their dot products add in the same
 // order.
 
-// x += alpha p, r -= alpha q; returns this thread's share of r.r and, in rm,
-// the largest |r| high word of its values.
+// x += alpha p, r -= alpha q; returns this thread's share of r.r.
 __device__ __forceinline__ double cg_update_rows(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                  const double* __restrict__ p, const double* __restrict__ q,
-                                                 double alpha, int64_t t0, int64_t stride, unsigned& rm)
+                                                 double alpha, int64_t t0, int64_t stride)
 {
     double rr = 0.0;
-    rm = 0;
     const int64_t npairs = n >> 1;
     const bool xvec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
     for (int64_t t = t0; t < npairs; t += stride) {
@@ -462,14 +442,12 @@ __device__ __forceinline__ double cg_update_rows(int64_t n, double* __restrict__
         reinterpret_cast<double2*>(r)[t] = rv;
         rr = __fma_rn(rv.x, rv.x, rr);
         rr = __fma_rn(rv.y, rv.y, rr);
-        rm = max(rm, max(xs_abs_hi(rv.x), xs_abs_hi(rv.y)));
     }
     if ((n & 1) && t0 == 0) {
         x[n - 1] = __fma_rn(alpha, p[n - 1], x[n - 1]);
         const double rt = __fma_rn(-alpha, q[n - 1], r[n - 1]);
         r[n - 1] = rt;
         rr = __fma_rn(rt, rt, rr);
-        rm = max(rm, xs_abs_hi(rt));
     }
     return rr;
 }
@@ -496,27 +474,20 @@ __device__ __forceinline__ unsigned cg_pupdate_rows(int64_t n, const double* __r
     return pm;
 }
 
-// Folds a block's largest high word (m, per thread) into slots[slot] -- and
-// into slots2[slot] when slots2 is given -- and, from the system's first block,
-// clears the slot after it.  All NT threads of the block call it.
-template <int NT = kCgBlock>
-__device__ __forceinline__ void cg_fold_max(unsigned m, unsigned long long* slots, unsigned long long* slots2,
-                                            int slot, bool first_block)
+// Folds a block's largest |p| high word (m, per thread) into S->pmax[slot] and,
+// from the system's first block, clears the slot after it.  All threads call it.
+__device__ __forceinline__ void cg_fold_pmax(unsigned m, CgScalars* S, int slot, bool first_block)
 {
-    __shared__ unsigned wmax[NT / 32];
+    __shared__ unsigned wmax[kCgBlock / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned b = 0;
-        for (int w = 0; w < NT / 32; ++w) b = max(b, wmax[w]);
-        atomicMax(&slots[slot], (unsigned long long)b << 32);
-        if (first_block) slots[(slot + 1) % 3] = 0;
-        if (slots2) {
-            atomicMax(&slots2[slot], (unsigned long long)b << 32);
-            if (first_block) slots2[(slot + 1) % 3] = 0;
-        }
+        for (int w = 0; w < kCgBlock / 32; ++w) b = max(b, wmax[w]);
+        atomicMax(&S->pmax[slot], (unsigned long long)b << 32);
+        if (first_block) S->pmax[(slot + 1) % 3] = 0;
     }
 }
 
@@ -531,10 +502,6 @@ bool spmv_tma_eligible(const OpDev& A, const double* p, const double* q, int nbl
 int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p);
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
                     int nshares, cudaStream_t stream);
-// The same with the p update folded in: forms p_i = r_i + beta p_(i-1) from the
-// maps of p_(i-1) and r_i into pn (not p_(i-1)'s buffer), then q = A p_i.
-int spmv_tma_fold_launch(const CUtensorMap& pmap, const CUtensorMap& rmap, const OpDev& A, double* pn,
-                         double* q, double* partials, CgScalars* S, int nshares, cudaStream_t stream);
 
 int check_op(const hs_op* A);
 OpDev to_dev(const hs_op* A);
@@ -550,7 +517,6 @@ struct hs_cg {
     double* r;
     double* p;
     double* q;
-    double* p2;            // the second direction buffer of the folded p update, or NULL
     double* partials;      // 2 * grid doubles
     hcg::CgScalars* S;     // device scalars
     hcg::CgScalars* S_host;  // host mirror of the scalars

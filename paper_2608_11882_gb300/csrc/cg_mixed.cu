@@ -765,8 +765,6 @@ int cg_create_mixed(hs_cg_t* out, const hs_op* A, const hs_cg_mixed_opts* opts, 
     m->q64 = c->q;
     dev_free(c->p, s);
     c->p = nullptr;
-    dev_free(c->p2, s);
-    c->p2 = nullptr;
     if (e == cudaSuccess) e = dev_alloc((void**)&m->partials, sizeof(double) * 3 * (size_t)G, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&m->S, sizeof(MxScalars), s);
     if (e == cudaSuccess) {

@@ -6,9 +6,8 @@
 // with the same arithmetic: a block of 128 threads owns a 64 x 8 tile for a
 // run of z-planes at a time, every thread two consecutive x points in each of
 // two adjacent rows, block b taking share b of the (tile, plane) pairs as
-// spmv_share and spmv_next_run give them.  The grid is one resident wave:
-// spmv_shares() blocks (760 at five per SM), every block the same bytes to
-// within a plane
+// spmv_share and spmv_next_run give them.  The grid is one resident wave: spmv_shares()
+// blocks (760 at five per SM), every block the same bytes to within a plane
 // (fixed 26-plane items for 1216 blocks left a second wave on part of the
 // GPU: 71.4 us at 256^3).  q and every thread's share of p.q therefore come
 // out bit for bit as in the staged kernel, so a single solve (this kernel)
@@ -28,18 +27,6 @@
 // Every thread converts its own four values of each new plane to fixed point in
 // place (and warps 0-2 the halo), so each staged value is converted once.
 //
-// Single solves whose context has a second direction buffer run the folded
-// form: each plane brings an r box besides the p box (of the previous
-// direction), and the conversion first forms p = fma(beta, p_prev, r) -- the
-// p update pass's arithmetic -- so the iteration runs two kernels instead of
-// three and moves 80 bytes per unknown instead of 88.  The new direction goes
-// to the other buffer (other blocks still read the previous one's halo), and
-// its largest |p| to the scalars' slot, as the p update pass would leave them.
-// The scale both forms convert on is fixed before p is formed
-// (cg_bound_emax), so the two agree bit for bit.  Measured at 256^3 (under
-// ncu): 113.7 us per folded launch against 73.1 + 61.6 us for the SpMV and the
-// p update; FP64 pipe 74%, DRAM 67%; live, CG 3856 against 3795 iterations/s.
-//
 // Each mbarrier wait is bounded (about a second); one that runs out marks the
 // solve with done = 3 (HS_ETIMEOUT on the host), waits (bounded) for the
 // block's loads in flight and ends the block.  If that wait runs out as well,
@@ -58,21 +45,14 @@ constexpr int kSpStage = (int)((kSpBoxBytes + 127) / 128 * 128 / sizeof(double))
 static_assert(kSpBW * sizeof(double) % 16 == 0, "TMA box rows are a 16-byte multiple");
 static_assert(kSpD * sizeof(double) == 16, "the box starts 16 bytes left of the tile");
 
-// One run of planes [kb, ke) of a tile.  FOLD: each stage holds the r box
-// (first) and the p box, and the run forms the direction p' = fma(beta, p, r)
-// of every staged value before converting it -- the p update of the iteration
-// before, folded in -- writes its own p' to pn and its largest |p'| high word
-// to pm; otherwise the stage is the p box alone.
-template <bool CONV, bool FOLD>
-__device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CUtensorMap* rmap,
-                                                const OpDev& A, double* __restrict__ q,
-                                                double* __restrict__ pn, double beta, int emax,
-                                                const SpmvPlan& P, int64_t tile, int kb, int ke,
-                                                long long* stage, uint64_t* bars, uint32_t& seq,
-                                                bool& aborted, bool& drained, unsigned& pm)
+template <bool CONV>
+__device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const OpDev& A,
+                                                double* __restrict__ q, int emax, const SpmvPlan& P,
+                                                int64_t tile, int kb, int ke, long long* stage,
+                                                uint64_t* bars, uint32_t& seq, bool& aborted,
+                                                bool& drained)
 {
     constexpr int V = 2, RT = kSpRT, BW = kSpBW, NST = kSpNst;
-    constexpr uint32_t TX = (FOLD ? 2 : 1) * kSpBoxBytes;   // bytes a plane brings
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int nx = A.nx, ny = A.ny;
     const int64_t sxy = (int64_t)nx * ny;
@@ -97,50 +77,23 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
     auto wait = [&](int sl, uint32_t ph) {
         if (!mbar_wait_bounded(&bars[sl], ph)) bad = true;
     };
-    auto pbox = [&](int sl) { return stage + ((FOLD ? 2 : 1) * sl + (FOLD ? 1 : 0)) * kSpStage; };
-    auto rbox = [&](int sl) { return stage + 2 * sl * kSpStage; };
-    auto load = [&](int sl, int plane) {   // thread 0
-        mbar_arrive_expect_tx(&bars[sl], TX);
-        if constexpr (FOLD) tma_load_3d(rbox(sl), rmap, x0 - kSpD, y0 - 1, plane, &bars[sl]);
-        tma_load_3d(pbox(sl), map, x0 - kSpD, y0 - 1, plane, &bars[sl]);
-    };
     auto fix = [&](long long b) -> long long { return CONV ? xs_fix(b, emax) : b; };
-    // the staged value at i of slot sl: p' (FOLD) or p, as raw bits; value2 the
-    // 16-byte aligned pair at i (i even)
-    auto pfold = [&](long long p, long long r) {
-        return __double_as_longlong(__fma_rn(beta, __longlong_as_double(p), __longlong_as_double(r)));
-    };
-    auto value = [&](int sl, int i) -> long long {
-        if constexpr (FOLD) return pfold(pbox(sl)[i], rbox(sl)[i]);
-        return pbox(sl)[i];
-    };
-    auto value2 = [&](int sl, int i) -> longlong2 {
-        const longlong2 pv = *reinterpret_cast<const longlong2*>(pbox(sl) + i);
-        if constexpr (FOLD) {
-            const longlong2 rv = *reinterpret_cast<const longlong2*>(rbox(sl) + i);
-            return make_longlong2(pfold(pv.x, rv.x), pfold(pv.y, rv.y));
-        }
-        return pv;
-    };
-    auto convert = [&](int sl, long long (&fx)[RT][V], double (&raw)[RT][V]) {
-        long long* pl = pbox(sl);
+    auto convert = [&](long long* pl, long long (&fx)[RT][V], double (&raw)[RT][V]) {
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
-            const longlong2 b = value2(sl, own + j * BW);
+            const longlong2 b = *reinterpret_cast<const longlong2*>(pl + own + j * BW);
             raw[j][0] = __longlong_as_double(b.x);
             raw[j][1] = __longlong_as_double(b.y);
             fx[j][0] = fix(b.x);
             fx[j][1] = fix(b.y);
-            if constexpr (FOLD) pm = max(pm, max(xs_abs_hi(raw[j][0]), xs_abs_hi(raw[j][1])));
-            if constexpr (CONV || FOLD)
-                *reinterpret_cast<longlong2*>(pl + own + j * BW) = make_longlong2(fx[j][0], fx[j][1]);
+            if constexpr (CONV) *reinterpret_cast<longlong2*>(pl + own + j * BW) = make_longlong2(fx[j][0], fx[j][1]);
         }
-        if constexpr (CONV || FOLD) {
+        if constexpr (CONV) {
             if (ty < 2) {
-                const longlong2 h = value2(sl, extra);
+                const longlong2 h = *reinterpret_cast<const longlong2*>(pl + extra);
                 *reinterpret_cast<longlong2*>(pl + extra) = make_longlong2(fix(h.x), fix(h.y));
             } else if (extra >= 0) {
-                pl[extra] = fix(value(sl, extra));
+                pl[extra] = fix(pl[extra]);
             }
         }
     };
@@ -148,8 +101,10 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
     int issued = 0;
     if (tid == 0) {
         fence_proxy_async_smem();
-        for (int sl = s0; issued < NST && issued < np; ++issued, sl = sl + 1 == NST ? 0 : sl + 1)
-            load(sl, kb - 1 + issued);
+        for (int sl = s0; issued < NST && issued < np; ++issued, sl = sl + 1 == NST ? 0 : sl + 1) {
+            mbar_arrive_expect_tx(&bars[sl], kSpBoxBytes);
+            tma_load_3d(stage + sl * kSpStage, map, x0 - kSpD, y0 - 1, kb - 1 + issued, &bars[sl]);
+        }
     }
     // the planes below, at and above k (fixed-point values, raw bits when
     // !CONV) and the raw values at and above k
@@ -160,19 +115,17 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
     wait(s_cur, ph_cur);
 #pragma unroll
     for (int j = 0; j < RT; ++j) {
-        const longlong2 b = value2(s_cur, own + j * BW);
+        const longlong2 b = *reinterpret_cast<const longlong2*>(stage + s_cur * kSpStage + own + j * BW);
         B[j][0] = fix(b.x);
         B[j][1] = fix(b.y);
-        if constexpr (FOLD)
-            pm = max(pm, max(xs_abs_hi(__longlong_as_double(b.x)), xs_abs_hi(__longlong_as_double(b.y))));
     }
     if (++s_cur == NST) {
         s_cur = 0;
         ph_cur ^= 1u;
     }
     wait(s_cur, ph_cur);
-    convert(s_cur, C, RC);
-    if constexpr (CONV || FOLD) fence_proxy_async_smem();
+    convert(stage + s_cur * kSpStage, C, RC);
+    if constexpr (CONV) fence_proxy_async_smem();
     // the barriers reduce the threads' wait results, so all agree on an abort
     aborted = __syncthreads_or(bad) != 0;
 
@@ -181,8 +134,8 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
         const int s_nxt = s_cur + 1 == NST ? 0 : s_cur + 1;
         const uint32_t ph_nxt = s_nxt == 0 ? ph_cur ^ 1u : ph_cur;
         wait(s_nxt, ph_nxt);
-        convert(s_nxt, Ab, RA);
-        const long long* pc = pbox(s_cur) + own;
+        convert(stage + s_nxt * kSpStage, Ab, RA);
+        const long long* pc = stage + s_cur * kSpStage + own;
         const long long ym[V] = {pc[-BW], pc[1 - BW]}, yp[V] = {pc[RT * BW], pc[RT * BW + 1]};
         const long long left[RT] = {pc[-1], pc[BW - 1]}, right[RT] = {pc[V], pc[BW + V]};
         double qv[RT][V];
@@ -190,9 +143,8 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
 #pragma unroll
         for (int j = 0; j < RT; ++j)
             if (ok[j]) {
-                const int64_t at = (int64_t)k * sxy + (int64_t)(Y0 + j) * nx + X;
-                *reinterpret_cast<double2*>(q + at) = make_double2(qv[j][0], qv[j][1]);
-                if constexpr (FOLD) *reinterpret_cast<double2*>(pn + at) = make_double2(RC[j][0], RC[j][1]);
+                double* dst = q + (int64_t)k * sxy + (int64_t)(Y0 + j) * nx + X;
+                *reinterpret_cast<double2*>(dst) = make_double2(qv[j][0], qv[j][1]);
                 pq = __fma_rn(RC[j][0], qv[j][0], pq);
                 pq = __fma_rn(RC[j][1], qv[j][1], pq);
             }
@@ -204,12 +156,14 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
                 C[j][i] = Ab[j][i];
                 RC[j][i] = RA[j][i];
             }
-        if constexpr (CONV || FOLD) fence_proxy_async_smem();
+        if constexpr (CONV) fence_proxy_async_smem();
         aborted = __syncthreads_or(bad) != 0;
         // the slot of the plane below is free: every thread is past its last use
         if (!aborted && tid == 0 && issued < np) {
+            const int sl = s_cur == 0 ? NST - 1 : s_cur - 1;
             fence_proxy_async_smem();
-            load(s_cur == 0 ? NST - 1 : s_cur - 1, kb - 1 + issued);
+            mbar_arrive_expect_tx(&bars[sl], kSpBoxBytes);
+            tma_load_3d(stage + sl * kSpStage, map, x0 - kSpD, y0 - 1, kb - 1 + issued, &bars[sl]);
             ++issued;
         }
         s_cur = s_nxt;
@@ -229,20 +183,16 @@ __device__ __forceinline__ double spmv_item_tma(const CUtensorMap* map, const CU
     return pq;
 }
 
-// FOLD: the single-solve form that forms p_i = r_i + beta p_(i-1) itself (from
-// map = p_(i-1) and rmap = r_i, into pn) and folds max|p_i| into the scalars'
-// slot, in place of the p update pass; otherwise map = p_i and rmap is unused.
-template <bool FOLD>
 __global__ void __launch_bounds__(kSpBlock, 5)
-    k_cg_spmv_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap rmap, OpDev A,
-                  double* __restrict__ pn, double* __restrict__ q, double* partials, CgScalars* S)
+    k_cg_spmv_tma(const __grid_constant__ CUtensorMap map, OpDev A, double* __restrict__ q,
+                  double* partials, CgScalars* S)
 {
-    __shared__ __align__(128) long long stage[(FOLD ? 2 : 1) * kSpNst * kSpStage];
+    __shared__ __align__(128) long long stage[kSpNst * kSpStage];
     __shared__ __align__(8) uint64_t bars[kSpNst];
     __shared__ double sh[kSpBlock / 32];
     __shared__ int32_t s_done;
     const int tid = threadIdx.x;
-    grid_dependency_wait();   // p, r, the scalars and the stop flag come from the kernels before
+    grid_dependency_wait();   // p, the scalars and the stop flag come from the kernels before
     if (tid == 0) {
         // one read for the block: another block's abort may change the flag
         s_done = *(volatile int32_t*)&S->done;
@@ -251,23 +201,18 @@ __global__ void __launch_bounds__(kSpBlock, 5)
     }
     __syncthreads();
     if (s_done) return;
-    const int it = S->iters;
-    const double beta = FOLD ? S->beta : 0.0;
-    const int emax = cg_bound_emax(S);
+    const int emax = cg_pemax(S);
     const bool conv = cg_xs_ok(emax);
     const SpmvPlan P = spmv_plan(A);
     uint32_t seq = 0;
     bool aborted = false, drained = true;
     double pq = 0.0;
-    unsigned pm = 0;
     for (SpmvShare sh = spmv_share(A, P, blockIdx.x, gridDim.x); sh.next < sh.last;) {
         int64_t tile;
         int kb, ke;
         spmv_next_run(A, sh, tile, kb, ke);
-        pq += conv ? spmv_item_tma<true, FOLD>(&map, &rmap, A, q, pn, beta, emax, P, tile, kb, ke, stage, bars,
-                                               seq, aborted, drained, pm)
-                   : spmv_item_tma<false, FOLD>(&map, &rmap, A, q, pn, beta, emax, P, tile, kb, ke, stage, bars,
-                                                seq, aborted, drained, pm);
+        pq += conv ? spmv_item_tma<true>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained)
+                   : spmv_item_tma<false>(&map, A, q, emax, P, tile, kb, ke, stage, bars, seq, aborted, drained);
         if (aborted) break;   // the same in every thread
     }
     if (aborted) {
@@ -275,8 +220,6 @@ __global__ void __launch_bounds__(kSpBlock, 5)
         if (tid == 0) atomicMax(reinterpret_cast<int*>(&S->done), drained ? 3 : 4);
         return;
     }
-    // p_i's largest |p| for the next iteration's bound, as the p update pass folds it
-    if constexpr (FOLD) cg_fold_max<kSpBlock>(pm, S->pmax, nullptr, it % 3, blockIdx.x == 0);
     allow_dependents();
     const double blk = block_sum<kSpBlock>(pq, sh);
     if (!arrive_last(blk, partials, &S->ticket)) return;
@@ -308,35 +251,22 @@ int spmv_tma_map(CUtensorMap* map, const OpDev& A, const double* p)
 int spmv_tma_launch(const CUtensorMap& map, const OpDev& A, double* q, double* partials, CgScalars* S,
                     int nshares, cudaStream_t stream)
 {
-    const cudaError_t e = launch_dependent(k_cg_spmv_tma<false>, nshares, kSpBlock, stream, map, map, A,
-                                           (double*)nullptr, q, partials, S);
+    const cudaError_t e = launch_dependent(k_cg_spmv_tma, nshares, kSpBlock, stream, map, A, q, partials, S);
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "cg: spmv+dot kernel (TMA-staged)");
 }
 
-int spmv_tma_fold_launch(const CUtensorMap& pmap, const CUtensorMap& rmap, const OpDev& A, double* pn,
-                         double* q, double* partials, CgScalars* S, int nshares, cudaStream_t stream)
-{
-    const cudaError_t e = launch_dependent(k_cg_spmv_tma<true>, nshares, kSpBlock, stream, pmap, rmap, A, pn, q,
-                                           partials, S);
-    return e == cudaSuccess ? HS_OK : cuda_fail(e, "cg: p update + spmv + dot kernel (TMA-staged)");
-}
-
 // Resident TMA-staged blocks, asked once per process (a single GPU): blocks per
-// SM of the two TMA-staged kernels (the fewer), times the SM count.  One count
-// for both, so a solve with the p update folded in and one without split p.q
-// alike.
+// SM at the kernel's registers and shared memory, times the SM count.
 int spmv_shares(int nblocks)
 {
     static const int slots = [] {
-        int a = 0, b = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_spmv_tma<false>, kSpBlock, 0) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cg_spmv_tma<true>, kSpBlock, 0) != cudaSuccess ||
+        int per_sm = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv_tma, kSpBlock, 0) != cudaSuccess ||
             cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             return kNumSMs * kSpMinBlocks;
         }
-        const int per_sm = a < b ? a : b;
         return per_sm > 0 && sms > 0 ? per_sm * sms : kNumSMs * kSpMinBlocks;
     }();
     return nblocks < slots ? nblocks : slots;

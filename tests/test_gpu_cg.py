@@ -170,11 +170,10 @@ def test_unaligned_solution_buffer_same_result(pkg, kind):
                                         ((20, 18, 16), "stencil"), ((12, 10, 14), "csr")])
 def test_launch_count_of_a_solve(pkg, shape, kind):
     """hs_launch_count counts every kernel a solve launches, once: q = A x0, the
-    start kernel, the kernels of each enqueued iteration (iterations go out in
+    start kernel, three kernels per enqueued iteration (iterations go out in
     chunks of 4, 8, 16, then 32 between reads of the stop flag), the final
-    A x and the residual norm -- whichever SpMV kernel the grid takes: two per
-    iteration where the TMA-staged SpMV folds the p update in (176^3), three
-    otherwise (load-staged for nx = 175, row kernel for the small grid, CSR)."""
+    A x and the residual norm -- whichever SpMV kernel the grid takes (TMA-staged
+    for 176^3, load-staged for nx = 175, row kernel for the small grid, CSR)."""
     from paper_2608_11882_gb300 import _native
     nz, ny, nx = shape
     n = nx * ny * nz
@@ -189,5 +188,4 @@ def test_launch_count_of_a_solve(pkg, shape, kind):
     while enq < info["iters"]:
         enq += chunk
         chunk = min(2 * chunk, 32)
-    per_iter = 2 if shape == (176, 176, 176) else 3
-    assert launched == 4 + per_iter * enq
+    assert launched == 4 + 3 * enq
