@@ -98,3 +98,24 @@ def test_mixed_precision_workload_512_rtol_1e10(pkg):
         x, info = cg.run(dev(b), rtol=1e-10, max_iter=200000)
     assert info["converged"] and info["refinements"] >= 1
     assert true_relres(x.cpu().numpy(), b, (n, n, n)) <= 1.5e-10
+
+
+def test_mixed_repeat_runs_agree_bitwise(pkg):
+    """The matrix-free FP32 SpMV forms each new direction into the other of two
+    p buffers, so a second solve on the same context may start from either
+    buffer: its x, iteration and refinement counts must equal the first solve's
+    and a fresh context's bit for bit (ragged x and y tiles: nx = 136 is one
+    128-point tile and 8 points, ny = 21 is two 8-row tiles and 5 rows)."""
+    nz, ny, nx = 40, 21, 136
+    b = cg_rhs(nx * ny * nz, seed=35)
+    op = pkg.Operator.stencil(nx, ny, nz)
+    with pkg.CG(op, mixed=True) as cg:
+        x1, i1 = cg.run(dev(b), rtol=1e-10, max_iter=50000)
+        x2, i2 = cg.run(dev(b), rtol=1e-10, max_iter=50000)
+    with pkg.CG(op, mixed=True) as cg:
+        x3, i3 = cg.run(dev(b), rtol=1e-10, max_iter=50000)
+    assert i1["converged"]
+    for x, i in ((x2, i2), (x3, i3)):
+        assert (i["iters"], i["refinements"]) == (i1["iters"], i1["refinements"])
+        assert np.array_equal(x.cpu().numpy(), x1.cpu().numpy())
+    assert true_relres(x1.cpu().numpy(), b, (nz, ny, nx)) <= 1.5e-10
