@@ -124,3 +124,15 @@ def test_side_selection(bench):
     assert bench.sides_of(ns(no_serving=True)) == set(bench.SIDES) - {"serving"}
     with pytest.raises(SystemExit):
         bench.sides_of(ns(sides="bogus"))
+
+
+def test_cg_byte_models(bench):
+    """Bytes per unknown and iteration behind the CG roofline objects: FP64 CG
+    moves 16 (SpMV) + 48 (x/r update) + 24 (p update) = 88 B per row; the
+    mixed-precision inner iteration 40 B matrix-free (the p update folded into
+    the FP32 SpMV: read r and p, write p and q = 16 B, update 24 B) and 44 B
+    for CSR (SpMV 8 B + 24 B + p update 12 B), each FP32 value 4 B."""
+    assert bench.CG_BYTES_PER_ROW == 16 + 48 + 24
+    assert bench.MIXED_INNER_BYTES_PER_ROW == {"matrix_free": 4 * 4 + 6 * 4, "csr": 2 * 4 + 6 * 4 + 3 * 4}
+    r = bench.hbm_roofline("CG", 851 * 88 * 256.0 ** 3, 228.5, 6794.8, "measured")
+    assert r["frac"] == pytest.approx(851 * 88 * 256.0 ** 3 / 0.2285 / 1e9 / 6794.8)
