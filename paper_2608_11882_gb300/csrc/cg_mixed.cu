@@ -315,7 +315,6 @@ static_assert(kMxBW * sizeof(float) % 16 == 0 && kMxD * sizeof(float) == 16, "TM
 static_assert(kMxTY * 32 == kCgBlock, "one warp per tile row");
 static_assert(2 * kMxTY <= 32, "one warp forms the halo columns");
 
-
 __global__ void __launch_bounds__(kCgBlock)
     k_mx_spmv_tma(const __grid_constant__ CUtensorMap rmap, const __grid_constant__ CUtensorMap pmap,
                   OpDev32 A, float* __restrict__ pn, float* __restrict__ q, double* partials, MxScalars* S)
